@@ -1,0 +1,356 @@
+#!/usr/bin/env python3
+"""Throughput of the fused collide-and-stream update on one (or N) GB300.
+
+Workload (one "step"): one lattice Boltzmann time step (Eq. LB: streaming
+with walls, moments, metric equilibrium, improved forcing with Christoffel
+symbols and body force, BGK) of every instance of a Dean-number sweep: a
+64 x 4 x 256 cylindrical channel (eta = r_i/r_o = 0.975, r_i = 1), 24
+instances = 12 Dean numbers in [25, 60] x tau in {0.55, 0.6}, FP32, started
+from the laminar curved-channel profile plus +-1e-4 seeded noise. The state
+(2 x 258 MB) is larger than L2 (129 MB), so no L2 flush is needed.
+
+Metric: MLUPS (million lattice-node updates per second, whole job).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+For N > 1 launch with torch.distributed.run; every rank runs the full sweep
+on its own GPU (weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+BYTES_PER_UPDATE = {"fp64": 2 * 41 * 8, "fp32": 2 * 41 * 4}
+PROFILE_FILE = os.path.join(ROOT, "profiles", "k_step_fp32_cyl64x4x256_b24.md")
+KERNEL_SOURCES = ["paper_1411_3133_gb300/csrc/lbm_device.cuh", "paper_1411_3133_gb300/csrc/kernels.cuh",
+                  "paper_1411_3133_gb300/csrc/step_f32.cu", "paper_1411_3133_gb300/csrc/lattice.cuh"]
+METRIC = "MLUPS and % of HBM roofline at 1 GB300"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for p in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic():
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel source; else None."""
+    try:
+        text = open(PROFILE_FILE).read()
+    except OSError:
+        return None
+    m_hash = re.search(r"kernel_source_sha:\s*([0-9a-f]+)", text)
+    m_tr = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    if not m_hash or not m_tr or m_hash.group(1) != kernel_source_hash():
+        return None
+    return float(m_tr.group(1))
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def workload_desc():
+    from paper_1411_3133_gb300.workloads import cylinder_sweep
+    return cylinder_sweep()
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), float(parts[3]), parts[4:]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        load = [r for r in rows if r[2] > 200.0] or rows
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in load:
+            for name, flag in zip(names, r[3][1:]):
+                if flag.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(r[0] for r in load), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": sorted(reasons), "samples": len(load),
+                "power_w_max": max(r[2] for r in rows)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (reference arm and cpu_baseline)
+# ---------------------------------------------------------------------------
+ORACLE_CHILD = r"""
+import json, sys, time
+import numpy as np
+sys.path.insert(0, {root!r})
+from oracle.geometry import Channel
+from oracle.lbm import Params, Simulation
+from paper_1411_3133_gb300.workloads import cylinder_sweep, noise_field
+wl = cylinder_sweep()
+ch = Channel(**wl.geometry_kwargs())
+sim = Simulation(ch, Params(wl.taus[0], 1e-6))
+sim.init_rest(noise_field(wl.seeds[0], ch.ncells, wl.noise_amp))
+mode, steps, reps, budget = {mode!r}, {steps}, {reps}, {budget}
+if mode == "full":
+    sim.step(1)
+    out = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        sim.step(steps)
+        out.append(time.perf_counter() - t0)
+    print(json.dumps({{"seconds": out, "cells": ch.ncells * steps}}))
+else:
+    # each rep updates one contiguous block of m nodes (one step of the
+    # oracle restricted to those nodes), m sized so that all reps fit budget
+    t0 = time.perf_counter(); sim.step_cells(np.arange(2048)); c = (time.perf_counter() - t0) / 2048
+    m = int(min(ch.ncells, max(64, budget / reps / c)))
+    cells = np.arange(m)
+    out = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        sim.step_cells(cells)
+        out.append(time.perf_counter() - t0)
+    print(json.dumps({{"seconds": out, "cells": m}}))
+"""
+
+
+def time_oracle(mode: str, steps: int = 1, reps: int = 1, budget: float = 120.0):
+    """Time the oracle on one instance of the workload, single-threaded BLAS,
+    in a fresh process (no CUDA context). mode "full": `reps` timings of
+    `steps` whole steps; mode "sample": `reps` one-step updates of a block of
+    nodes sized to fit `budget` seconds in total."""
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[k] = "1"
+    code = ORACLE_CHILD.format(root=ROOT, mode=mode, steps=steps, reps=reps, budget=budget)
+    res = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
+                         timeout=3600)
+    if res.returncode != 0:
+        raise RuntimeError(res.stderr[-2000:])
+    return json.loads(res.stdout.strip().splitlines()[-1])
+
+
+# ---------------------------------------------------------------------------
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20000)
+    ap.add_argument("--warmup", type=int, default=200)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--cpu-steps", type=int, default=20)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    assert args.warmup >= 3, "at least 3 warm-up steps"
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        return reference_arm(args, rank)
+
+    import numpy as np
+    import torch
+
+    from paper_1411_3133_gb300 import build as _build
+    from paper_1411_3133_gb300 import lbgm as L
+
+    _build.build()
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+
+    wl = workload_desc()
+    spec = L.ChannelSpec(**wl.geometry_kwargs())
+    desc = spec.desc()
+    params = []
+    for b in range(wl.batch):
+        G = L.lb_force_for_dean("cylindrical", desc, wl.taus[b], wl.deans[b])
+        params.append(L.make_params(wl.taus[b], G, False, wl.seeds[b] + 1000 * rank, wl.noise_amp, True))
+    ctx = L.LBContext(spec, batch=wl.batch, precision=wl.precision)
+    ctx.lb_set_option(L.LB_OPT_USE_GRAPH, 1)
+    ctx.lb_init(params)
+    cells = wl.batch * wl.ncells
+    stream = ctx.stream
+
+    # warm-up
+    ctx.lb_step(args.warmup)
+    torch.cuda.synchronize()
+
+    # timed region: K steps = K launches of the fused step kernel
+    sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    if sampler:
+        sampler.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    ctx.lb_step(args.steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms = ev0.elapsed_time(ev1)
+    clocks = sampler.stop() if sampler else None
+    d = ctx.lb_diagnostics()
+    finite = all(x["nonfinite"] == 0 for x in d)
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    sec = ms / 1e3
+    value = world * cells * args.steps / sec / 1e6
+    per_launch = sec / args.steps
+    bpu = BYTES_PER_UPDATE[wl.precision]
+    achieved = bpu * cells / per_launch / 1e9
+    peak, peak_kind = peaks()
+    traffic = measured_traffic()
+
+    # end to end through the C ABI with host buffers: each step uploads the
+    # state from pinned host memory, advances it one step and reads it back
+    nbytes = ctx.lb_state_bytes()
+    host_in = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+    host_out = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+    ctx.lb_get_state(host_in)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        ctx.lb_set_state(host_in)
+        ctx.lb_step(1)
+        ctx.lb_get_state(host_out)
+    torch.cuda.synchronize()
+    e2e_sec = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([e2e_sec], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_sec = float(t.item())
+    e2e_value = world * cells * args.e2e_steps / e2e_sec / 1e6
+    ctx.close()
+
+    if rank == 0:
+        cpu = None
+        if not args.no_cpu_baseline:
+            r = time_oracle("full", steps=args.cpu_steps)
+            cpu = {"value": r["cells"] / sum(r["seconds"]) / 1e6, "unit": "MLUPS",
+                   "cores": 1, "kind": "oracle",
+                   "sample": f"{args.cpu_steps} steps of one 64x4x256 instance of the same sweep "
+                             f"(numpy FP64 oracle, single-threaded BLAS, {sum(r['seconds']):.1f} s)"}
+        line = {
+            "metric": METRIC, "value": round(value, 2), "unit": "MLUPS", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 6),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": f"Dean sweep, cylindrical channel {wl.nr}x{wl.ntheta}x{wl.n3}, "
+                                   f"eta=0.975, {wl.batch} instances (12 De in 25..60 x tau 0.55/0.6), "
+                                   f"D3Q41, FP32",
+                       "cells_per_instance": wl.ncells, "instances": wl.batch,
+                       "precision": wl.precision, "bytes_per_update": bpu,
+                       "l2": f"inputs larger than L2: state {2 * nbytes / 1e6:.0f} MB, no flush",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+                         "unit": "GB/s", "frac": round(achieved / peak, 4),
+                         "traffic": traffic, "peak_source": peak_kind,
+                         "kernel": "k_step<float,KCYL>",
+                         "algorithmic_bytes_per_launch": bpu * cells},
+            "e2e": {"value": round(e2e_value, 2), "unit": "MLUPS", "h2d_bytes_per_step": nbytes,
+                    "d2h_bytes_per_step": nbytes, "steps": args.e2e_steps},
+            "gpu_launches": args.steps,
+            "clocks": clocks,
+            "cpu_baseline": cpu,
+            "finite": finite,
+            "dean_measured": [round(x["dean"], 3) for x in d[:3]],
+        }
+        print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+
+
+def reference_arm(args, rank):
+    """The oracle, as it stands, on the host cores. Each step is a bounded
+    sample of the workload: one oracle update of a block of nodes of one
+    instance, sized so that warm-up and timed steps take about two minutes."""
+    if rank != 0:
+        return
+    r = time_oracle("sample", reps=args.warmup + args.steps, budget=120.0)
+    secs = r["seconds"][args.warmup:]
+    sec = sum(secs)
+    value = r["cells"] * len(secs) / sec / 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "MLUPS",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(1e3 * sec / len(secs), 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "Dean sweep, cylindrical channel 64x4x256, eta=0.975, D3Q41 "
+                               f"(each step: {r['cells']} nodes of one instance)",
+                   "parallelism": "host, 1 core"},
+        "cpu_baseline": {"value": round(value, 4), "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                         "sample": f"{len(secs)} one-step updates of {r['cells']} nodes"},
+        "e2e": {"value": round(value, 4), "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

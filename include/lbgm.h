@@ -1,0 +1,230 @@
+/*
+ * lbgm.h -- lattice Boltzmann for generalized metrics on one NVIDIA GB300.
+ *
+ * C ABI of liblbgm.so: the per-time-step fused collide-and-stream update of
+ * the lattice Boltzmann (LB) model in curvilinear coordinates of
+ *   J.-D. Debus, M. Mendoza, H. J. Herrmann, "Dean Instability in
+ *   Double-Curved Channels" (arXiv:1411.3133),
+ * Sec. II (method), Sec. III (cylindrical channel), Sec. IV (double-curved
+ * channel in ellipsoidal coordinates).
+ *
+ * Conventions for every entry point
+ *   - Every call returns lb_status and never aborts the process. On failure
+ *     lb_last_error(ctx) (or lb_last_error(NULL) for calls without a context)
+ *     returns a message.
+ *   - After a CUDA error or a detected non-finite state the context is
+ *     poisoned: lb_step, lb_macros and lb_diagnostics return LB_ERR_STATE
+ *     until lb_init, lb_init_fields, lb_set_populations or lb_set_state
+ *     succeeds.
+ *   - The library owns the device memory of a context (allocated at
+ *     lb_create_geometry, through the caller's lb_allocator if one is given);
+ *     callers own every output buffer they pass in.
+ *   - Work is enqueued on the context's CUDA stream. Calls returning host data
+ *     synchronise that stream. Calls on one context are not thread-safe.
+ *   - Field layout (lb_macros, lb_init_fields): for instance b and node
+ *     (i_r, i_theta, i_3) the linear index is
+ *       b * N + (i_r * ntheta + i_theta) * n3 + i_3,   N = nr * ntheta * n3.
+ *     Vector fields add the component as the slowest axis inside an instance:
+ *       u[(b * 3 + i) * N + cell], i = 0 (r), 1 (theta), 2 (x3).
+ *   - Population layout (lb_get_populations, lb_set_populations):
+ *       f[(b * LB_Q + l) * N + cell], l in the order of lb_velocity_set().
+ *   - Units are lattice units: time step 1, lattice spacing h = (r_outer -
+ *     r_inner) / nr on every axis (Sec. III: Delta r = Delta theta = Delta z
+ *     = Delta t), velocities per step in coordinate components.
+ */
+#ifndef LBGM_H
+#define LBGM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LB_Q 41            /* D3Q41, Table I */
+#define LB_GEO_STRIDE 44   /* doubles per row of lb_geometry_eval */
+
+typedef struct lb_ctx lb_ctx;
+
+typedef enum {
+  LB_OK = 0,
+  LB_ERR_ARG = 1,        /* invalid argument; nothing was changed */
+  LB_ERR_CUDA = 2,       /* a CUDA call failed; context poisoned */
+  LB_ERR_NONFINITE = 3,  /* the state holds NaN/Inf (divergence); poisoned */
+  LB_ERR_TIMEOUT = 4,    /* a bounded device wait gave up */
+  LB_ERR_STATE = 5       /* context poisoned or not initialised */
+} lb_status;
+
+typedef enum {
+  LB_METRIC_FLAT = 0,         /* Cartesian channel, walls normal to x^1 */
+  LB_METRIC_CYLINDRICAL = 1,  /* (r, theta, z), Sec. III */
+  LB_METRIC_ELLIPSOIDAL = 2   /* (r, theta, phi), a = c = 1, Sec. IV */
+} lb_metric;
+
+typedef enum {
+  LB_FP64 = 0,          /* populations and arithmetic in FP64 */
+  LB_FP32 = 1,          /* populations and arithmetic in FP32 */
+  LB_FP16_SHIFTED = 2,  /* reserved: FP16 deviations, FP32 arithmetic */
+  LB_BF16_SHIFTED = 3   /* reserved: BF16 deviations, FP32 arithmetic */
+} lb_precision;
+
+/* Channel geometry (Sec. III lattice map; Sec. IV lattice map and the
+ * rescaled spacings of Sec. IV.B).
+ *   Nodes sit at r = r_inner + (i_r + 1/2) h, i_r = 0..nr-1, so that the walls
+ *   are halfway outside the first and last node, exactly at r_inner and
+ *   r_outer. The third axis is centred: x3 = (i_3 + 1/2 - n3/2) h * d3_scale.
+ *   The metric is evaluated at theta = 0 for every theta node (quasi-2-D
+ *   channel, periodic in theta); the Christoffel symbols of both coordinate
+ *   systems do not depend on theta. */
+typedef struct {
+  double r_inner, r_outer;  /* wall positions, 0 < r_inner < r_outer
+                               (any r_inner < r_outer for FLAT) */
+  double b;                 /* ellipsoid semi-axis b > 0; ignored otherwise */
+  int nr, ntheta, n3;       /* nodes per axis: nr >= 7, ntheta >= 1, n3 >= 1
+                               (n3 >= 7 when periodic3 == 0) */
+  int periodic3;            /* 1: periodic third axis; 0: walls there too */
+  double dtheta_scale;      /* Delta theta / h (> 0; 1 unless rescaled) */
+  double d3_scale;          /* Delta x3 / h (> 0; 1 unless rescaled) */
+} lb_geometry_desc;
+
+/* Per-instance run parameters (Sec. II; Sec. III for the driving force). */
+typedef struct {
+  double tau;               /* BGK relaxation time in steps, > 1/2;
+                               nu = (tau - 1/2) cs^2 (Eq. viscosity) */
+  double force_G;           /* constant covariant streamwise force per step:
+                               F^i_ext = g^{i theta} * force_G */
+  int old_forcing;          /* 0: improved forcing a2 = a2^eq - sigma (Sec. II);
+                               1: the earlier method, a2 = a2^eq */
+  unsigned long long seed;  /* velocity noise seed (see lb_init) */
+  double noise_amp;         /* noise amplitude (lattice velocity units) */
+  int init_base_flow;       /* 1: start from the laminar profile for force_G
+                               (FLAT and CYLINDRICAL with dtheta_scale == 1) */
+} lb_params;
+
+/* Observables of one instance (Sec. III Eq. dean-number and its Sec. IV
+ * form, the mean streamwise velocity and the mean absolute streamwise
+ * vorticity). */
+typedef struct {
+  double mass_rho_prime;    /* sum over nodes of rho' */
+  double mass_physical;     /* sum over nodes of rho' g  (= rho sqrt g) */
+  double mean_v_theta;      /* <v_theta>, area mean of sqrt(g_thth) u^theta */
+  double dean;              /* <v_theta> nr / nu * sqrt(d / R); 0 for FLAT */
+  double mean_vorticity;    /* <omega^theta> */
+  double vortex_amp;        /* rms of u^r over all nodes */
+  double vortex_amp_x3;     /* rms of u^r minus its mean along x3 */
+  double max_speed;         /* largest Euclidean norm of u (coordinates) */
+  long long nonfinite;      /* nodes with a non-finite rho' or u */
+  long long step;           /* time steps since initialisation */
+} lb_diag;
+
+/* Optional device allocator (e.g. a framework's caching allocator). alloc
+ * returns a device pointer aligned to 256 bytes or NULL; free releases it. */
+typedef struct {
+  void* (*alloc)(size_t bytes, void* stream, void* user);
+  void (*free)(void* ptr, size_t bytes, void* stream, void* user);
+  void* user;
+} lb_allocator;
+
+typedef enum {
+  LB_OPT_CHECK_EVERY = 0,   /* lb_step checks for non-finite values every k
+                               steps (k >= 0; 0: never; default 0) */
+  LB_OPT_BLOCK_THREADS = 1, /* threads per block of the step kernel
+                               (64..256, multiple of 32; default 256) */
+  LB_OPT_USE_GRAPH = 2      /* 1: lb_step replays a captured CUDA graph of
+                               pairs of steps (default 0) */
+} lb_option;
+
+/* --------------------------------------------------------------------- */
+
+/* Library's D3Q41 velocities c[l*3 + i] and weights w[l] (Table I) in the
+ * order used by lb_get_populations. Either pointer may be NULL. Returns
+ * LB_Q. Host only. */
+int lb_velocity_set(int* c, double* w);
+
+/* Host-only geometry evaluation (Sec. III metric and symbols; Sec. IV metric
+ * and symbols; Sec. IV.B rescaling; lattice Christoffels h * Gamma). Writes
+ * nr * n3 rows (row = i_r * n3 + i_3) of LB_GEO_STRIDE doubles:
+ *   [0..8]   Delta^ij = g^ij - delta^ij   (row-major 3x3, scaled metric)
+ *   [9..35]  h * Gamma^i_jk               (index (i*3 + j)*3 + k)
+ *   [36..38] g^{i theta}                  (body force per unit force_G)
+ *   [39] sqrt(det g)   [40] sqrt(g_thth)  [41] area weight of the (r, x3)
+ *   cross-section (physical metric)       [42] sqrt(g_thth) physical
+ *   [43] physical radius r of the node.
+ * out_len is the capacity of out in doubles. Needs no GPU. */
+lb_status lb_geometry_eval(lb_metric metric, const lb_geometry_desc* geom,
+                           double* out, size_t out_len);
+
+/* Force per step giving Dean number De in the laminar state (Sec. III Eq.
+ * dean-number with the curved channel Poiseuille profile v = A r ln r + B r
+ * + C / r, A = -G / (2 nu h^2), averaged over the nodes). CYLINDRICAL with
+ * dtheta_scale == 1 only (LB_ERR_ARG otherwise). Needs no GPU. */
+lb_status lb_force_for_dean(lb_metric metric, const lb_geometry_desc* geom,
+                            double tau, double De, double* G_out);
+
+/* Create a context holding `batch` independent instances of one channel
+ * geometry (each with its own lb_params), in precision `prec`, working on
+ * `cuda_stream` (a cudaStream_t; NULL: the library creates its own stream).
+ * Evaluates the geometry on the host in FP64 (lb_geometry_eval) and uploads
+ * it. `alloc` may be NULL (cudaMalloc). On success *out owns its memory
+ * until lb_destroy. */
+lb_status lb_create_geometry(lb_metric metric, const lb_geometry_desc* geom,
+                             int batch, lb_precision prec, void* cuda_stream,
+                             const lb_allocator* alloc, lb_ctx** out);
+
+/* Initial state (end of Sec. II: f = f^eq(rho', u) from initial fields) for
+ * every instance b from params[b]: rho' = 1/sqrt(g) (uniform rho = rho' sqrt g
+ * = 1, Sec. IV) and u = base flow (init_base_flow) plus noise
+ *   u^i += noise_amp * (2 U - 1),  U = (s >> 11) * 2^-53,
+ * where s is output number k = 3 * cell + i (cell within the instance,
+ * counting from 0) of the SplitMix64 generator seeded with params[b].seed.
+ * Resets the step counter. */
+lb_status lb_init(lb_ctx* ctx, const lb_params* params);
+
+/* Initial state f = f^eq(rho', u) from caller fields rho[batch * N] and
+ * u[batch * 3 * N] (host pointers if on_device == 0, else device pointers on
+ * the context's device), with params[b] for tau and the force. */
+lb_status lb_init_fields(lb_ctx* ctx, const lb_params* params, const double* rho,
+                         const double* u, int on_device);
+
+/* n >= 0 time steps (Eq. LB): pull streaming with full bounce-back at the
+ * walls, moments, f^eq, non-equilibrium stress, forcing term with the
+ * Christoffel symbols and the body force, BGK collision. Asynchronous unless
+ * LB_OPT_CHECK_EVERY is set; then returns LB_ERR_NONFINITE when a check
+ * finds a non-finite density. */
+lb_status lb_step(lb_ctx* ctx, long long n);
+
+/* rho' and u of the current state (moments of the streamed populations,
+ * Sec. II) into rho[batch * N], u[batch * 3 * N] (either may be NULL). */
+lb_status lb_macros(lb_ctx* ctx, double* rho, double* u, int on_device);
+
+/* Observables of every instance into out[batch] (host). Synchronises. */
+lb_status lb_diagnostics(lb_ctx* ctx, lb_diag* out);
+
+/* Populations of the state as FP64 in the documented layout, f[batch * LB_Q
+ * * N]. For LB_FP32 the conversion is exact both ways. */
+lb_status lb_get_populations(lb_ctx* ctx, double* f, int on_device);
+lb_status lb_set_populations(lb_ctx* ctx, const double* f, int on_device);
+
+/* Raw state for checkpointing (private layout, native precision) plus the
+ * step counter. lb_state_bytes gives the size. */
+size_t lb_state_bytes(const lb_ctx* ctx);
+lb_status lb_get_state(lb_ctx* ctx, void* buf, size_t bytes, int on_device);
+lb_status lb_set_state(lb_ctx* ctx, const void* buf, size_t bytes, int on_device);
+
+/* Set a context option (lb_option). */
+lb_status lb_set_option(lb_ctx* ctx, int option, long long value);
+
+/* Time steps taken since initialisation. */
+long long lb_step_count(const lb_ctx* ctx);
+
+/* Release everything the context owns. NULL is allowed. */
+void lb_destroy(lb_ctx* ctx);
+
+/* Message of the last failure on ctx (NULL: of the calling thread's last
+ * call without a context). Never NULL. */
+const char* lb_last_error(const lb_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBGM_H */

@@ -1,0 +1,214 @@
+// Initialisation, macroscopic fields, state conversion and the observables
+// reduction (Sec. II initial state and moments; Sec. III-IV Dean number,
+// mean velocity and mean vorticity).
+#include "kernels.cuh"
+#include "launch.h"
+
+namespace lbgm {
+
+namespace {
+
+uint32_t blocks_for(const Dims& d, int threads) {
+  const uint32_t total = uint32_t(d.batch) * uint32_t(d.ncell);
+  return (total + threads - 1) / threads;
+}
+
+template <typename Real>
+cudaError_t macros_t(int K, const Real* fin, double* rho, double* u, const Dims& d, cudaStream_t s) {
+  const uint32_t nb = blocks_for(d, 256);
+  switch (K) {
+    case KFLAT: k_macros<Real, KFLAT><<<nb, 256, 0, s>>>(fin, rho, u, d); break;
+    case KCYL: k_macros<Real, KCYL><<<nb, 256, 0, s>>>(fin, rho, u, d); break;
+    case KELL: k_macros<Real, KELL><<<nb, 256, 0, s>>>(fin, rho, u, d); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+template <typename Real>
+cudaError_t init_t(int K, Real* f, const GeoDev<Real>& geo, const double* sqrtg, const double* base,
+                   const InitInst* ini, const double* rho_in, const double* u_in, const Dims& d,
+                   cudaStream_t s) {
+  const uint32_t nb = blocks_for(d, 256);
+  switch (K) {
+    case KFLAT: k_init<Real, KFLAT><<<nb, 256, 0, s>>>(f, geo, sqrtg, base, ini, rho_in, u_in, d); break;
+    case KCYL: k_init<Real, KCYL><<<nb, 256, 0, s>>>(f, geo, sqrtg, base, ini, rho_in, u_in, d); break;
+    case KELL: k_init<Real, KELL><<<nb, 256, 0, s>>>(f, geo, sqrtg, base, ini, rho_in, u_in, d); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+template <typename Real>
+__global__ void k_convert(Real* state, double* dbl, size_t n, int to_double) {
+  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n;
+       i += size_t(gridDim.x) * blockDim.x) {
+    if (to_double)
+      dbl[i] = double(state[i]);
+    else
+      state[i] = Real(dbl[i]);
+  }
+}
+
+// mean of u^r along x3 for every (instance, i_r, i_theta) row
+__global__ void k_rowmean(const double* __restrict__ u, double* __restrict__ rowmean, Dims d) {
+  const int rows_per = d.nr * d.nt;
+  const int row = blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= d.batch * rows_per) return;
+  const int b = row / rows_per;
+  const int rr = row - b * rows_per;
+  const double* ur = u + size_t(b) * 3 * d.ncell + size_t(rr) * d.n3;
+  double s = 0.0;
+  for (int i = 0; i < d.n3; ++i) s += ur[i];
+  rowmean[row] = s / d.n3;
+}
+
+// derivative along an axis from the values at offsets -1, 0, +1; the wall
+// version uses u = 0 half a node outside the first and last node.
+__device__ __forceinline__ double d_axis(double um, double u0, double up, int i, int n, bool walled) {
+  if (!walled) return 0.5 * (up - um);
+  if (n == 1) return 0.0;
+  if (i == 0) return u0 + up / 3.0;
+  if (i == n - 1) return -(u0 + um / 3.0);
+  return 0.5 * (up - um);
+}
+
+constexpr int DIAG_THREADS = 256;
+
+__device__ __forceinline__ void block_reduce(double (&a)[DIAG_NQ], double* sh) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < DIAG_NQ; ++q) {
+    double v = a[q];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double w = __shfl_down_sync(0xffffffffu, v, o);
+      v = (q == 7) ? fmax(v, w) : v + w;
+    }
+    if (lane == 0) sh[warp * DIAG_NQ + q] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < DIAG_NQ) {
+    const int q = threadIdx.x;
+    double v = sh[q];
+    for (int w = 1; w < DIAG_THREADS / 32; ++w)
+      v = (q == 7) ? fmax(v, sh[w * DIAG_NQ + q]) : v + sh[w * DIAG_NQ + q];
+    a[q] = v;  // valid in thread q only
+  }
+}
+
+// Per-block partial sums of one instance (blockIdx.y), in a fixed order.
+//   0 rho'   1 rho' g   2 sqrt(g_thth) u^theta wA   3 wA   4 |omega| wOmega
+//   5 (u^r)^2   6 (u^r - row mean)^2   7 max |u|   8 non-finite nodes
+__global__ void __launch_bounds__(DIAG_THREADS)
+    k_diag_partial(const double* __restrict__ rho, const double* __restrict__ u,
+                   const double* __restrict__ rowmean, const double* __restrict__ geo64, Dims d,
+                   double* __restrict__ partial, int nblk) {
+  __shared__ double sh[(DIAG_THREADS / 32) * DIAG_NQ];
+  const int b = blockIdx.y;
+  const int N = d.ncell;
+  const double* ur = u + size_t(b) * 3 * N;
+  const double* ut = ur + N;
+  const double* uz = ur + 2 * size_t(N);
+  const double* rb = rho + size_t(b) * N;
+  double a[DIAG_NQ];
+#pragma unroll
+  for (int q = 0; q < DIAG_NQ; ++q) a[q] = 0.0;
+  const int plane = d.nt * d.n3;
+  for (int c = blockIdx.x * DIAG_THREADS + threadIdx.x; c < N; c += nblk * DIAG_THREADS) {
+    const int ir = c / plane;
+    const int rem = c - ir * plane;
+    const int it = rem / d.n3;
+    const int i3 = rem - it * d.n3;
+    const double* gr = geo64 + size_t(ir * d.n3 + i3) * 4;
+    const double sg = gr[0], sp = gr[1], wA = gr[2], wOm = gr[3];
+    const double r = rb[c];
+    const double u0 = ur[c], u1 = ut[c], u2 = uz[c];
+    // d_3 u^r
+    double um, up;
+    if (d.periodic3) {
+      um = ur[c - i3 + (i3 == 0 ? d.n3 - 1 : i3 - 1)];
+      up = ur[c - i3 + (i3 == d.n3 - 1 ? 0 : i3 + 1)];
+    } else {
+      um = i3 > 0 ? ur[c - 1] : 0.0;
+      up = i3 < d.n3 - 1 ? ur[c + 1] : 0.0;
+    }
+    const double d3ur = d_axis(um, u0, up, i3, d.n3, !d.periodic3);
+    // d_r u^3 (walls on r)
+    const double zm = ir > 0 ? uz[c - plane] : 0.0;
+    const double zp = ir < d.nr - 1 ? uz[c + plane] : 0.0;
+    const double drz = d_axis(zm, u2, zp, ir, d.nr, true);
+    const double fl = u0 - rowmean[(size_t(b) * d.nr + ir) * d.nt + it];
+    a[0] += r;
+    a[1] += sg * sg * r;
+    a[2] += sp * u1 * wA;
+    a[3] += wA;
+    a[4] += fabs(d3ur - drz) * wOm;
+    a[5] += u0 * u0;
+    a[6] += fl * fl;
+    a[7] = fmax(a[7], sqrt(u0 * u0 + u1 * u1 + u2 * u2));
+    const bool fin = isfinite(r) && isfinite(u0) && isfinite(u1) && isfinite(u2);
+    a[8] += fin ? 0.0 : 1.0;
+  }
+  block_reduce(a, sh);
+  if (threadIdx.x < DIAG_NQ) partial[(size_t(b) * nblk + blockIdx.x) * DIAG_NQ + threadIdx.x] =
+      a[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(DIAG_THREADS)
+    k_diag_final(const double* __restrict__ partial, int nblk, double* __restrict__ out) {
+  __shared__ double sh[(DIAG_THREADS / 32) * DIAG_NQ];
+  const int b = blockIdx.x;
+  double a[DIAG_NQ];
+#pragma unroll
+  for (int q = 0; q < DIAG_NQ; ++q) a[q] = 0.0;
+  for (int k = threadIdx.x; k < nblk; k += DIAG_THREADS) {
+    const double* p = partial + (size_t(b) * nblk + k) * DIAG_NQ;
+#pragma unroll
+    for (int q = 0; q < DIAG_NQ; ++q) a[q] = (q == 7) ? fmax(a[q], p[q]) : a[q] + p[q];
+  }
+  block_reduce(a, sh);
+  if (threadIdx.x < DIAG_NQ) out[size_t(b) * DIAG_NQ + threadIdx.x] = a[threadIdx.x];
+}
+
+}  // namespace
+
+cudaError_t launch_macros(int prec, int K, const void* fin, double* rho, double* u, const Dims& d,
+                          cudaStream_t s) {
+  if (prec == 0) return macros_t<double>(K, static_cast<const double*>(fin), rho, u, d, s);
+  return macros_t<float>(K, static_cast<const float*>(fin), rho, u, d, s);
+}
+
+cudaError_t launch_init(int prec, int K, void* f, const void* geo, const double* sqrtg,
+                        const double* base_uth, const InitInst* ini, const double* rho_in,
+                        const double* u_in, const Dims& d, cudaStream_t s) {
+  if (prec == 0)
+    return init_t<double>(K, static_cast<double*>(f), *static_cast<const GeoDev<double>*>(geo), sqrtg,
+                          base_uth, ini, rho_in, u_in, d, s);
+  return init_t<float>(K, static_cast<float*>(f), *static_cast<const GeoDev<float>*>(geo), sqrtg,
+                       base_uth, ini, rho_in, u_in, d, s);
+}
+
+cudaError_t launch_convert(int prec, int to_double, void* state, double* dbl, size_t n,
+                           cudaStream_t s) {
+  const int threads = 256;
+  const size_t want = (n + threads - 1) / threads;
+  const int blocks = int(want < 152 * 16 ? (want ? want : 1) : 152 * 16);
+  if (prec == 0)
+    k_convert<double><<<blocks, threads, 0, s>>>(static_cast<double*>(state), dbl, n, to_double);
+  else
+    k_convert<float><<<blocks, threads, 0, s>>>(static_cast<float*>(state), dbl, n, to_double);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_diag(const double* rho, const double* u, double* rowmean, const double* geo64,
+                        const Dims& d, double* partial, int nblk, double* out, cudaStream_t s) {
+  const int rows = d.batch * d.nr * d.nt;
+  k_rowmean<<<(rows + 255) / 256, 256, 0, s>>>(u, rowmean, d);
+  k_diag_partial<<<dim3(nblk, d.batch), DIAG_THREADS, 0, s>>>(rho, u, rowmean, geo64, d, partial,
+                                                              nblk);
+  k_diag_final<<<d.batch, DIAG_THREADS, 0, s>>>(partial, nblk, out);
+  return cudaGetLastError();
+}
+
+}  // namespace lbgm

@@ -1,0 +1,35 @@
+// Host-side launchers of the device kernels (one translation unit per
+// precision for the step kernel so that the large unrolled bodies compile in
+// parallel).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "lbm_device.cuh"
+
+namespace lbgm {
+
+struct InitInst;
+
+cudaError_t launch_step_f64(int K, const double* fin, double* fout, const GeoDev<double>& geo,
+                            const InstParams<double>* inst, const Dims& d, int* flag, int threads,
+                            cudaStream_t s);
+cudaError_t launch_step_f32(int K, const float* fin, float* fout, const GeoDev<float>& geo,
+                            const InstParams<float>* inst, const Dims& d, int* flag, int threads,
+                            cudaStream_t s);
+
+// prec: 0 = FP64, 1 = FP32 (fin/f are double* or float*, geo a GeoDev of that type)
+cudaError_t launch_macros(int prec, int K, const void* fin, double* rho, double* u, const Dims& d,
+                          cudaStream_t s);
+cudaError_t launch_init(int prec, int K, void* f, const void* geo, const double* sqrtg,
+                        const double* base_uth, const InitInst* ini, const double* rho_in,
+                        const double* u_in, const Dims& d, cudaStream_t s);
+cudaError_t launch_convert(int prec, int to_double, void* state, double* dbl, size_t n,
+                           cudaStream_t s);
+
+// Observables: NQ sums per instance written to out[batch * DIAG_NQ].
+constexpr int DIAG_NQ = 9;
+cudaError_t launch_diag(const double* rho, const double* u, double* rowmean, const double* geo64,
+                        const Dims& d, double* partial, int nblk, double* out, cudaStream_t s);
+
+}  // namespace lbgm

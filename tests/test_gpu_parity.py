@@ -1,0 +1,299 @@
+"""GPU parity: the CUDA library (through the C ABI) against the FP64 oracle on
+the same seeded inputs, element by element.
+
+Tolerances (stated by the target, applied relative to the field's scale):
+FP64 1e-12 (rho' against max rho', u against max |u|), FP32 1e-5 of u_max.
+Sizes span several thread blocks, ragged tails (n3 not a multiple of 32),
+walls on one and on two axes, theta extents 1, 2 and 4, all three metrics.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from analytic import curved_poiseuille
+from gpu_helpers import Twin, lib, max_rel
+from oracle.diagnostics import diagnostics
+from oracle.geometry import Channel
+from paper_1411_3133_gb300.workloads import noise_field
+
+pytestmark = pytest.mark.gpu
+
+ETA = 0.975
+CYL1 = Channel("cylindrical", 1.0, 1 / ETA, 16, 4, 32)          # 16 x 4 x 32 cylinder
+G_LAMINAR = 1.745e-4                                            # De ~ 0.8 at tau = 0.8
+
+
+def _rest_fields(tw, amps_seeds):
+    rho = np.stack([1.0 / s.sqrtg for s in tw.sims])
+    u = np.stack([noise_field(seed, tw.N, amp) for amp, seed in amps_seeds])
+    return rho, u
+
+
+def _compare_macros(tw, tol_rho, tol_u):
+    rl, ul = tw.lib_macros()
+    ro, uo = tw.oracle_macros()
+    er = max_rel(rl, ro, np.abs(ro).max())
+    eu = max_rel(ul, uo, np.abs(uo).max())
+    assert er <= tol_rho and eu <= tol_u, (er, eu)
+    return er, eu
+
+
+def test_seeded_init_matches_oracle():
+    params = [dict(tau=0.8, seed=20241111, amp=1e-3), dict(tau=0.7, seed=7, amp=2e-2)]
+    tw = Twin(CYL1, params)
+    tw.ctx.lb_init(tw.lparams)
+    for b, s in enumerate(tw.sims):
+        s.init_rest(noise_field(params[b]["seed"], tw.N, params[b]["amp"]))
+    fl = tw.lib_f()
+    fo = np.stack([s.f for s in tw.sims])
+    assert max_rel(fl, fo, np.abs(fo).max()) <= 1e-14
+    tw.close()
+
+
+def test_base_flow_init_matches_closed_form():
+    params = [dict(tau=0.8, G=G_LAMINAR, seed=3, amp=1e-4, base=True)]
+    tw = Twin(CYL1, params)
+    tw.ctx.lb_init(tw.lparams)
+    _, _, uth = curved_poiseuille(CYL1.r_inner, CYL1.r_outer, CYL1.nr, G_LAMINAR, 0.8)
+    u = noise_field(3, tw.N, 1e-4)
+    u[:, 1] += np.repeat(uth, CYL1.ntheta * CYL1.n3)
+    tw.sims[0].init_rest(u)
+    fo = tw.sims[0].f
+    assert max_rel(tw.lib_f()[0], fo, np.abs(fo).max()) <= 1e-14
+    tw.close()
+
+
+CASES = {
+    "cyl16x4x32": (CYL1, [dict(tau=0.8, G=G_LAMINAR, seed=11, amp=1e-3, base=True)]),
+    "cyl_ragged9x3x13": (Channel("cylindrical", 1.0, 1 / 0.9, 9, 3, 13),
+                         [dict(tau=0.65, G=2e-4, seed=5, amp=5e-3)]),
+    "cyl_ntheta1": (Channel("cylindrical", 1.0, 1 / ETA, 12, 1, 40),
+                    [dict(tau=0.9, G=1e-4, seed=6, amp=1e-3)]),
+    "cyl_old_forcing": (Channel("cylindrical", 1.0, 1 / 0.8, 10, 2, 20),
+                        [dict(tau=0.75, G=3e-4, seed=8, amp=1e-2, old=True)]),
+    "flat_walls4": (Channel("flat", 0.0, 1.0, 8, 2, 9, periodic3=False),
+                    [dict(tau=0.6, G=1e-3, seed=9, amp=1e-2)]),
+    "ell_4walls": (Channel("ellipsoidal", 1.0, 1.1, 10, 4, 14, b=0.9, periodic3=False),
+                   [dict(tau=0.7, G=3e-4, seed=10, amp=1e-2)]),
+    "ell_rescaled": (Channel("ellipsoidal", 0.5, 0.525, 12, 2, 40, b=2 ** 0.5, periodic3=False,
+                             dtheta_scale=1.0, d3_scale=2.0),
+                     [dict(tau=0.55, G=5e-4, seed=12, amp=1e-2)]),
+    "ell_periodic_phi": (Channel("ellipsoidal", 1.0, 1.1, 8, 3, 35, b=1.2),
+                         [dict(tau=0.8, G=2e-4, seed=13, amp=1e-2)]),
+    "batch3": (Channel("cylindrical", 1.0, 1 / ETA, 8, 4, 33),
+               [dict(tau=0.8, G=1e-4, seed=1, amp=1e-3), dict(tau=0.6, G=3e-4, seed=2, amp=2e-3),
+                dict(tau=1.1, G=0.0, seed=3, amp=5e-3, old=True)]),
+}
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_fp64_step_parity(case):
+    ch, params = CASES[case]
+    tw = Twin(ch, params, "fp64")
+    tw.ctx.lb_init(tw.lparams)
+    for b, s in enumerate(tw.sims):
+        p = params[b]
+        u = noise_field(p["seed"], tw.N, p["amp"])
+        if p.get("base"):
+            _, _, uth = curved_poiseuille(ch.r_inner, ch.r_outer, ch.nr, p["G"], p["tau"])
+            u[:, 1] += np.repeat(uth, ch.ntheta * ch.n3)
+        s.init_rest(u)
+    done = 0
+    for n in (1, 10, 100):
+        tw.step(n - done)
+        done = n
+        _compare_macros(tw, 1e-12, 1e-12)
+    fl, fo = tw.lib_f(), np.stack([s.f for s in tw.sims])
+    assert max_rel(fl, fo, np.abs(fo).max()) <= 1e-12
+    tw.close()
+
+
+def test_fp64_laminar_5000_steps():
+    ch = Channel("cylindrical", 1.0, 1 / ETA, 16, 1, 32)
+    params = [dict(tau=0.8, G=G_LAMINAR, seed=21, amp=1e-4, base=True)]
+    tw = Twin(ch, params, "fp64")
+    tw.ctx.lb_init(tw.lparams)
+    _, _, uth = curved_poiseuille(ch.r_inner, ch.r_outer, ch.nr, G_LAMINAR, 0.8)
+    u = noise_field(21, tw.N, 1e-4)
+    u[:, 1] += np.repeat(uth, ch.ntheta * ch.n3)
+    tw.sims[0].init_rest(u)
+    tw.step(5000)
+    _compare_macros(tw, 1e-12, 1e-12)
+    tw.close()
+
+
+@pytest.mark.parametrize("ch", [CYL1, Channel("ellipsoidal", 1.0, 1.1, 10, 4, 40, b=0.9,
+                                              periodic3=False)], ids=["cyl", "ell"])
+def test_fp32_step_parity(ch):
+    params = [dict(tau=0.8, G=G_LAMINAR, seed=31, amp=1e-3, base=ch.metric == "cylindrical")]
+    tw = Twin(ch, params, "fp32")
+    tw.ctx.lb_init(tw.lparams)
+    u = noise_field(31, tw.N, 1e-3)
+    if ch.metric == "cylindrical":
+        _, _, uth = curved_poiseuille(ch.r_inner, ch.r_outer, ch.nr, G_LAMINAR, 0.8)
+        u[:, 1] += np.repeat(uth, ch.ntheta * ch.n3)
+    tw.sims[0].init_rest(u)
+    done = 0
+    for n in (1, 10, 100):
+        tw.step(n - done)
+        done = n
+        _compare_macros(tw, 1e-5, 1e-5)
+    tw.close()
+
+
+def test_init_fields_matches_oracle():
+    ch = Channel("ellipsoidal", 1.0, 1.1, 9, 2, 16, b=0.8, periodic3=False)
+    params = [dict(tau=0.7, G=1e-4), dict(tau=0.9, G=0.0)]
+    tw = Twin(ch, params, "fp64")
+    rng = np.random.default_rng(0)
+    rho = 1.0 + 0.01 * rng.random((2, tw.N))
+    u = 0.02 * rng.standard_normal((2, tw.N, 3))
+    tw.init_fields(rho, u)
+    fo = np.stack([s.f for s in tw.sims])
+    assert max_rel(tw.lib_f(), fo, np.abs(fo).max()) <= 1e-14
+    tw.step(7)
+    _compare_macros(tw, 1e-12, 1e-12)
+    tw.close()
+
+
+def test_diagnostics_match_oracle():
+    ch = Channel("ellipsoidal", 1.0, 1.1, 10, 3, 16, b=0.9, periodic3=False)
+    params = [dict(tau=0.7, G=3e-4, seed=4, amp=1e-2), dict(tau=0.6, G=1e-4, seed=5, amp=1e-2)]
+    tw = Twin(ch, params, "fp64")
+    tw.ctx.lb_init(tw.lparams)
+    for b, s in enumerate(tw.sims):
+        s.init_rest(noise_field(params[b]["seed"], tw.N, params[b]["amp"]))
+    tw.step(20)
+    dl = tw.ctx.lb_diagnostics()
+    for b, s in enumerate(tw.sims):
+        rho, u = s.macros()
+        do = diagnostics(ch, tw.geo, params[b]["tau"], rho, u)
+        for k in ("mass_rho_prime", "mass_physical", "mean_v_theta", "dean", "mean_vorticity",
+                  "vortex_amp", "vortex_amp_x3", "max_speed"):
+            assert dl[b][k] == pytest.approx(do[k], rel=1e-11, abs=1e-18), k
+        assert dl[b]["nonfinite"] == 0 and dl[b]["step"] == 20
+    tw.close()
+
+
+def test_mass_budget_on_gpu():
+    """sum f(t+1) - sum f(t) = sum_x -2 rho' u^r Gamma^theta_{r theta} (cylinder)."""
+    L = lib()
+    ch = Channel("cylindrical", 1.0, 1 / ETA, 16, 4, 64)
+    tw = Twin(ch, [dict(tau=0.7, G=2e-4, seed=1, amp=1e-2)], "fp64")
+    tw.ctx.lb_init(tw.lparams)
+    g = tw.geo["Gamma_hat"][:, 0, 1, 0, 1]             # h / r per i_r
+    for _ in range(3):
+        f0 = tw.ctx.lb_get_populations().sum()
+        rho, u = tw.lib_macros()
+        src = (-2.0 * rho[0] * u[0, :, 0] * np.repeat(g, ch.ntheta * ch.n3)).sum()
+        tw.ctx.lb_step(1)
+        f1 = tw.ctx.lb_get_populations().sum()
+        assert abs(f1 - f0 - src) <= 1e-13 * f0
+    tw.close()
+
+
+def test_checkpoint_resume_bitwise():
+    L = lib()
+    for prec in ("fp64", "fp32"):
+        tw = Twin(CYL1, [dict(tau=0.8, G=1e-4, seed=2, amp=1e-3)], prec)
+        tw.ctx.lb_init(tw.lparams)
+        tw.ctx.lb_step(5)
+        buf = np.zeros(tw.ctx.lb_state_bytes(), dtype=np.uint8)
+        tw.ctx.lb_get_state(buf)
+        tw.ctx.lb_step(10)
+        a = tw.ctx.lb_get_populations()
+        tw.ctx.lb_set_state(buf)
+        assert tw.ctx.lb_step_count() == 15        # the counter is not part of the raw state
+        tw.ctx.lb_step(10)
+        b = tw.ctx.lb_get_populations()
+        assert np.array_equal(a, b)
+        # populations round trip exactly
+        tw.ctx.lb_set_populations(a)
+        assert np.array_equal(tw.ctx.lb_get_populations(), a)
+        tw.close()
+
+
+def test_graph_replay_matches_plain_launches():
+    L = lib()
+    outs = []
+    for graph in (0, 1):
+        tw = Twin(CYL1, [dict(tau=0.8, G=1e-4, seed=2, amp=1e-3)], "fp32")
+        tw.ctx.lb_set_option(L.LB_OPT_USE_GRAPH, graph)
+        tw.ctx.lb_init(tw.lparams)
+        tw.ctx.lb_step(1)
+        tw.ctx.lb_step(37)
+        outs.append(tw.ctx.lb_get_populations())
+        assert tw.ctx.lb_step_count() == 38
+        tw.close()
+    assert np.array_equal(outs[0], outs[1])
+
+
+def test_block_size_option_is_bitwise_neutral():
+    L = lib()
+    outs = []
+    for threads in (64, 128, 256):
+        tw = Twin(CYL1, [dict(tau=0.8, G=1e-4, seed=2, amp=1e-3)], "fp32")
+        tw.ctx.lb_set_option(L.LB_OPT_BLOCK_THREADS, threads)
+        tw.ctx.lb_init(tw.lparams)
+        tw.ctx.lb_step(12)
+        outs.append(tw.ctx.lb_get_populations())
+        tw.close()
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
+
+
+def test_nan_injection_is_detected_and_poisons():
+    L = lib()
+    tw = Twin(CYL1, [dict(tau=0.8, G=1e-4, seed=2, amp=1e-3)], "fp64")
+    tw.ctx.lb_init(tw.lparams)
+    f = tw.ctx.lb_get_populations()
+    f[0, 5, 100] = np.nan
+    tw.ctx.lb_set_populations(f)
+    tw.ctx.lb_set_option(L.LB_OPT_CHECK_EVERY, 1)
+    with pytest.raises(L.LBError) as e:
+        tw.ctx.lb_step(3)
+    assert e.value.status == L.LB_ERR_NONFINITE
+    with pytest.raises(L.LBError) as e:
+        tw.ctx.lb_step(1)
+    assert e.value.status == L.LB_ERR_STATE
+    tw.ctx.lb_init(tw.lparams)                      # a fresh start clears the poison
+    tw.ctx.lb_step(2)
+    assert tw.ctx.lb_diagnostics()[0]["nonfinite"] == 0
+    tw.close()
+
+
+def test_literal_dean30_on_16_nodes_is_reported():
+    """De = 30 at N_r = 16, tau = 0.8 needs <v> ~ 1.3 (Mach > 2): the run
+    either diverges, which lb_step must report as LB_ERR_NONFINITE, or stays
+    finite; it must not hang or crash."""
+    L = lib()
+    desc = L.make_desc(1.0, 1 / ETA, 16, 4, 32)
+    G = L.lb_force_for_dean("cylindrical", desc, 0.8, 30.0)
+    tw = Twin(CYL1, [dict(tau=0.8, G=G, seed=20241111, amp=1e-4)], "fp64")
+    tw.ctx.lb_set_option(L.LB_OPT_CHECK_EVERY, 100)
+    tw.ctx.lb_init(tw.lparams)
+    try:
+        tw.ctx.lb_step(5000)
+        d = tw.ctx.lb_diagnostics()[0]
+        assert d["nonfinite"] == 0
+    except L.LBError as e:
+        assert e.status == L.LB_ERR_NONFINITE
+    tw.close()
+
+
+def test_state_and_argument_errors():
+    L = lib()
+    tw = Twin(CYL1, [dict(tau=0.8)], "fp32")
+    with pytest.raises(L.LBError) as e:
+        tw.ctx.lb_step(1)
+    assert e.value.status == L.LB_ERR_STATE
+    with pytest.raises(L.LBError) as e:
+        tw.ctx.lb_init([L.make_params(0.5)])
+    assert e.value.status == L.LB_ERR_ARG
+    tw.ctx.lb_init(tw.lparams)
+    with pytest.raises(L.LBError) as e:
+        tw.ctx.lb_step(-1)
+    assert e.value.status == L.LB_ERR_ARG
+    with pytest.raises(L.LBError):
+        tw.ctx.lb_set_option(L.LB_OPT_BLOCK_THREADS, 100)
+    tw.close()
