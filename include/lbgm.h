@@ -217,6 +217,31 @@ lb_status lb_set_option(lb_ctx* ctx, int option, long long value);
 /* Time steps taken since initialisation. */
 long long lb_step_count(const lb_ctx* ctx);
 
+/* Observables of `batch` instances from fields the caller already holds on
+ * the device, for callers that cannot call cudaMalloc -- e.g. a program whose
+ * device memory is all owned by another allocator, or a loop that must not
+ * allocate after start-up. The paper has no counterpart; this is a way to
+ * run lb_diagnostics' reduction without a context.
+ *   metric, geom  the channel (as for lb_create_geometry)
+ *   batch         1..LB_NOALLOC_MAX_BATCH instances
+ *   tau           host array [batch] (for the Dean number)
+ *   rho, u        device arrays [batch * N] and [batch * 3 * N] in the field
+ *                 layout above (e.g. written by lb_macros with on_device = 1)
+ *   cuda_stream   cudaStream_t to work on (NULL: the legacy default stream)
+ *   out           host array [batch]; out[b].step is -1
+ * Allocates no device memory: its working memory is one file-scope device
+ * array of LB_NOALLOC_SCRATCH_BYTES bytes, held by every GPU that loads the
+ * library until the process exits. Sizes needing more return LB_ERR_ARG.
+ * The first call on a device (with it current) looks the array's address up;
+ * make that call before any stream capture. All calls share the array, so
+ * calls that overlap on the GPU race. Synchronises cuda_stream. Errors are
+ * reported through lb_last_error(NULL). */
+#define LB_NOALLOC_SCRATCH_BYTES (4u << 20)
+#define LB_NOALLOC_MAX_BATCH 64
+lb_status lb_diagnostics_noalloc(lb_metric metric, const lb_geometry_desc* geom, int batch,
+                                 const double* tau, const double* rho, const double* u,
+                                 void* cuda_stream, lb_diag* out);
+
 /* Release everything the context owns. NULL is allowed. */
 void lb_destroy(lb_ctx* ctx);
 

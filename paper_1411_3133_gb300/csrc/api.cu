@@ -278,6 +278,8 @@ const void* geo_ptr(lb_ctx* c) {
 
 }  // namespace
 
+void lbgm::set_last_error_noctx(const std::string& msg) { g_err = msg; }
+
 // ---------------------------------------------------------------------------
 extern "C" {
 

@@ -5,6 +5,8 @@
 
 #include <cuda_runtime.h>
 
+#include <string>
+
 #include "lbm_device.cuh"
 
 namespace lbgm {
@@ -31,5 +33,8 @@ cudaError_t launch_convert(int prec, int to_double, void* state, double* dbl, si
 constexpr int DIAG_NQ = 9;
 cudaError_t launch_diag(const double* rho, const double* u, double* rowmean, const double* geo64,
                         const Dims& d, double* partial, int nblk, double* out, cudaStream_t s);
+
+// Message for lb_last_error(NULL) from entry points without a context.
+void set_last_error_noctx(const std::string& msg);
 
 }  // namespace lbgm

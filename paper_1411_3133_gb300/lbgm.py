@@ -84,6 +84,9 @@ SIGNATURES = {
     "lb_set_state": (ctypes.c_int, [_P, _P, ctypes.c_size_t, ctypes.c_int]),
     "lb_set_option": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_longlong]),
     "lb_step_count": (ctypes.c_longlong, [_P]),
+    "lb_diagnostics_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(lb_geometry_desc),
+                                              ctypes.c_int, _D, _P, _P, _P,
+                                              ctypes.POINTER(lb_diag)]),
     "lb_destroy": (None, [_P]),
     "lb_last_error": (ctypes.c_char_p, [_P]),
 }
@@ -193,6 +196,18 @@ def torch_allocator(device=None):
     alloc = lb_allocator(a_fn, f_fn, None)
     alloc._keep = (a_fn, f_fn)   # keep the callbacks alive
     return alloc
+
+
+def lb_diagnostics_noalloc(metric: str, desc: lb_geometry_desc, taus, rho, u, stream=None):
+    """Observables from device fields rho [B*N], u [B*3*N] (torch tensors)
+    without any device allocation by the library; see include/lbgm.h."""
+    taus = np.ascontiguousarray(taus, dtype=np.float64)
+    out = (lb_diag * len(taus))()
+    handle = None if stream is None else ctypes.c_void_p(stream.cuda_stream)
+    _check(load_library().lb_diagnostics_noalloc(METRICS[metric], ctypes.byref(desc), len(taus),
+                                                 taus.ctypes.data_as(_D), _ptr(rho), _ptr(u),
+                                                 handle, out))
+    return [d.as_dict() for d in out]
 
 
 # ---------------------------------------------------------------------------
