@@ -66,6 +66,10 @@ struct lb_ctx {
   int use_graph = 0;
   cudaGraphExec_t graph = nullptr;   // two steps, buffer 0 -> 1 -> 0
   int graph_threads = 0;
+  int graph_kernel = -1;
+  int step_kernel = 0;               // LB_OPT_STEP_KERNEL
+  bool tma_ok = false;               // tensor maps built for both buffers
+  alignas(64) unsigned char tmap[2][128];
 };
 
 namespace {
@@ -238,10 +242,16 @@ std::string check_sparsity(const std::vector<double>& rows, const lb_geometry_de
   return "";
 }
 
+bool use_tma(const lb_ctx* c) { return c->prec == LB_FP32 && c->tma_ok && c->step_kernel != 1; }
+
 lb_status launch_step_once(lb_ctx* c) {
   const int src = c->cur, dst = 1 - c->cur;
   cudaError_t e;
-  if (c->prec == LB_FP64)
+  if (use_tma(c))
+    e = launch_step_tma_f32(c->K, c->tmap[src], static_cast<const float*>(c->f[src]),
+                            static_cast<float*>(c->f[dst]), c->geo_f,
+                            static_cast<const InstParams<float>*>(c->inst), c->dims, c->flag, c->stream);
+  else if (c->prec == LB_FP64)
     e = launch_step_f64(c->K, static_cast<const double*>(c->f[src]), static_cast<double*>(c->f[dst]),
                         c->geo_d, static_cast<const InstParams<double>*>(c->inst), c->dims, c->flag,
                         c->block_threads, c->stream);
@@ -258,6 +268,7 @@ lb_status check_flag(lb_ctx* c) {
   int h = 0;
   LB_CUDA(c, cudaMemcpyAsync(&h, c->flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   LB_CUDA(c, cudaStreamSynchronize(c->stream));
+  if (h & 2) return fail(c, LB_ERR_TIMEOUT, "a bounded device wait expired in the step kernel");
   if (h) return fail(c, LB_ERR_NONFINITE, "non-finite density after step " + std::to_string(c->step));
   return LB_OK;
 }
@@ -445,6 +456,9 @@ lb_status lb_create_geometry(lb_metric metric, const lb_geometry_desc* geom, int
   if (e == cudaSuccess) e = cudaMemsetAsync(c->flag, 0, sizeof(int), c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return bail(LB_ERR_CUDA, std::string("geometry upload: ") + cudaGetErrorString(e));
+  if (prec == LB_FP32 && tma_step_supported(d) && tensor_map_bytes() <= sizeof(c->tmap[0]))
+    c->tma_ok = make_state_tensor_map(c->tmap[0], static_cast<const float*>(c->f[0]), d) == cudaSuccess &&
+                make_state_tensor_map(c->tmap[1], static_cast<const float*>(c->f[1]), d) == cudaSuccess;
   *out = c;
   return LB_OK;
 }
@@ -520,7 +534,7 @@ lb_status lb_step(lb_ctx* c, long long n) {
       ++c->step;
       --n;
     }
-    if (!c->graph || c->graph_threads != c->block_threads) {
+    if (!c->graph || c->graph_threads != c->block_threads || c->graph_kernel != c->step_kernel) {
       if (c->graph) cudaGraphExecDestroy(c->graph);
       c->graph = nullptr;
       cudaGraph_t g = nullptr;
@@ -534,6 +548,7 @@ lb_status lb_step(lb_ctx* c, long long n) {
       cudaGraphDestroy(g);
       if (e != cudaSuccess) return cuda_fail(c, e, "cudaGraphInstantiate");
       c->graph_threads = c->block_threads;
+      c->graph_kernel = c->step_kernel;
     }
     for (long long i = 0; i + 1 < n; i += 2) {
       LB_CUDA(c, cudaGraphLaunch(c->graph, c->stream));
@@ -687,6 +702,12 @@ lb_status lb_set_option(lb_ctx* c, int option, long long value) {
       return LB_OK;
     case LB_OPT_USE_GRAPH:
       c->use_graph = value ? 1 : 0;
+      return LB_OK;
+    case LB_OPT_STEP_KERNEL:
+      if (value < 0 || value > 2) return fail(c, LB_ERR_ARG, "need 0 (auto), 1 (plain) or 2 (TMA)");
+      if (value == 2 && !c->tma_ok)
+        return fail(c, LB_ERR_ARG, "the TMA step kernel needs FP32 and n3 in {128, 256}");
+      c->step_kernel = int(value);
       return LB_OK;
     default:
       return fail(c, LB_ERR_ARG, "unknown option");

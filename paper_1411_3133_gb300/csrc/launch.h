@@ -20,6 +20,15 @@ cudaError_t launch_step_f32(int K, const float* fin, float* fout, const GeoDev<f
                             const InstParams<float>* inst, const Dims& d, int* flag, int threads,
                             cudaStream_t s);
 
+// TMA-pipelined FP32 step (n3 in {128, 256}); map is a CUtensorMap over the
+// input state (make_state_tensor_map).
+bool tma_step_supported(const Dims& d);
+size_t tensor_map_bytes();
+cudaError_t make_state_tensor_map(void* map_out, const float* base, const Dims& d);
+cudaError_t launch_step_tma_f32(int K, const void* map, const float* fin, float* fout,
+                                const GeoDev<float>& geo, const InstParams<float>* inst, const Dims& d,
+                                int* flag, cudaStream_t s);
+
 // prec: 0 = FP64, 1 = FP32 (fin/f are double* or float*, geo a GeoDev of that type)
 cudaError_t launch_macros(int prec, int K, const void* fin, double* rho, double* u, const Dims& d,
                           cudaStream_t s);

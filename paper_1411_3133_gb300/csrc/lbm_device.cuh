@@ -194,6 +194,23 @@ __device__ __forceinline__ bool near_wall(const CellPos& p, const Dims& d) {
   return p.ir < 3 || p.ir > d.nr - 4 || (!d.periodic3 && (p.i3 < 3 || p.i3 > d.n3 - 4));
 }
 
+// Streamed populations of a node near a wall: every moving population from
+// its (possibly folded) source, read from the post-collision state fin.
+template <typename Real>
+__device__ __forceinline__ void gather_wall(const Real* __restrict__ fin, const CellPos& p,
+                                            const Dims& d, Real (&f)[Q]) {
+  const int N = d.ncell;
+  static_for<0, NPAIR>([&](auto P_) {
+    constexpr int P = decltype(P_)::value;
+    using C = Pair<P>;
+    bool fp, fm;
+    const int sp = src_wall<C::x, C::y, C::z, C::s>(p, d, fp);
+    const int sm = src_wall<-C::x, -C::y, -C::z, C::s>(p, d, fm);
+    f[2 * P + 1] = __ldg(fin + (fp ? 2 * P + 2 : 2 * P + 1) * N + sp);
+    f[2 * P + 2] = __ldg(fin + (fm ? 2 * P + 1 : 2 * P + 2) * N + sm);
+  });
+}
+
 // Load the 41 streamed populations of node p from the post-collision state
 // fin (one instance's block: population l of cell c at fin[l * ncell + c]).
 template <typename Real>
@@ -213,15 +230,7 @@ __device__ __forceinline__ void gather(const Real* __restrict__ fin, const CellP
       f[2 * P + 2] = __ldg(fin + (2 * P + 2) * N + sm);
     });
   } else {
-    static_for<0, NPAIR>([&](auto P_) {
-      constexpr int P = decltype(P_)::value;
-      using C = Pair<P>;
-      bool fp, fm;
-      const int sp = src_wall<C::x, C::y, C::z, C::s>(p, d, fp);
-      const int sm = src_wall<-C::x, -C::y, -C::z, C::s>(p, d, fm);
-      f[2 * P + 1] = __ldg(fin + (fp ? 2 * P + 2 : 2 * P + 1) * N + sp);
-      f[2 * P + 2] = __ldg(fin + (fm ? 2 * P + 1 : 2 * P + 2) * N + sm);
-    });
+    gather_wall(fin, p, d, f);
   }
 }
 

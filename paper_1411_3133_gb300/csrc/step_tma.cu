@@ -1,0 +1,243 @@
+// Fused time step, FP32, with the pull gather staged through shared memory by
+// TMA (cp.async.bulk.tensor) in a two-stage mbarrier pipeline.
+//
+// A tile is one (instance, i_r, i_theta) row of NX = n3 nodes. For every
+// population l the tile needs one row of the previous state: the row
+// (i_r - c_r, i_theta - c_theta) of population l, all x3 -- the x3 shift and
+// its periodic wrap are applied when reading shared memory, so every TMA box
+// starts at x3 = 0 (16-byte aligned) and no halo is needed. One thread per
+// node; thread 0 issues the 41 box loads of the tile two ahead into the stage
+// the CTA has just finished reading, so the copies overlap the collision.
+// Rows within 3 nodes of an r-wall, and nodes near x3-walls, gather from
+// global memory with the folded bounce-back path instead.
+//
+// Every wait on an mbarrier is bounded; on expiry the kernel sets bit 1 of
+// the status flag, waits (bounded) for its copies still in flight, and
+// returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include "kernels.cuh"
+#include "launch.h"
+
+namespace lbgm {
+namespace {
+
+constexpr uint32_t kWaitPolls = 1u << 24;
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  for (uint32_t i = 0; i < kWaitPolls; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_row(float* dst, const CUtensorMap* map, uint64_t* bar, int x,
+                                             int t, int r, int pl) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_addr(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(t), "r"(r), "r"(pl), "r"(smem_addr(bar))
+      : "memory");
+}
+
+struct TileRow {
+  int b, ir, it;
+};
+
+__device__ __forceinline__ TileRow tile_row(int tile, const Dims& d) {
+  TileRow tr;
+  const int rows = d.nr * d.nt;
+  tr.b = tile / rows;
+  const int rr = tile - tr.b * rows;
+  tr.ir = rr / d.nt;
+  tr.it = rr - tr.ir * d.nt;
+  return tr;
+}
+
+// 41 box loads of one tile into a stage; the barrier expects all their bytes.
+template <int NX>
+__device__ __forceinline__ void issue_tile(const CUtensorMap* map, float* stage, uint64_t* bar, int tile,
+                                           const Dims& d) {
+  const TileRow tr = tile_row(tile, d);
+  mbar_expect_tx(bar, uint32_t(Q * NX * sizeof(float)));
+  tma_load_row(stage, map, bar, 0, tr.it, tr.ir, tr.b * Q);
+  static_for<0, NPAIR>([&](auto P_) {
+    constexpr int P = decltype(P_)::value;
+    using C = Pair<P>;
+    // population +c comes from row (i_r - c_r, i_theta - c_theta), -c from (+c_r, +c_theta);
+    // rows outside [0, nr) are zero-filled by the TMA unit and never read
+    tma_load_row(stage + (2 * P + 1) * NX, map, bar, 0, wrap_small(tr.it - C::y, d.nt), tr.ir - C::x,
+                 tr.b * Q + 2 * P + 1);
+    tma_load_row(stage + (2 * P + 2) * NX, map, bar, 0, wrap_small(tr.it + C::y, d.nt), tr.ir + C::x,
+                 tr.b * Q + 2 * P + 2);
+  });
+}
+
+template <int K, int NX>
+__global__ void __launch_bounds__(NX, 512 / NX) k_step_tma(const __grid_constant__ CUtensorMap map,
+                                                 const float* __restrict__ fin, float* __restrict__ fout,
+                                                 GeoDev<float> geo, const InstParams<float>* __restrict__ inst,
+                                                 Dims d, int* __restrict__ flag) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  float* stages = reinterpret_cast<float*>(smem);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + 2 * Q * NX * sizeof(float));
+  const int x = threadIdx.x;
+  const int ntiles = d.batch * d.nr * d.nt;
+  const int G = gridDim.x;
+  if (x == 0) {
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (x == 0) {
+    if (int(blockIdx.x) < ntiles) issue_tile<NX>(&map, stages, &bars[0], blockIdx.x, d);
+    if (int(blockIdx.x) + G < ntiles) issue_tile<NX>(&map, stages + Q * NX, &bars[1], blockIdx.x + G, d);
+  }
+  // x3 index of the source of a shift c3 (periodic wrap; NX = n3 is a power of two)
+  int xs[7];
+#pragma unroll
+  for (int c = -3; c <= 3; ++c) xs[c + 3] = (x - c) & (NX - 1);
+
+  int k = 0;
+  for (int tile = blockIdx.x; tile < ntiles; tile += G, ++k) {
+    const int s = k & 1;
+    const bool ok = mbar_wait_bounded(&bars[s], uint32_t((k >> 1) & 1));
+    if (__syncthreads_or(!ok)) {
+      if (x == 0) {
+        atomicOr(flag, 2);
+        // copies may still be in flight into either stage: wait for them (bounded)
+        mbar_wait_bounded(&bars[s], uint32_t((k >> 1) & 1));
+        if (tile + G < ntiles) mbar_wait_bounded(&bars[s ^ 1], uint32_t(((k + 1) >> 1) & 1));
+      }
+      return;
+    }
+    const TileRow tr = tile_row(tile, d);
+    CellPos p;
+    p.b = tr.b;
+    p.ir = tr.ir;
+    p.it = tr.it;
+    p.i3 = x;
+    p.cell = (tr.ir * d.nt + tr.it) * NX + x;
+    const float* st = stages + s * Q * NX;
+    float f[Q];
+    if (!near_wall(p, d)) {
+      f[0] = st[x];
+      static_for<0, NPAIR>([&](auto P_) {
+        constexpr int P = decltype(P_)::value;
+        using C = Pair<P>;
+        f[2 * P + 1] = st[(2 * P + 1) * NX + xs[C::z + 3]];
+        f[2 * P + 2] = st[(2 * P + 2) * NX + xs[-C::z + 3]];
+      });
+    } else {
+      const float* fb = fin + size_t(p.b) * Q * d.ncell;
+      f[0] = __ldg(fb + p.cell);
+      gather_wall(fb, p, d, f);
+    }
+    __syncthreads();  // every read of stage s is done: refill it
+    if (x == 0 && tile + 2 * G < ntiles) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue_tile<NX>(&map, stages + s * Q * NX, &bars[s], tile + 2 * G, d);
+    }
+    const Moments<float> m = moments(f);
+    if (!(fabsf(m.rho) < 1e30f)) {
+      if (*flag == 0) atomicOr(flag, 1);
+    }
+    NodeGeo<float, K> g;
+    const int row = K == KELL ? p.ir * d.geo_rows3 + p.i3 : p.ir;
+    g.load(geo, row);
+    const InstParams<float> ip = inst[p.b];
+    const Coef<float> kc = coefficients<float, K>(m, g, ip.kappa, ip.G);
+    collide<float, K>(f, kc, g, ip.omega);
+    float* out = fout + size_t(p.b) * Q * d.ncell + p.cell;
+#pragma unroll
+    for (int l = 0; l < Q; ++l) out[size_t(l) * d.ncell] = f[l];
+  }
+}
+
+template <int NX>
+cudaError_t launch_nx(int K, const void* map, const float* fin, float* fout, const GeoDev<float>& geo,
+                      const InstParams<float>* inst, const Dims& d, int* flag, cudaStream_t s) {
+  const size_t smem = 2 * Q * NX * sizeof(float) + 64;
+  static int configured[3] = {0, 0, 0};
+  static int blocks_per_sm[3] = {1, 1, 1};
+  static int sms = 0;
+  auto kern = K == KFLAT ? k_step_tma<KFLAT, NX> : K == KCYL ? k_step_tma<KCYL, NX> : k_step_tma<KELL, NX>;
+  if (!configured[K]) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm[K], kern, NX, smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    configured[K] = 1;
+  }
+  const int ntiles = d.batch * d.nr * d.nt;
+  int grid = sms * (blocks_per_sm[K] > 0 ? blocks_per_sm[K] : 1);
+  if (grid > ntiles) grid = ntiles;
+  kern<<<grid, NX, smem, s>>>(*static_cast<const CUtensorMap*>(map), fin, fout, geo, inst, d, flag);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+bool tma_step_supported(const Dims& d) { return d.n3 == 128 || d.n3 == 256; }
+
+size_t tensor_map_bytes() { return sizeof(CUtensorMap); }
+
+cudaError_t make_state_tensor_map(void* map_out, const float* base, const Dims& d) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (!encode) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
+    encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  const cuuint64_t dims[4] = {cuuint64_t(d.n3), cuuint64_t(d.nt), cuuint64_t(d.nr), cuuint64_t(d.batch) * Q};
+  const cuuint64_t strides[3] = {cuuint64_t(d.n3) * 4, cuuint64_t(d.n3) * d.nt * 4,
+                                 cuuint64_t(d.n3) * d.nt * d.nr * 4};
+  const cuuint32_t box[4] = {cuuint32_t(d.n3), 1, 1, 1};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  CUresult r = encode(static_cast<CUtensorMap*>(map_out), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4,
+                      const_cast<float*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                      CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+cudaError_t launch_step_tma_f32(int K, const void* map, const float* fin, float* fout,
+                                const GeoDev<float>& geo, const InstParams<float>* inst, const Dims& d,
+                                int* flag, cudaStream_t s) {
+  if (d.n3 == 256) return launch_nx<256>(K, map, fin, fout, geo, inst, d, flag, s);
+  if (d.n3 == 128) return launch_nx<128>(K, map, fin, fout, geo, inst, d, flag, s);
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace lbgm

@@ -307,3 +307,38 @@ def test_state_and_argument_errors():
     with pytest.raises(L.LBError):
         tw.ctx.lb_set_option(L.LB_OPT_BLOCK_THREADS, 100)
     tw.close()
+
+
+@pytest.mark.parametrize("ch,batch", [
+    (Channel("cylindrical", 1.0, 1 / ETA, 16, 4, 256), 2),
+    (Channel("ellipsoidal", 1.0, 1.1, 12, 3, 128, b=0.9, periodic3=False), 1),
+    (Channel("ellipsoidal", 1.0, 1.1, 9, 2, 128, b=1.1), 1),
+    (Channel("flat", 0.0, 1.0, 10, 1, 256), 3),
+], ids=["cyl256", "ell4wall128", "ellper128", "flat256"])
+def test_tma_kernel_is_bitwise_equal_to_plain_kernel(ch, batch):
+    """The TMA-pipelined FP32 kernel and the plain kernel share the arithmetic;
+    they must give identical states."""
+    L = lib()
+    params = [dict(tau=0.6 + 0.1 * b, G=2e-4, seed=40 + b, amp=1e-2) for b in range(batch)]
+    outs = []
+    for kern in (1, 2):
+        tw = Twin(ch, params, "fp32")
+        tw.ctx.lb_set_option(L.LB_OPT_STEP_KERNEL, kern)
+        tw.ctx.lb_init(tw.lparams)
+        tw.ctx.lb_step(30)
+        outs.append(tw.ctx.lb_get_populations())
+        tw.close()
+    assert np.array_equal(outs[0], outs[1])
+
+
+def test_tma_kernel_option_validation():
+    L = lib()
+    tw = Twin(CYL1, [dict(tau=0.8)], "fp32")          # n3 = 32: not supported
+    with pytest.raises(L.LBError) as e:
+        tw.ctx.lb_set_option(L.LB_OPT_STEP_KERNEL, 2)
+    assert e.value.status == L.LB_ERR_ARG
+    tw.close()
+    tw = Twin(Channel("cylindrical", 1.0, 1 / ETA, 8, 2, 256), [dict(tau=0.8)], "fp64")
+    with pytest.raises(L.LBError):
+        tw.ctx.lb_set_option(L.LB_OPT_STEP_KERNEL, 2)
+    tw.close()
