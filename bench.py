@@ -195,6 +195,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--cpu-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--step-kernel", default="auto", choices=["auto", "plain", "tma"])
     args = ap.parse_args()
     assert args.warmup >= 3, "at least 3 warm-up steps"
 
@@ -227,6 +228,7 @@ def main():
         params.append(L.make_params(wl.taus[b], G, False, wl.seeds[b] + 1000 * rank, wl.noise_amp, True))
     ctx = L.LBContext(spec, batch=wl.batch, precision=wl.precision)
     ctx.lb_set_option(L.LB_OPT_USE_GRAPH, 1)
+    ctx.lb_set_option(L.LB_OPT_STEP_KERNEL, {"auto": 0, "plain": 1, "tma": 2}[args.step_kernel])
     ctx.lb_init(params)
     cells = wl.batch * wl.ncells
     stream = ctx.stream
@@ -311,7 +313,7 @@ def main():
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
                          "unit": "GB/s", "frac": round(achieved / peak, 4),
                          "traffic": traffic, "peak_source": peak_kind,
-                         "kernel": "k_step<float,KCYL>",
+                         "kernel": "k_step_tma<KCYL,256>" if args.step_kernel == "tma" else "k_step<float,KCYL>",
                          "algorithmic_bytes_per_launch": bpu * cells},
             "e2e": {"value": round(e2e_value, 2), "unit": "MLUPS", "h2d_bytes_per_step": nbytes,
                     "d2h_bytes_per_step": nbytes, "steps": args.e2e_steps},

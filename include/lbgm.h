@@ -129,14 +129,15 @@ typedef enum {
   LB_OPT_CHECK_EVERY = 0,   /* lb_step checks for non-finite values every k
                                steps (k >= 0; 0: never; default 0) */
   LB_OPT_BLOCK_THREADS = 1, /* threads per block of the step kernel
-                               (64..256, multiple of 32; default 256) */
+                               (64..256, multiple of 32; default 128) */
   LB_OPT_USE_GRAPH = 2,     /* 1: lb_step replays a captured CUDA graph of
                                pairs of steps (default 0) */
-  LB_OPT_STEP_KERNEL = 3    /* 0: automatic (default); 1: the one-node-per-
-                               thread kernel with gathers from global memory;
-                               2: the TMA-pipelined kernel (FP32 and n3 in
-                               {128, 256} only; LB_ERR_ARG otherwise). Both
-                               give bitwise identical states. */
+  LB_OPT_STEP_KERNEL = 3    /* 0: automatic (default: the one-node-per-
+                               thread kernel, the fastest measured); 1: that
+                               kernel, gathering from global memory; 2: the
+                               TMA-pipelined kernel (FP32 and n3 in {128,
+                               256} only; LB_ERR_ARG otherwise). Both give
+                               bitwise identical states. */
 } lb_option;
 
 /* --------------------------------------------------------------------- */

@@ -62,7 +62,7 @@ struct lb_ctx {
   std::string err;
 
   long long check_every = 0;
-  int block_threads = 256;
+  int block_threads = 128;
   int use_graph = 0;
   cudaGraphExec_t graph = nullptr;   // two steps, buffer 0 -> 1 -> 0
   int graph_threads = 0;
@@ -242,7 +242,7 @@ std::string check_sparsity(const std::vector<double>& rows, const lb_geometry_de
   return "";
 }
 
-bool use_tma(const lb_ctx* c) { return c->prec == LB_FP32 && c->tma_ok && c->step_kernel != 1; }
+bool use_tma(const lb_ctx* c) { return c->prec == LB_FP32 && c->tma_ok && c->step_kernel == 2; }
 
 lb_status launch_step_once(lb_ctx* c) {
   const int src = c->cur, dst = 1 - c->cur;

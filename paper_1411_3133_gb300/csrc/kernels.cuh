@@ -22,12 +22,11 @@ __global__ void __launch_bounds__(256) k_step(const Real* __restrict__ fin, Real
   Real f[Q];
   gather(fin + base, p, d, f);
   const Moments<Real> m = moments(f);
-  if (!(fabs(m.rho) < Real(1e30))) {  // NaN or Inf
+  if (!finite_v(m.rho)) {  // NaN or Inf
     if (*flag == 0) atomicExch(flag, 1);
   }
-  NodeGeo<Real, K> g;
   const int row = K == KELL ? p.ir * d.geo_rows3 + p.i3 : p.ir;
-  g.load(geo, row);
+  const NodeGeo<Real, K> g = load_geo<Real, K>(geo, row);
   const InstParams<Real> ip = inst[p.b];
   const Coef<Real> k = coefficients<Real, K>(m, g, ip.kappa, ip.G);
   collide<Real, K>(f, k, g, ip.omega);
@@ -101,9 +100,8 @@ __global__ void __launch_bounds__(256) k_init(Real* __restrict__ f, GeoDev<Real>
       u[i] += in.amp * (2.0 * U - 1.0);
     }
   }
-  NodeGeo<Real, K> g;
   const int row = K == KELL ? p.ir * d.geo_rows3 + p.i3 : p.ir;
-  g.load(geo, row);
+  const NodeGeo<Real, K> g = load_geo<Real, K>(geo, row);
   Real fe[Q];
   equilibrium<Real, K>(Real(rho), Real(u[0]), Real(u[1]), Real(u[2]), g, fe);
   Real* out = f + size_t(p.b) * Q * d.ncell + p.cell;

@@ -235,63 +235,140 @@ __device__ __forceinline__ void gather(const Real* __restrict__ fin, const CellP
 }
 
 // ---------------------------------------------------------------------------
+// arithmetic types
+// ---------------------------------------------------------------------------
+// The update is written once for an arithmetic type V: double, float, or PF2
+// -- two nodes per thread in packed FP32x2 instructions (FFMA2/FADD2/FMUL2 of
+// sm_100 and later), one node per lane, each lane rounded exactly like the
+// scalar float instruction. Multiplications by the lattice's integer
+// velocity components are spelled out with compile-time helpers (mac, dot3)
+// so that no multiplication by 0 or +-1 is issued for any type.
+struct PF2 {
+  float2 v;
+  PF2() = default;
+  __device__ __forceinline__ PF2(float2 a) : v(a) {}
+  __device__ __forceinline__ PF2(float a, float b) : v(make_float2(a, b)) {}
+  __device__ __forceinline__ explicit PF2(double c) : v(make_float2(float(c), float(c))) {}
+};
+__device__ __forceinline__ PF2 operator+(PF2 a, PF2 b) { return PF2(__fadd2_rn(a.v, b.v)); }
+__device__ __forceinline__ PF2 operator*(PF2 a, PF2 b) { return PF2(__fmul2_rn(a.v, b.v)); }
+__device__ __forceinline__ PF2 operator-(PF2 a, PF2 b) {
+  return PF2(__ffma2_rn(b.v, make_float2(-1.f, -1.f), a.v));
+}
+__device__ __forceinline__ PF2 fmav(PF2 a, PF2 b, PF2 c) { return PF2(__ffma2_rn(a.v, b.v, c.v)); }
+__device__ __forceinline__ float fmav(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fmav(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ PF2 rcpv(PF2 a) { return PF2(__frcp_rn(a.v.x), __frcp_rn(a.v.y)); }
+__device__ __forceinline__ float rcpv(float a) { return 1.0f / a; }
+__device__ __forceinline__ double rcpv(double a) { return 1.0 / a; }
+__device__ __forceinline__ bool finite_v(PF2 a) { return fabsf(a.v.x) < 1e30f && fabsf(a.v.y) < 1e30f; }
+__device__ __forceinline__ bool finite_v(float a) { return fabsf(a) < 1e30f; }
+__device__ __forceinline__ bool finite_v(double a) { return fabs(a) < 1e300; }
+
+// acc + C x, compile-time integer C
+template <int C, class V>
+__device__ __forceinline__ V mac(const V& acc, const V& x) {
+  if constexpr (C == 0) return acc;
+  else if constexpr (C == 1) return acc + x;
+  else if constexpr (C == -1) return acc - x;
+  else return fmav(V(double(C)), x, acc);
+}
+// C x, compile-time integer C != 0
+template <int C, class V>
+__device__ __forceinline__ V mulc(const V& x) {
+  static_assert(C != 0, "mulc by zero");
+  if constexpr (C == 1) return x;
+  else return V(double(C)) * x;
+}
+// cx ax + cy ay + cz az; the first non-zero component of every pair's
+// representative velocity is positive
+template <int CX, int CY, int CZ, class V>
+__device__ __forceinline__ V dot3(const V& ax, const V& ay, const V& az) {
+  if constexpr (CX != 0) return mac<CZ>(mac<CY>(mulc<CX>(ax), ay), az);
+  else if constexpr (CY != 0) return mac<CZ>(mulc<CY>(ay), az);
+  else return mulc<CZ>(az);
+}
+
+// ---------------------------------------------------------------------------
 // moments and collision
 // ---------------------------------------------------------------------------
-template <typename Real>
+template <typename V>
 struct Moments {
-  Real rho, jx, jy, jz;
-  Real sxx, syy, szz, sxy, sxz, syz;  // sum_l c^i c^j f_l
+  V rho, jx, jy, jz;
+  V sxx, syy, szz, sxy, sxz, syz;  // sum_l c^i c^j f_l
 };
 
-template <typename Real>
-__device__ __forceinline__ Moments<Real> moments(const Real (&f)[Q]) {
-  Moments<Real> m;
+template <typename V>
+__device__ __forceinline__ Moments<V> moments(const V (&f)[Q]) {
+  Moments<V> m;
+  const V z = V(0.0);
   m.rho = f[0];
-  m.jx = m.jy = m.jz = Real(0);
-  m.sxx = m.syy = m.szz = m.sxy = m.sxz = m.syz = Real(0);
+  m.jx = m.jy = m.jz = z;
+  m.sxx = m.syy = m.szz = m.sxy = m.sxz = m.syz = z;
   static_for<0, NPAIR>([&](auto P_) {
     constexpr int P = decltype(P_)::value;
     using C = Pair<P>;
-    const Real s = f[2 * P + 1] + f[2 * P + 2];
-    const Real df = f[2 * P + 1] - f[2 * P + 2];
-    m.rho += s;
-    if constexpr (C::x != 0) m.jx += Real(C::x) * df;
-    if constexpr (C::y != 0) m.jy += Real(C::y) * df;
-    if constexpr (C::z != 0) m.jz += Real(C::z) * df;
-    if constexpr (C::x != 0) m.sxx += Real(C::x * C::x) * s;
-    if constexpr (C::y != 0) m.syy += Real(C::y * C::y) * s;
-    if constexpr (C::z != 0) m.szz += Real(C::z * C::z) * s;
-    if constexpr (C::x * C::y != 0) m.sxy += Real(C::x * C::y) * s;
-    if constexpr (C::x * C::z != 0) m.sxz += Real(C::x * C::z) * s;
-    if constexpr (C::y * C::z != 0) m.syz += Real(C::y * C::z) * s;
+    const V s = f[2 * P + 1] + f[2 * P + 2];
+    const V df = f[2 * P + 1] - f[2 * P + 2];
+    m.rho = m.rho + s;
+    m.jx = mac<C::x>(m.jx, df);
+    m.jy = mac<C::y>(m.jy, df);
+    m.jz = mac<C::z>(m.jz, df);
+    m.sxx = mac<C::x * C::x>(m.sxx, s);
+    m.syy = mac<C::y * C::y>(m.syy, s);
+    m.szz = mac<C::z * C::z>(m.szz, s);
+    m.sxy = mac<C::x * C::y>(m.sxy, s);
+    m.sxz = mac<C::x * C::z>(m.sxz, s);
+    m.syz = mac<C::y * C::z>(m.syz, s);
   });
   return m;
 }
 
-// Geometry of one node, read for the metric kind K.
-template <typename Real, int K>
+// Geometry of one node, read for the metric kind K. The Christoffel symbols
+// are kept with a minus sign (F^i = F_ext^i - Gamma^i_jk c^j c^k).
+template <typename V, int K>
 struct NodeGeo {
-  Real dtt = Real(0), dpp = Real(0);
-  Real g_rtt = Real(0), g_rpp = Real(0), g_trt = Real(0), g_prp = Real(0), g_ttp = Real(0),
-       g_ptt = Real(0);
-  Real fth = Real(1);
-
-  __device__ __forceinline__ void load(const GeoDev<Real>& g, int row) {
-    fth = __ldg(g.fth + row);
-    if constexpr (K == KCYL || K == KELL) {
-      dtt = __ldg(g.dtt + row);
-      g_rtt = __ldg(g.g_rtt + row);
-      g_trt = __ldg(g.g_trt + row);
-    }
-    if constexpr (K == KELL) {
-      dpp = __ldg(g.dpp + row);
-      g_rpp = __ldg(g.g_rpp + row);
-      g_prp = __ldg(g.g_prp + row);
-      g_ttp = __ldg(g.g_ttp + row);
-      g_ptt = __ldg(g.g_ptt + row);
-    }
-  }
+  V dtt = V(0.0), dpp = V(0.0);
+  V n_rtt = V(0.0), n_rpp = V(0.0), n_trt = V(0.0), n_prp = V(0.0), n_ttp = V(0.0), n_ptt = V(0.0);
+  V fth = V(1.0);
 };
+
+template <typename Real, int K>
+__device__ __forceinline__ NodeGeo<Real, K> load_geo(const GeoDev<Real>& g, int row) {
+  NodeGeo<Real, K> n;
+  n.fth = __ldg(g.fth + row);
+  if constexpr (K == KCYL || K == KELL) {
+    n.dtt = __ldg(g.dtt + row);
+    n.n_rtt = -__ldg(g.g_rtt + row);
+    n.n_trt = -__ldg(g.g_trt + row);
+  }
+  if constexpr (K == KELL) {
+    n.dpp = __ldg(g.dpp + row);
+    n.n_rpp = -__ldg(g.g_rpp + row);
+    n.n_prp = -__ldg(g.g_prp + row);
+    n.n_ttp = -__ldg(g.g_ttp + row);
+    n.n_ptt = -__ldg(g.g_ptt + row);
+  }
+  return n;
+}
+
+// two nodes' rows into the lanes of a PF2 geometry
+template <int K>
+__device__ __forceinline__ NodeGeo<PF2, K> load_geo2(const GeoDev<float>& g, int row0, int row1) {
+  const NodeGeo<float, K> a = load_geo<float, K>(g, row0);
+  const NodeGeo<float, K> b = row1 == row0 ? a : load_geo<float, K>(g, row1);
+  NodeGeo<PF2, K> n;
+  n.dtt = PF2(a.dtt, b.dtt);
+  n.dpp = PF2(a.dpp, b.dpp);
+  n.n_rtt = PF2(a.n_rtt, b.n_rtt);
+  n.n_rpp = PF2(a.n_rpp, b.n_rpp);
+  n.n_trt = PF2(a.n_trt, b.n_trt);
+  n.n_prp = PF2(a.n_prp, b.n_prp);
+  n.n_ttp = PF2(a.n_ttp, b.n_ttp);
+  n.n_ptt = PF2(a.n_ptt, b.n_ptt);
+  n.fth = PF2(a.fth, b.fth);
+  return n;
+}
 
 // Per-node coefficients of the equilibrium and of the forcing term.
 //   f^eq(+-c) = w (E +- O), forcing(+-c) = w (Fe +- Fo), with
@@ -305,167 +382,186 @@ struct NodeGeo {
 //   A2 = a2 + kappa Pi,  Pi = sum c c f - rho (cs^2 g^-1 + u u)
 //   (sum c c f^eq = rho cs^2 g^ij + rho u^i u^j by the lattice's 4th-moment
 //   identity), A2s = A2 / cs^4, F^i = F_ext^i - Gamma^i_jk c^j c^k.
-template <typename Real>
+// Stored with signs chosen so that every term is one multiply-add:
+// nv = -Vs, nfB = -fB, na = -A2s, and eAt = eA Delta^thth etc.
+template <typename V>
 struct Coef {
-  Real rho, ux, uy, uz;
-  Real e0, eA, eB, oA, oC;
-  Real vx, vy, vz;  // Vs = V / (2 cs^4)
-  Real fA, fB, t0;
-  Real axx, ayy, azz, axy, axz, ayz;  // A2s
-  Real fext_t;                         // F^theta_ext
+  V ux, uy, uz;
+  V e0, eB, oA, oC;
+  V eAt, eAp, eBt, eBp;     // eA dtt, eA dpp, eB dtt, eB dpp
+  V nvx, nvy, nvz;
+  V fA, nfB, t0;
+  V naxx, nayy, nazz, naxy, naxz, nayz;
+  V fext_t;
 };
 
-template <typename Real, int K>
-__device__ __forceinline__ Coef<Real> coefficients(const Moments<Real>& m, const NodeGeo<Real, K>& g,
-                                                   Real kappa, Real G) {
-  constexpr Real cs2 = Real(CS2);
-  constexpr Real inv_cs2 = Real(1.0 / CS2);
-  constexpr Real inv_cs4 = Real(1.0 / (CS2 * CS2));
-  Coef<Real> c;
-  const Real rho = m.rho;
-  const Real irho = Real(1) / rho;
-  const Real ux = m.jx * irho, uy = m.jy * irho, uz = m.jz * irho;
-  c.rho = rho;
+template <typename V, int K>
+__device__ __forceinline__ Coef<V> coefficients(const Moments<V>& m, const NodeGeo<V, K>& g, const V& kappa,
+                                                const V& G) {
+  const V cs2 = V(CS2);
+  const V inv_cs2 = V(1.0 / CS2);
+  const V inv_cs4 = V(1.0 / (CS2 * CS2));
+  Coef<V> c;
+  const V rho = m.rho;
+  const V irho = rcpv(rho);
+  const V ux = m.jx * irho, uy = m.jy * irho, uz = m.jz * irho;
   c.ux = ux;
   c.uy = uy;
   c.uz = uz;
-  const Real uu = ux * ux + uy * uy + uz * uz;
-  const Real trD = g.dtt + g.dpp;
-  const Real tra2 = rho * (cs2 * trD + uu);
-  c.e0 = rho - Real(0.5) * inv_cs2 * tra2;
-  c.eA = rho * Real(0.5 * (1.0 / CS2));
-  c.eB = rho * Real(0.5 / (CS2 * CS2));
+  const V uu = fmav(uz, uz, fmav(uy, uy, ux * ux));
+  const V trD = g.dtt + g.dpp;
+  const V tra2 = rho * fmav(cs2, trD, uu);
+  c.e0 = fmav(V(-0.5 / CS2), tra2, rho);
+  const V eA = rho * V(0.5 / CS2);
+  c.eB = rho * V(0.5 / (CS2 * CS2));
+  c.eAt = eA * g.dtt;
+  c.eAp = eA * g.dpp;
+  c.eBt = c.eB * g.dtt;
+  c.eBp = c.eB * g.dpp;
   c.oA = rho * inv_cs2;
-  c.oC = rho * Real(1.0 / (6.0 * CS2 * CS2 * CS2));
-  // V / (2 cs^4), Delta diagonal (dtt on theta, dpp on x3)
-  const Real vs = Real(0.5 / (CS2 * CS2)) * rho;
-  c.vx = vs * (cs2 * (trD * ux) + uu * ux);
-  c.vy = vs * (cs2 * (trD * uy + Real(2) * g.dtt * uy) + uu * uy);
-  c.vz = vs * (cs2 * (trD * uz + Real(2) * g.dpp * uz) + uu * uz);
+  c.oC = rho * V(1.0 / (6.0 * CS2 * CS2 * CS2));
+  // -V / (2 cs^4), Delta diagonal (dtt on theta, dpp on x3)
+  const V nvs = V(-0.5 / (CS2 * CS2)) * rho;
+  const V trDc = cs2 * trD;
+  c.nvx = nvs * (fmav(trDc, ux, uu * ux));
+  c.nvy = nvs * (fmav(fmav(V(2.0 * CS2), g.dtt, trDc), uy, uu * uy));
+  c.nvz = nvs * (fmav(fmav(V(2.0 * CS2), g.dpp, trDc), uz, uu * uz));
   c.fA = rho * inv_cs4;
-  c.fB = rho * inv_cs2;
+  c.nfB = rho * V(-1.0 / CS2);
   // A2 = (1 - kappa) rho (cs^2 Delta + u u) + kappa (S - rho cs^2 delta)
-  const Real k1 = Real(1) - kappa;
-  const Real rc = rho * cs2;
-  Real axx = k1 * (rho * ux * ux) + kappa * (m.sxx - rc);
-  Real ayy = k1 * (rho * (cs2 * g.dtt + uy * uy)) + kappa * (m.syy - rc);
-  Real azz = k1 * (rho * (cs2 * g.dpp + uz * uz)) + kappa * (m.szz - rc);
-  Real axy = k1 * (rho * ux * uy) + kappa * m.sxy;
-  Real axz = k1 * (rho * ux * uz) + kappa * m.sxz;
-  Real ayz = k1 * (rho * uy * uz) + kappa * m.syz;
-  const Real trA2 = axx + ayy + azz;
-  c.t0 = c.fB - Real(0.5) * inv_cs4 * trA2;
-  c.axx = axx * inv_cs4;
-  c.ayy = ayy * inv_cs4;
-  c.azz = azz * inv_cs4;
-  c.axy = axy * inv_cs4;
-  c.axz = axz * inv_cs4;
-  c.ayz = ayz * inv_cs4;
+  const V k1 = V(1.0) - kappa;
+  const V rc = rho * cs2;
+  const V rk = rho * k1;
+  const V axx = fmav(rk, ux * ux, kappa * (m.sxx - rc));
+  const V ayy = fmav(rk, fmav(cs2, g.dtt, uy * uy), kappa * (m.syy - rc));
+  const V azz = fmav(rk, fmav(cs2, g.dpp, uz * uz), kappa * (m.szz - rc));
+  const V axy = fmav(rk, ux * uy, kappa * m.sxy);
+  const V axz = fmav(rk, ux * uz, kappa * m.sxz);
+  const V ayz = fmav(rk, uy * uz, kappa * m.syz);
+  const V trA2 = axx + ayy + azz;
+  c.t0 = fmav(V(-0.5 / (CS2 * CS2)), trA2, rho * inv_cs2);
+  const V nic4 = V(-1.0 / (CS2 * CS2));
+  c.naxx = axx * nic4;
+  c.nayy = ayy * nic4;
+  c.nazz = azz * nic4;
+  c.naxy = axy * nic4;
+  c.naxz = axz * nic4;
+  c.nayz = ayz * nic4;
   c.fext_t = G * g.fth;
   return c;
 }
 
-// BGK collision with the forcing term for the pair (c, -c), in place.
-template <typename Real, int K, int P>
-__device__ __forceinline__ void collide_pair(Real& fp, Real& fm, const Coef<Real>& k,
-                                             const NodeGeo<Real, K>& g, Real omega) {
+// BGK collision with the forcing term for the pair (c, -c), in place:
+//   f* = (1 - omega) f + omega f^eq + F
+//      = (1 - omega) f + w (omega E + Fe) +- w (omega O + Fo)
+template <typename V, int K, int P>
+__device__ __forceinline__ void collide_pair(V& fp, V& fm, const Coef<V>& k, const NodeGeo<V, K>& g,
+                                             const V& omega, const V& om1) {
   using C = Pair<P>;
   constexpr int cx = C::x, cy = C::y, cz = C::z;
-  constexpr Real w = Real(C::w);
-  constexpr Real half_inv_cs2 = Real(0.5 / CS2);
-  // u.c and c.Delta.c
-  Real uc = Real(0);
-  if constexpr (cx != 0) uc += Real(cx) * k.ux;
-  if constexpr (cy != 0) uc += Real(cy) * k.uy;
-  if constexpr (cz != 0) uc += Real(cz) * k.uz;
-  Real cDc = Real(0);
-  if constexpr (cy != 0) cDc += Real(cy * cy) * g.dtt;
-  if constexpr (cz != 0 && K == KELL) cDc += Real(cz * cz) * g.dpp;
-  Real vc = Real(0);
-  if constexpr (cx != 0) vc += Real(cx) * k.vx;
-  if constexpr (cy != 0) vc += Real(cy) * k.vy;
-  if constexpr (cz != 0) vc += Real(cz) * k.vz;
-  const Real uc2 = uc * uc;
-  const Real E = k.e0 + k.eA * cDc + k.eB * uc2;
-  const Real O = uc * (k.oA + k.eB * cDc + k.oC * uc2) - vc;
-  // F = F_ext - Gamma(c, c) (even in c)
-  Real Fr = Real(0), Ft = k.fext_t, Fz = Real(0);
-  if constexpr (K == KCYL || K == KELL) {
-    if constexpr (cy != 0) Fr -= Real(cy * cy) * g.g_rtt;
-    if constexpr (cx * cy != 0) Ft -= Real(2 * cx * cy) * g.g_trt;
+  constexpr bool curv = K != KFLAT;
+  constexpr bool ell = K == KELL;
+  const V uc = dot3<cx, cy, cz>(k.ux, k.uy, k.uz);
+  const V uc2 = uc * uc;
+  V E = fmav(k.eB, uc2, k.e0);
+  V X = fmav(k.oC, uc2, k.oA);
+  if constexpr (curv && cy != 0) {
+    E = mac<cy * cy>(E, k.eAt);
+    X = mac<cy * cy>(X, k.eBt);
   }
-  if constexpr (K == KELL) {
-    if constexpr (cz != 0) Fr -= Real(cz * cz) * g.g_rpp;
-    if constexpr (cy * cz != 0) Ft -= Real(2 * cy * cz) * g.g_ttp;
-    if constexpr (cx * cz != 0) Fz -= Real(2 * cx * cz) * g.g_prp;
-    if constexpr (cy != 0) Fz -= Real(cy * cy) * g.g_ptt;
+  if constexpr (ell && cz != 0) {
+    E = mac<cz * cz>(E, k.eAp);
+    X = mac<cz * cz>(X, k.eBp);
   }
-  Real Fc = Real(cy) * Ft;
-  if constexpr (cx != 0) Fc += Real(cx) * Fr;
-  if constexpr (cz != 0) Fc += Real(cz) * Fz;
-  Real uF = k.ux * Fr + k.uy * Ft;
-  if constexpr (K == KELL) uF += k.uz * Fz;
-  // A2s c
-  Real ax = Real(0), ay = Real(0), az = Real(0);
-  if constexpr (cx != 0) { ax += Real(cx) * k.axx; ay += Real(cx) * k.axy; az += Real(cx) * k.axz; }
-  if constexpr (cy != 0) { ax += Real(cy) * k.axy; ay += Real(cy) * k.ayy; az += Real(cy) * k.ayz; }
-  if constexpr (cz != 0) { ax += Real(cz) * k.axz; ay += Real(cz) * k.ayz; az += Real(cz) * k.azz; }
-  Real cAc = Real(0);
-  if constexpr (cx != 0) cAc += Real(cx) * ax;
-  if constexpr (cy != 0) cAc += Real(cy) * ay;
-  if constexpr (cz != 0) cAc += Real(cz) * az;
-  Real FAc = Fr * ax + Ft * ay;
-  if constexpr (K == KELL) FAc += Fz * az;
-  const Real Fe = k.fA * uc * Fc - k.fB * uF;
-  const Real Fo = Fc * (k.t0 + half_inv_cs2 * cAc) - FAc;
-  // BGK: f* = f + omega (f^eq - f) + forcing
-  const Real eqp = w * (E + O), eqm = w * (E - O);
-  const Real frp = w * (Fe + Fo), frm = w * (Fe - Fo);
-  fp = fp + omega * (eqp - fp) + frp;
-  fm = fm + omega * (eqm - fm) + frm;
+  const V O = fmav(uc, X, dot3<cx, cy, cz>(k.nvx, k.nvy, k.nvz));
+  // F = F_ext - Gamma(c, c), even in c; which components exist is known here
+  constexpr bool hasFr = curv && (cy != 0 || (ell && cz != 0));
+  constexpr bool hasFz = ell && (cx * cz != 0 || cy != 0);
+  V Fr = V(0.0), Fz = V(0.0);
+  if constexpr (curv && cy != 0) Fr = mulc<cy * cy>(g.n_rtt);
+  if constexpr (ell && cz != 0) Fr = (cy != 0) ? mac<cz * cz>(Fr, g.n_rpp) : mulc<cz * cz>(g.n_rpp);
+  V Ft = k.fext_t;
+  if constexpr (curv && cx * cy != 0) Ft = mac<2 * cx * cy>(Ft, g.n_trt);
+  if constexpr (ell && cy * cz != 0) Ft = mac<2 * cy * cz>(Ft, g.n_ttp);
+  if constexpr (ell && cx * cz != 0) Fz = mulc<2 * cx * cz>(g.n_prp);
+  if constexpr (ell && cy != 0) Fz = (cx * cz != 0) ? mac<cy * cy>(Fz, g.n_ptt) : mulc<cy * cy>(g.n_ptt);
+  // F.c and u.F
+  constexpr bool hasFc = cy != 0 || (cx != 0 && hasFr) || (cz != 0 && hasFz);
+  V Fc = V(0.0);
+  if constexpr (hasFc) {
+    constexpr int ax_ = hasFr ? cx : 0, az_ = hasFz ? cz : 0;
+    Fc = dot3<ax_, cy, az_>(Fr, Ft, Fz);
+  }
+  V uF = k.uy * Ft;
+  if constexpr (hasFr) uF = fmav(k.ux, Fr, uF);
+  if constexpr (hasFz) uF = fmav(k.uz, Fz, uF);
+  // -A2s c, its quadratic form, and F.(-A2s c)
+  const V nax = dot3<cx, cy, cz>(k.naxx, k.naxy, k.naxz);
+  const V nay = dot3<cx, cy, cz>(k.naxy, k.nayy, k.nayz);
+  const V naz = dot3<cx, cy, cz>(k.naxz, k.nayz, k.nazz);
+  V FnA = Ft * nay;
+  if constexpr (hasFr) FnA = fmav(Fr, nax, FnA);
+  if constexpr (hasFz) FnA = fmav(Fz, naz, FnA);
+  // Fe = fA uc Fc - fB uF,  Fo = Fc (t0 + cAc / (2 cs^2)) - F.A2s c
+  V Fe = k.nfB * uF;
+  V Fo = FnA;
+  if constexpr (hasFc) {
+    Fe = fmav(k.fA * uc, Fc, Fe);
+    const V ncAc = dot3<cx, cy, cz>(nax, nay, naz);
+    Fo = fmav(Fc, fmav(V(-0.5 / CS2), ncAc, k.t0), FnA);
+  }
+  const V w = V(C::w);
+  const V A = fmav(omega, E, Fe) * w;
+  const V B = fmav(omega, O, Fo) * w;
+  fp = fmav(om1, fp, A + B);
+  fm = fmav(om1, fm, A - B);
 }
 
-template <typename Real, int K>
-__device__ __forceinline__ void collide(Real (&f)[Q], const Coef<Real>& k, const NodeGeo<Real, K>& g,
-                                        Real omega) {
-  constexpr Real w0 = Real(W_REST);
+template <typename V, int K>
+__device__ __forceinline__ void collide(V (&f)[Q], const Coef<V>& k, const NodeGeo<V, K>& g, const V& omega) {
+  const V om1 = V(1.0) - omega;
   // rest velocity: f^eq = w0 e0, forcing = -w0 fB (u . F_ext)
-  const Real eq0 = w0 * k.e0;
-  const Real fr0 = -w0 * k.fB * (k.uy * k.fext_t);
-  f[0] = f[0] + omega * (eq0 - f[0]) + fr0;
+  f[0] = fmav(om1, f[0], fmav(omega, k.e0, k.nfB * (k.uy * k.fext_t)) * V(W_REST));
   static_for<0, NPAIR>([&](auto P_) {
     constexpr int P = decltype(P_)::value;
-    collide_pair<Real, K, P>(f[2 * P + 1], f[2 * P + 2], k, g, omega);
+    collide_pair<V, K, P>(f[2 * P + 1], f[2 * P + 2], k, g, omega, om1);
   });
 }
 
 // f^eq(rho, u) for all 41 velocities (initial state, Sec. II).
-template <typename Real, int K>
-__device__ __forceinline__ void equilibrium(Real rho, Real ux, Real uy, Real uz,
-                                            const NodeGeo<Real, K>& g, Real (&f)[Q]) {
-  Moments<Real> m;
+template <typename V, int K>
+__device__ __forceinline__ void equilibrium(const V& rho, const V& ux, const V& uy, const V& uz,
+                                            const NodeGeo<V, K>& g, V (&f)[Q]) {
+  Moments<V> m;
   m.rho = rho;
   m.jx = rho * ux;
   m.jy = rho * uy;
   m.jz = rho * uz;
-  // kappa = 0: the second moment is not used
-  m.sxx = m.syy = m.szz = m.sxy = m.sxz = m.syz = Real(0);
-  Coef<Real> k = coefficients<Real, K>(m, g, Real(0), Real(0));
+  m.sxx = m.syy = m.szz = m.sxy = m.sxz = m.syz = V(0.0);  // unused with kappa = 0
+  Coef<V> k = coefficients<V, K>(m, g, V(0.0), V(0.0));
   k.ux = ux;
   k.uy = uy;
   k.uz = uz;
-  f[0] = Real(W_REST) * k.e0;
+  f[0] = k.e0 * V(W_REST);
   static_for<0, NPAIR>([&](auto P_) {
     constexpr int P = decltype(P_)::value;
     using C = Pair<P>;
-    constexpr Real w = Real(C::w);
-    Real uc = Real(C::x) * ux + Real(C::y) * uy + Real(C::z) * uz;
-    Real cDc = Real(C::y * C::y) * g.dtt + Real(C::z * C::z) * g.dpp;
-    Real vc = Real(C::x) * k.vx + Real(C::y) * k.vy + Real(C::z) * k.vz;
-    const Real E = k.e0 + k.eA * cDc + k.eB * uc * uc;
-    const Real O = uc * (k.oA + k.eB * cDc + k.oC * uc * uc) - vc;
-    f[2 * P + 1] = w * (E + O);
-    f[2 * P + 2] = w * (E - O);
+    constexpr int cx = C::x, cy = C::y, cz = C::z;
+    const V uc = dot3<cx, cy, cz>(ux, uy, uz);
+    const V uc2 = uc * uc;
+    V E = fmav(k.eB, uc2, k.e0);
+    V X = fmav(k.oC, uc2, k.oA);
+    if constexpr (cy != 0) {
+      E = mac<cy * cy>(E, k.eAt);
+      X = mac<cy * cy>(X, k.eBt);
+    }
+    if constexpr (cz != 0) {
+      E = mac<cz * cz>(E, k.eAp);
+      X = mac<cz * cz>(X, k.eBp);
+    }
+    const V O = fmav(uc, X, dot3<cx, cy, cz>(k.nvx, k.nvy, k.nvz));
+    f[2 * P + 1] = (E + O) * V(C::w);
+    f[2 * P + 2] = (E - O) * V(C::w);
   });
 }
 

@@ -6,8 +6,8 @@
 // (i_r - c_r, i_theta - c_theta) of population l, all x3 -- the x3 shift and
 // its periodic wrap are applied when reading shared memory, so every TMA box
 // starts at x3 = 0 (16-byte aligned) and no halo is needed. One thread per
-// node; thread 0 issues the 41 box loads of the tile two ahead into the stage
-// the CTA has just finished reading, so the copies overlap the collision.
+// node; warp 0 issues the 41 box loads of the tile two ahead into the stage
+// every warp has finished reading, so the copies overlap the collision.
 // Rows within 3 nodes of an r-wall, and nodes near x3-walls, gather from
 // global memory with the folded bounce-back path instead.
 //
@@ -79,45 +79,63 @@ __device__ __forceinline__ TileRow tile_row(int tile, const Dims& d) {
   return tr;
 }
 
-// 41 box loads of one tile into a stage; the barrier expects all their bytes.
-template <int NX>
-__device__ __forceinline__ void issue_tile(const CUtensorMap* map, float* stage, uint64_t* bar, int tile,
-                                           const Dims& d) {
-  const TileRow tr = tile_row(tile, d);
-  mbar_expect_tx(bar, uint32_t(Q * NX * sizeof(float)));
-  tma_load_row(stage, map, bar, 0, tr.it, tr.ir, tr.b * Q);
-  static_for<0, NPAIR>([&](auto P_) {
-    constexpr int P = decltype(P_)::value;
-    using C = Pair<P>;
-    // population +c comes from row (i_r - c_r, i_theta - c_theta), -c from (+c_r, +c_theta);
-    // rows outside [0, nr) are zero-filled by the TMA unit and never read
-    tma_load_row(stage + (2 * P + 1) * NX, map, bar, 0, wrap_small(tr.it - C::y, d.nt), tr.ir - C::x,
-                 tr.b * Q + 2 * P + 1);
-    tma_load_row(stage + (2 * P + 2) * NX, map, bar, 0, wrap_small(tr.it + C::y, d.nt), tr.ir + C::x,
-                 tr.b * Q + 2 * P + 2);
-  });
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
 
+// The 41 box loads of one tile into a stage, issued by the lanes of one warp
+// (population l by lane l % 32); the barrier expects all their bytes.
+// Population l comes from row (i_r - c_r, i_theta - c_theta); rows outside
+// [0, nr) are zero-filled by the TMA unit and never read.
+template <int NX>
+__device__ __forceinline__ void issue_tile(const CUtensorMap* map, float* stage, uint64_t* bar, int tile,
+                                           const Dims& d, const int4* vel, int lane) {
+  const TileRow tr = tile_row(tile, d);
+  if (lane == 0) mbar_expect_tx(bar, uint32_t(Q * NX * sizeof(float)));
+  __syncwarp();
+  for (int l = lane; l < Q; l += 32) {
+    const int4 c = vel[l];
+    tma_load_row(stage + l * NX, map, bar, 0, wrap_small(tr.it - c.y, d.nt), tr.ir - c.x, tr.b * Q + l);
+  }
+}
+
+// Warps of a CTA run decoupled: each waits for the stage's data (full
+// barrier), gathers from it, and signals it has finished reading (empty
+// barrier, one arrival per warp). Warp 0 refills a stage once every warp has
+// read it; no CTA-wide barrier is taken inside the tile loop.
 template <int K, int NX>
 __global__ void __launch_bounds__(NX, 512 / NX) k_step_tma(const __grid_constant__ CUtensorMap map,
                                                  const float* __restrict__ fin, float* __restrict__ fout,
                                                  GeoDev<float> geo, const InstParams<float>* __restrict__ inst,
                                                  Dims d, int* __restrict__ flag) {
+  constexpr int NW = NX / 32;
   extern __shared__ __align__(1024) unsigned char smem[];
   float* stages = reinterpret_cast<float*>(smem);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + 2 * Q * NX * sizeof(float));
-  const int x = threadIdx.x;
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + 2 * Q * NX * sizeof(float));
+  uint64_t* empty = full + 2;
+  int4* vel = reinterpret_cast<int4*>(full + 4);
+  const int x = threadIdx.x, lane = x & 31, warp = x >> 5;
   const int ntiles = d.batch * d.nr * d.nt;
   const int G = gridDim.x;
+  if (x == 0) vel[0] = make_int4(0, 0, 0, 0);
+  static_for<0, NPAIR>([&](auto P_) {
+    constexpr int P = decltype(P_)::value;
+    using C = Pair<P>;
+    if (x == 2 * P + 1) vel[x] = make_int4(C::x, C::y, C::z, 0);
+    if (x == 2 * P + 2) vel[x] = make_int4(-C::x, -C::y, -C::z, 0);
+  });
   if (x == 0) {
-    mbar_init(&bars[0], 1);
-    mbar_init(&bars[1], 1);
+    mbar_init(&full[0], 1);
+    mbar_init(&full[1], 1);
+    mbar_init(&empty[0], NW);
+    mbar_init(&empty[1], NW);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
-  if (x == 0) {
-    if (int(blockIdx.x) < ntiles) issue_tile<NX>(&map, stages, &bars[0], blockIdx.x, d);
-    if (int(blockIdx.x) + G < ntiles) issue_tile<NX>(&map, stages + Q * NX, &bars[1], blockIdx.x + G, d);
+  if (warp == 0) {
+    if (int(blockIdx.x) < ntiles) issue_tile<NX>(&map, stages, &full[0], blockIdx.x, d, vel, lane);
+    if (int(blockIdx.x) + G < ntiles)
+      issue_tile<NX>(&map, stages + Q * NX, &full[1], blockIdx.x + G, d, vel, lane);
   }
   // x3 index of the source of a shift c3 (periodic wrap; NX = n3 is a power of two)
   int xs[7];
@@ -127,14 +145,11 @@ __global__ void __launch_bounds__(NX, 512 / NX) k_step_tma(const __grid_constant
   int k = 0;
   for (int tile = blockIdx.x; tile < ntiles; tile += G, ++k) {
     const int s = k & 1;
-    const bool ok = mbar_wait_bounded(&bars[s], uint32_t((k >> 1) & 1));
-    if (__syncthreads_or(!ok)) {
-      if (x == 0) {
-        atomicOr(flag, 2);
-        // copies may still be in flight into either stage: wait for them (bounded)
-        mbar_wait_bounded(&bars[s], uint32_t((k >> 1) & 1));
-        if (tile + G < ntiles) mbar_wait_bounded(&bars[s ^ 1], uint32_t(((k + 1) >> 1) & 1));
-      }
+    const uint32_t par = uint32_t((k >> 1) & 1);
+    if (!mbar_wait_bounded(&full[s], par)) {
+      if (lane == 0) atomicOr(flag, 2);
+      if (warp == 0 && lane == 0 && tile + G < ntiles)  // copies into the other stage may be in flight
+        mbar_wait_bounded(&full[s ^ 1], uint32_t(((k + 1) >> 1) & 1));
       return;
     }
     const TileRow tr = tile_row(tile, d);
@@ -159,18 +174,25 @@ __global__ void __launch_bounds__(NX, 512 / NX) k_step_tma(const __grid_constant
       f[0] = __ldg(fb + p.cell);
       gather_wall(fb, p, d, f);
     }
-    __syncthreads();  // every read of stage s is done: refill it
-    if (x == 0 && tile + 2 * G < ntiles) {
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[s]);
+    if (warp == 0 && tile + 2 * G < ntiles) {
+      if (!mbar_wait_bounded(&empty[s], par)) {
+        if (lane == 0) {
+          atomicOr(flag, 2);
+          if (tile + G < ntiles) mbar_wait_bounded(&full[s ^ 1], uint32_t(((k + 1) >> 1) & 1));
+        }
+        return;
+      }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      issue_tile<NX>(&map, stages + s * Q * NX, &bars[s], tile + 2 * G, d);
+      issue_tile<NX>(&map, stages + s * Q * NX, &full[s], tile + 2 * G, d, vel, lane);
     }
     const Moments<float> m = moments(f);
-    if (!(fabsf(m.rho) < 1e30f)) {
+    if (!finite_v(m.rho)) {
       if (*flag == 0) atomicOr(flag, 1);
     }
-    NodeGeo<float, K> g;
     const int row = K == KELL ? p.ir * d.geo_rows3 + p.i3 : p.ir;
-    g.load(geo, row);
+    const NodeGeo<float, K> g = load_geo<float, K>(geo, row);
     const InstParams<float> ip = inst[p.b];
     const Coef<float> kc = coefficients<float, K>(m, g, ip.kappa, ip.G);
     collide<float, K>(f, kc, g, ip.omega);
@@ -183,7 +205,7 @@ __global__ void __launch_bounds__(NX, 512 / NX) k_step_tma(const __grid_constant
 template <int NX>
 cudaError_t launch_nx(int K, const void* map, const float* fin, float* fout, const GeoDev<float>& geo,
                       const InstParams<float>* inst, const Dims& d, int* flag, cudaStream_t s) {
-  const size_t smem = 2 * Q * NX * sizeof(float) + 64;
+  const size_t smem = 2 * Q * NX * sizeof(float) + 4 * sizeof(uint64_t) + Q * sizeof(int4);
   static int configured[3] = {0, 0, 0};
   static int blocks_per_sm[3] = {1, 1, 1};
   static int sms = 0;
