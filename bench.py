@@ -31,10 +31,14 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-BYTES_PER_UPDATE = {"fp64": 2 * 41 * 8, "fp32": 2 * 41 * 4}
+BYTES_PER_UPDATE = {"fp64": 2 * 41 * 8, "fp32": 2 * 41 * 4, "fp16_shifted": 2 * 41 * 2,
+                    "bf16_shifted": 2 * 41 * 2}
+DTYPE = {"fp64": "f64", "fp32": "f32", "fp16_shifted": "f16 storage / f32 math",
+         "bf16_shifted": "bf16 storage / f32 math"}
 PROFILE_FILE = os.path.join(ROOT, "profiles", "k_step_fp32_cyl64x4x256_b24.md")
 KERNEL_SOURCES = ["paper_1411_3133_gb300/csrc/lbm_device.cuh", "paper_1411_3133_gb300/csrc/kernels.cuh",
-                  "paper_1411_3133_gb300/csrc/step_f32.cu", "paper_1411_3133_gb300/csrc/lattice.cuh"]
+                  "paper_1411_3133_gb300/csrc/step_launch.cuh", "paper_1411_3133_gb300/csrc/step_f32.cu",
+                  "paper_1411_3133_gb300/csrc/lattice.cuh"]
 METRIC = "MLUPS and % of HBM roofline at 1 GB300"
 
 
@@ -69,9 +73,9 @@ def peaks():
         return 6800.0, "fallback"
 
 
-def workload_desc():
+def workload_desc(precision="fp32"):
     from paper_1411_3133_gb300.workloads import cylinder_sweep
-    return cylinder_sweep()
+    return cylinder_sweep(precision=precision)
 
 
 # ---------------------------------------------------------------------------
@@ -196,6 +200,7 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--step-kernel", default="auto", choices=["auto", "plain", "tma"])
+    ap.add_argument("--precision", default="fp32", choices=sorted(BYTES_PER_UPDATE))
     args = ap.parse_args()
     assert args.warmup >= 3, "at least 3 warm-up steps"
 
@@ -219,7 +224,7 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
 
-    wl = workload_desc()
+    wl = workload_desc(args.precision)
     spec = L.ChannelSpec(**wl.geometry_kwargs())
     desc = spec.desc()
     params = []
@@ -265,7 +270,7 @@ def main():
     bpu = BYTES_PER_UPDATE[wl.precision]
     achieved = bpu * cells / per_launch / 1e9
     peak, peak_kind = peaks()
-    traffic = measured_traffic()
+    traffic = measured_traffic() if wl.precision == "fp32" else None
 
     # end to end through the C ABI with host buffers: each step uploads the
     # state from pinned host memory, advances it one step and reads it back
@@ -301,11 +306,11 @@ def main():
         line = {
             "metric": METRIC, "value": round(value, 2), "unit": "MLUPS", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 6),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": DTYPE[wl.precision], "data": "synthetic",
             "config": {"workload": f"Dean sweep, cylindrical channel {wl.nr}x{wl.ntheta}x{wl.n3}, "
                                    f"eta=0.975, {wl.batch} instances (12 De in 25..60 x tau 0.55/0.6), "
-                                   f"D3Q41, FP32",
+                                   f"D3Q41, {wl.precision}",
                        "cells_per_instance": wl.ncells, "instances": wl.batch,
                        "precision": wl.precision, "bytes_per_update": bpu,
                        "l2": f"inputs larger than L2: state {2 * nbytes / 1e6:.0f} MB, no flush",

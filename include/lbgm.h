@@ -64,8 +64,10 @@ typedef enum {
 typedef enum {
   LB_FP64 = 0,          /* populations and arithmetic in FP64 */
   LB_FP32 = 1,          /* populations and arithmetic in FP32 */
-  LB_FP16_SHIFTED = 2,  /* reserved: FP16 deviations, FP32 arithmetic */
-  LB_BF16_SHIFTED = 3   /* reserved: BF16 deviations, FP32 arithmetic */
+  LB_FP16_SHIFTED = 2,  /* populations stored in FP16 as the scaled deviation
+                           (f_l - w_l) / w_l from the rest state at rho' = 1;
+                           FP32 arithmetic */
+  LB_BF16_SHIFTED = 3   /* the same deviation stored in BF16; FP32 arithmetic */
 } lb_precision;
 
 /* Channel geometry (Sec. III lattice map; Sec. IV lattice map and the
@@ -207,7 +209,9 @@ lb_status lb_macros(lb_ctx* ctx, double* rho, double* u, int on_device);
 lb_status lb_diagnostics(lb_ctx* ctx, lb_diag* out);
 
 /* Populations of the state as FP64 in the documented layout, f[batch * LB_Q
- * * N]. For LB_FP32 the conversion is exact both ways. */
+ * * N]. The conversion is exact both ways for LB_FP32; for the reduced-
+ * precision formats a state read out and written back is unchanged (the
+ * stored deviations round-trip). */
 lb_status lb_get_populations(lb_ctx* ctx, double* f, int on_device);
 lb_status lb_set_populations(lb_ctx* ctx, const double* f, int on_device);
 

@@ -255,9 +255,18 @@ lb_status launch_step_once(lb_ctx* c) {
     e = launch_step_f64(c->K, static_cast<const double*>(c->f[src]), static_cast<double*>(c->f[dst]),
                         c->geo_d, static_cast<const InstParams<double>*>(c->inst), c->dims, c->flag,
                         c->block_threads, c->stream);
-  else
+  else if (c->prec == LB_FP32)
     e = launch_step_f32(c->K, static_cast<const float*>(c->f[src]), static_cast<float*>(c->f[dst]),
                         c->geo_f, static_cast<const InstParams<float>*>(c->inst), c->dims, c->flag,
+                        c->block_threads, c->stream);
+  else if (c->prec == LB_FP16_SHIFTED)
+    e = launch_step_h16(c->K, static_cast<const __half*>(c->f[src]), static_cast<__half*>(c->f[dst]),
+                        c->geo_f, static_cast<const InstParams<float>*>(c->inst), c->dims, c->flag,
+                        c->block_threads, c->stream);
+  else
+    e = launch_step_b16(c->K, static_cast<const __nv_bfloat16*>(c->f[src]),
+                        static_cast<__nv_bfloat16*>(c->f[dst]), c->geo_f,
+                        static_cast<const InstParams<float>*>(c->inst), c->dims, c->flag,
                         c->block_threads, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "step kernel launch");
   c->cur = dst;
@@ -346,8 +355,8 @@ lb_status lb_create_geometry(lb_metric metric, const lb_geometry_desc* geom, int
   const std::string v = validate_geometry(metric, *geom);
   if (!v.empty()) return fail(nullptr, LB_ERR_ARG, v);
   if (batch < 1) return fail(nullptr, LB_ERR_ARG, "need batch >= 1");
-  if (prec != LB_FP64 && prec != LB_FP32)
-    return fail(nullptr, LB_ERR_ARG, "precision not available in this build (FP64 and FP32 are)");
+  if (prec != LB_FP64 && prec != LB_FP32 && prec != LB_FP16_SHIFTED && prec != LB_BF16_SHIFTED)
+    return fail(nullptr, LB_ERR_ARG, "unknown precision");
   if (alloc && (!alloc->alloc || !alloc->free)) return fail(nullptr, LB_ERR_ARG, "allocator needs alloc and free");
   const double total = double(batch) * geom->nr * geom->ntheta * geom->n3;
   if (total >= 4294967295.0) return fail(nullptr, LB_ERR_ARG, "batch * nodes must fit in uint32");
@@ -404,14 +413,14 @@ lb_status lb_create_geometry(lb_metric metric, const lb_geometry_desc* geom, int
   d.div_nt = FastDiv::make(uint32_t(d.nt));
   c->ncell = size_t(d.ncell);
   c->state_elems = size_t(batch) * Q * c->ncell;
-  c->elem_bytes = prec == LB_FP64 ? 8 : 4;
+  c->elem_bytes = prec == LB_FP64 ? 8 : prec == LB_FP32 ? 4 : 2;
 
   const size_t nrows = size_t(geom->nr) * d.geo_rows3;
   const size_t nrow64 = size_t(geom->nr) * geom->n3;
   c->nblk = int(std::min<size_t>(1024, (c->ncell + 255) / 256));
   c->f[0] = dalloc(c, c->state_elems * c->elem_bytes);
   c->f[1] = dalloc(c, c->state_elems * c->elem_bytes);
-  c->geo_real = dalloc(c, 9 * nrows * c->elem_bytes);
+  c->geo_real = dalloc(c, 9 * nrows * (prec == LB_FP64 ? sizeof(double) : sizeof(float)));
   c->geo64 = static_cast<double*>(dalloc(c, nrow64 * 4 * sizeof(double)));
   c->sqrtg = static_cast<double*>(dalloc(c, nrow64 * sizeof(double)));
   c->base_uth = static_cast<double*>(dalloc(c, size_t(batch) * geom->nr * sizeof(double)));
@@ -441,7 +450,7 @@ lb_status lb_create_geometry(lb_metric metric, const lb_geometry_desc* geom, int
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(c->sqrtg, sg.data(), sg.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream);
   if (e == cudaSuccess) {
-    if (prec == LB_FP64) {
+    if (prec == LB_FP64) {  // FP64 tables for the FP64 path, FP32 for the others
       auto t = geo_host_tables<double>(c->host_geo, *geom, c->K);
       e = cudaMemcpyAsync(c->geo_real, t.data(), t.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream);
       if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
@@ -499,7 +508,7 @@ lb_status lb_init(lb_ctx* c, const lb_params* p) {
   LB_CUDA(c, cudaMemcpyAsync(c->ini, ini.data(), ini.size() * sizeof(InitInst), cudaMemcpyHostToDevice,
                              c->stream));
   c->cur = 0;
-  LB_CUDA(c, launch_init(c->prec == LB_FP64 ? 0 : 1, c->K, c->f[0], geo_ptr(c), c->sqrtg,
+  LB_CUDA(c, launch_init(int(c->prec), c->K, c->f[0], geo_ptr(c), c->sqrtg,
                          any_base ? c->base_uth : nullptr, c->ini, nullptr, nullptr, c->dims, c->stream));
   return reset_after_init(c);
 }
@@ -518,7 +527,7 @@ lb_status lb_init_fields(lb_ctx* c, const lb_params* p, const double* rho, const
     du = c->u_s;
   }
   c->cur = 0;
-  LB_CUDA(c, launch_init(c->prec == LB_FP64 ? 0 : 1, c->K, c->f[0], geo_ptr(c), c->sqrtg, nullptr, c->ini,
+  LB_CUDA(c, launch_init(int(c->prec), c->K, c->f[0], geo_ptr(c), c->sqrtg, nullptr, c->ini,
                          drho, du, c->dims, c->stream));
   return reset_after_init(c);
 }
@@ -574,7 +583,7 @@ lb_status lb_macros(lb_ctx* c, double* rho, double* u, int on_device) {
   const size_t n = size_t(c->batch) * c->ncell;
   double* drho = on_device ? rho : (rho ? c->rho_s : nullptr);
   double* du = on_device ? u : (u ? c->u_s : nullptr);
-  LB_CUDA(c, launch_macros(c->prec == LB_FP64 ? 0 : 1, c->K, c->f[c->cur], drho, du, c->dims, c->stream));
+  LB_CUDA(c, launch_macros(int(c->prec), c->K, c->f[c->cur], drho, du, c->dims, c->stream));
   if (!on_device) {
     if (rho) LB_CUDA(c, cudaMemcpyAsync(rho, c->rho_s, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     if (u) LB_CUDA(c, cudaMemcpyAsync(u, c->u_s, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
@@ -587,8 +596,7 @@ lb_status lb_diagnostics(lb_ctx* c, lb_diag* out) {
   lb_status s;
   if (!usable(c, &s)) return s;
   if (!out) return fail(c, LB_ERR_ARG, "null argument");
-  LB_CUDA(c, launch_macros(c->prec == LB_FP64 ? 0 : 1, c->K, c->f[c->cur], c->rho_s, c->u_s, c->dims,
-                           c->stream));
+  LB_CUDA(c, launch_macros(int(c->prec), c->K, c->f[c->cur], c->rho_s, c->u_s, c->dims, c->stream));
   LB_CUDA(c, launch_diag(c->rho_s, c->u_s, c->rowmean, c->geo64, c->dims, c->partial, c->nblk, c->diag_out,
                          c->stream));
   std::vector<double> h(size_t(c->batch) * DIAG_NQ);
@@ -632,7 +640,7 @@ lb_status lb_get_populations(lb_ctx* c, double* f, int on_device) {
       if (!c->dbl_stage) return fail(c, LB_ERR_CUDA, "staging allocation failed");
       dst = c->dbl_stage;
     }
-    LB_CUDA(c, launch_convert(1, 1, c->f[c->cur], dst, n, c->stream));
+    LB_CUDA(c, launch_convert(int(c->prec), 1, c->f[c->cur], dst, n, c->ncell, c->stream));
     if (!on_device)
       LB_CUDA(c, cudaMemcpyAsync(f, dst, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   }
@@ -656,7 +664,7 @@ lb_status lb_set_populations(lb_ctx* c, const double* f, int on_device) {
       LB_CUDA(c, cudaMemcpyAsync(c->dbl_stage, f, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
       src = c->dbl_stage;
     }
-    LB_CUDA(c, launch_convert(1, 0, c->f[0], const_cast<double*>(src), n, c->stream));
+    LB_CUDA(c, launch_convert(int(c->prec), 0, c->f[0], const_cast<double*>(src), n, c->ncell, c->stream));
   }
   const long long keep = c->step;
   lb_status s = reset_after_init(c);

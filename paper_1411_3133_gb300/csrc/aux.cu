@@ -13,40 +13,58 @@ uint32_t blocks_for(const Dims& d, int threads) {
   return (total + threads - 1) / threads;
 }
 
-template <typename Real>
-cudaError_t macros_t(int K, const Real* fin, double* rho, double* u, const Dims& d, cudaStream_t s) {
+template <typename S, typename Real>
+cudaError_t macros_t(int K, const S* fin, double* rho, double* u, const Dims& d, cudaStream_t s) {
   const uint32_t nb = blocks_for(d, 256);
   switch (K) {
-    case KFLAT: k_macros<Real, KFLAT><<<nb, 256, 0, s>>>(fin, rho, u, d); break;
-    case KCYL: k_macros<Real, KCYL><<<nb, 256, 0, s>>>(fin, rho, u, d); break;
-    case KELL: k_macros<Real, KELL><<<nb, 256, 0, s>>>(fin, rho, u, d); break;
+    case KFLAT: k_macros<S, Real, KFLAT><<<nb, 256, 0, s>>>(fin, rho, u, d); break;
+    case KCYL: k_macros<S, Real, KCYL><<<nb, 256, 0, s>>>(fin, rho, u, d); break;
+    case KELL: k_macros<S, Real, KELL><<<nb, 256, 0, s>>>(fin, rho, u, d); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
 }
 
-template <typename Real>
-cudaError_t init_t(int K, Real* f, const GeoDev<Real>& geo, const double* sqrtg, const double* base,
+template <typename S, typename Real>
+cudaError_t init_t(int K, S* f, const GeoDev<Real>& geo, const double* sqrtg, const double* base,
                    const InitInst* ini, const double* rho_in, const double* u_in, const Dims& d,
                    cudaStream_t s) {
   const uint32_t nb = blocks_for(d, 256);
   switch (K) {
-    case KFLAT: k_init<Real, KFLAT><<<nb, 256, 0, s>>>(f, geo, sqrtg, base, ini, rho_in, u_in, d); break;
-    case KCYL: k_init<Real, KCYL><<<nb, 256, 0, s>>>(f, geo, sqrtg, base, ini, rho_in, u_in, d); break;
-    case KELL: k_init<Real, KELL><<<nb, 256, 0, s>>>(f, geo, sqrtg, base, ini, rho_in, u_in, d); break;
+    case KFLAT: k_init<S, Real, KFLAT><<<nb, 256, 0, s>>>(f, geo, sqrtg, base, ini, rho_in, u_in, d); break;
+    case KCYL: k_init<S, Real, KCYL><<<nb, 256, 0, s>>>(f, geo, sqrtg, base, ini, rho_in, u_in, d); break;
+    case KELL: k_init<S, Real, KELL><<<nb, 256, 0, s>>>(f, geo, sqrtg, base, ini, rho_in, u_in, d); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
 }
 
-template <typename Real>
-__global__ void k_convert(Real* state, double* dbl, size_t n, int to_double) {
+// weights by population index, for the element-wise conversions
+__constant__ double c_weight[Q];
+
+__device__ __forceinline__ double to_f(double v, double) { return v; }
+__device__ __forceinline__ double to_f(float v, double) { return v; }
+__device__ __forceinline__ double to_f(__half v, double w) { return w * (1.0 + double(__half2float(v))); }
+__device__ __forceinline__ double to_f(__nv_bfloat16 v, double w) {
+  return w * (1.0 + double(__bfloat162float(v)));
+}
+__device__ __forceinline__ void from_f(double& o, double f, double) { o = f; }
+__device__ __forceinline__ void from_f(float& o, double f, double) { o = float(f); }
+__device__ __forceinline__ void from_f(__half& o, double f, double w) { o = __double2half(f / w - 1.0); }
+__device__ __forceinline__ void from_f(__nv_bfloat16& o, double f, double w) {
+  o = __double2bfloat16(f / w - 1.0);
+}
+
+// state (documented population layout) <-> FP64 populations
+template <typename S>
+__global__ void k_convert(S* state, double* dbl, size_t n, size_t ncell, int to_double) {
   for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n;
        i += size_t(gridDim.x) * blockDim.x) {
+    const double w = c_weight[(i / ncell) % Q];
     if (to_double)
-      dbl[i] = double(state[i]);
+      dbl[i] = to_f(state[i], w);
     else
-      state[i] = Real(dbl[i]);
+      from_f(state[i], dbl[i], w);
   }
 }
 
@@ -175,29 +193,55 @@ __global__ void __launch_bounds__(DIAG_THREADS)
 
 cudaError_t launch_macros(int prec, int K, const void* fin, double* rho, double* u, const Dims& d,
                           cudaStream_t s) {
-  if (prec == 0) return macros_t<double>(K, static_cast<const double*>(fin), rho, u, d, s);
-  return macros_t<float>(K, static_cast<const float*>(fin), rho, u, d, s);
+  switch (prec) {
+    case 0: return macros_t<double, double>(K, static_cast<const double*>(fin), rho, u, d, s);
+    case 1: return macros_t<float, float>(K, static_cast<const float*>(fin), rho, u, d, s);
+    case 2: return macros_t<__half, float>(K, static_cast<const __half*>(fin), rho, u, d, s);
+    case 3: return macros_t<__nv_bfloat16, float>(K, static_cast<const __nv_bfloat16*>(fin), rho, u, d, s);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 cudaError_t launch_init(int prec, int K, void* f, const void* geo, const double* sqrtg,
                         const double* base_uth, const InitInst* ini, const double* rho_in,
                         const double* u_in, const Dims& d, cudaStream_t s) {
-  if (prec == 0)
-    return init_t<double>(K, static_cast<double*>(f), *static_cast<const GeoDev<double>*>(geo), sqrtg,
-                          base_uth, ini, rho_in, u_in, d, s);
-  return init_t<float>(K, static_cast<float*>(f), *static_cast<const GeoDev<float>*>(geo), sqrtg,
-                       base_uth, ini, rho_in, u_in, d, s);
+  const GeoDev<float>& gf = *static_cast<const GeoDev<float>*>(geo);
+  switch (prec) {
+    case 0:
+      return init_t<double, double>(K, static_cast<double*>(f), *static_cast<const GeoDev<double>*>(geo),
+                                    sqrtg, base_uth, ini, rho_in, u_in, d, s);
+    case 1: return init_t<float, float>(K, static_cast<float*>(f), gf, sqrtg, base_uth, ini, rho_in, u_in, d, s);
+    case 2: return init_t<__half, float>(K, static_cast<__half*>(f), gf, sqrtg, base_uth, ini, rho_in, u_in, d, s);
+    case 3:
+      return init_t<__nv_bfloat16, float>(K, static_cast<__nv_bfloat16*>(f), gf, sqrtg, base_uth, ini, rho_in,
+                                          u_in, d, s);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
-cudaError_t launch_convert(int prec, int to_double, void* state, double* dbl, size_t n,
+cudaError_t launch_convert(int prec, int to_double, void* state, double* dbl, size_t n, size_t ncell,
                            cudaStream_t s) {
+  static bool weights_set = false;
+  if (!weights_set) {
+    double w[Q];
+    for (int l = 0; l < Q; ++l) w[l] = weight(l);
+    cudaError_t e = cudaMemcpyToSymbol(c_weight, w, sizeof(w));
+    if (e != cudaSuccess) return e;
+    weights_set = true;
+  }
   const int threads = 256;
   const size_t want = (n + threads - 1) / threads;
   const int blocks = int(want < 152 * 16 ? (want ? want : 1) : 152 * 16);
-  if (prec == 0)
-    k_convert<double><<<blocks, threads, 0, s>>>(static_cast<double*>(state), dbl, n, to_double);
-  else
-    k_convert<float><<<blocks, threads, 0, s>>>(static_cast<float*>(state), dbl, n, to_double);
+  switch (prec) {
+    case 0: k_convert<double><<<blocks, threads, 0, s>>>(static_cast<double*>(state), dbl, n, ncell, to_double); break;
+    case 1: k_convert<float><<<blocks, threads, 0, s>>>(static_cast<float*>(state), dbl, n, ncell, to_double); break;
+    case 2: k_convert<__half><<<blocks, threads, 0, s>>>(static_cast<__half*>(state), dbl, n, ncell, to_double); break;
+    case 3:
+      k_convert<__nv_bfloat16><<<blocks, threads, 0, s>>>(static_cast<__nv_bfloat16*>(state), dbl, n, ncell,
+                                                          to_double);
+      break;
+    default: return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 

@@ -11,8 +11,8 @@ namespace lbgm {
 // non-equilibrium stress, forcing, BGK, store. fin/fout are whole states
 // (batch blocks of Q * ncell populations). flag is set to 1 when a node's
 // density is not finite.
-template <typename Real, int K>
-__global__ void __launch_bounds__(256) k_step(const Real* __restrict__ fin, Real* __restrict__ fout,
+template <typename S, typename Real, int K>
+__global__ void __launch_bounds__(256) k_step(const S* __restrict__ fin, S* __restrict__ fout,
                                               GeoDev<Real> geo, const InstParams<Real>* __restrict__ inst,
                                               Dims d, int* __restrict__ flag) {
   const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -30,14 +30,12 @@ __global__ void __launch_bounds__(256) k_step(const Real* __restrict__ fin, Real
   const InstParams<Real> ip = inst[p.b];
   const Coef<Real> k = coefficients<Real, K>(m, g, ip.kappa, ip.G);
   collide<Real, K>(f, k, g, ip.omega);
-  Real* out = fout + base + p.cell;
-#pragma unroll
-  for (int l = 0; l < Q; ++l) out[size_t(l) * d.ncell] = f[l];
+  store_node(fout + base + p.cell, d.ncell, f);
 }
 
 // rho' and u of the streamed populations (moments only).
-template <typename Real, int K>
-__global__ void __launch_bounds__(256) k_macros(const Real* __restrict__ fin, double* __restrict__ rho,
+template <typename S, typename Real, int K>
+__global__ void __launch_bounds__(256) k_macros(const S* __restrict__ fin, double* __restrict__ rho,
                                                 double* __restrict__ u, Dims d) {
   const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= uint32_t(d.batch) * uint32_t(d.ncell)) return;
@@ -70,8 +68,8 @@ struct InitInst {
 
 // Initial state f = f^eq(rho', u): either from caller fields (rho_in, u_in
 // non-NULL) or rho' = 1/sqrt(g), u = base(b, i_r) + noise.
-template <typename Real, int K>
-__global__ void __launch_bounds__(256) k_init(Real* __restrict__ f, GeoDev<Real> geo,
+template <typename S, typename Real, int K>
+__global__ void __launch_bounds__(256) k_init(S* __restrict__ f, GeoDev<Real> geo,
                                               const double* __restrict__ sqrtg,
                                               const double* __restrict__ base_uth,
                                               const InitInst* __restrict__ ini,
@@ -104,9 +102,7 @@ __global__ void __launch_bounds__(256) k_init(Real* __restrict__ f, GeoDev<Real>
   const NodeGeo<Real, K> g = load_geo<Real, K>(geo, row);
   Real fe[Q];
   equilibrium<Real, K>(Real(rho), Real(u[0]), Real(u[1]), Real(u[2]), g, fe);
-  Real* out = f + size_t(p.b) * Q * d.ncell + p.cell;
-#pragma unroll
-  for (int l = 0; l < Q; ++l) out[size_t(l) * d.ncell] = fe[l];
+  store_node(f + size_t(p.b) * Q * d.ncell + p.cell, d.ncell, fe);
 }
 
 }  // namespace lbgm

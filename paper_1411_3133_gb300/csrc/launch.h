@@ -19,6 +19,12 @@ cudaError_t launch_step_f64(int K, const double* fin, double* fout, const GeoDev
 cudaError_t launch_step_f32(int K, const float* fin, float* fout, const GeoDev<float>& geo,
                             const InstParams<float>* inst, const Dims& d, int* flag, int threads,
                             cudaStream_t s);
+cudaError_t launch_step_h16(int K, const __half* fin, __half* fout, const GeoDev<float>& geo,
+                            const InstParams<float>* inst, const Dims& d, int* flag, int threads,
+                            cudaStream_t s);
+cudaError_t launch_step_b16(int K, const __nv_bfloat16* fin, __nv_bfloat16* fout, const GeoDev<float>& geo,
+                            const InstParams<float>* inst, const Dims& d, int* flag, int threads,
+                            cudaStream_t s);
 
 // TMA-pipelined FP32 step (n3 in {128, 256}); map is a CUtensorMap over the
 // input state (make_state_tensor_map).
@@ -29,13 +35,14 @@ cudaError_t launch_step_tma_f32(int K, const void* map, const float* fin, float*
                                 const GeoDev<float>& geo, const InstParams<float>* inst, const Dims& d,
                                 int* flag, cudaStream_t s);
 
-// prec: 0 = FP64, 1 = FP32 (fin/f are double* or float*, geo a GeoDev of that type)
+// prec: 0 = FP64, 1 = FP32, 2 = FP16 deviations, 3 = BF16 deviations (state
+// pointers of the storage type; geo a GeoDev<double> for FP64, else GeoDev<float>)
 cudaError_t launch_macros(int prec, int K, const void* fin, double* rho, double* u, const Dims& d,
                           cudaStream_t s);
 cudaError_t launch_init(int prec, int K, void* f, const void* geo, const double* sqrtg,
                         const double* base_uth, const InitInst* ini, const double* rho_in,
                         const double* u_in, const Dims& d, cudaStream_t s);
-cudaError_t launch_convert(int prec, int to_double, void* state, double* dbl, size_t n,
+cudaError_t launch_convert(int prec, int to_double, void* state, double* dbl, size_t n, size_t ncell,
                            cudaStream_t s);
 
 // Observables: NQ sums per instance written to out[batch * DIAG_NQ].

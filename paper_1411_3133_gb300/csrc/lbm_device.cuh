@@ -7,6 +7,9 @@
 // the odd part O, and f(+c) uses E + O while f(-c) uses E - O.
 #pragma once
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include <cstdint>
 #include <type_traits>
 
@@ -104,6 +107,52 @@ struct Pair {
   static constexpr int s = (x != 0 ? (x < 0 ? -x : x) : (y != 0 ? (y < 0 ? -y : y) : (z < 0 ? -z : z)));
 };
 
+template <int L>
+struct WeightOf {
+  static constexpr double w = L == 0 ? W_REST : PAIRS[(L - 1) / 2].w;
+};
+
+// ---------------------------------------------------------------------------
+// population storage
+// ---------------------------------------------------------------------------
+// Codec<S, R> reads populations stored as S into the compute type R and back.
+// For the reduced-precision formats the stored value is the scaled deviation
+// (f_l - w_l rho_ref) / w_l with rho_ref = 1, so every population's stored
+// number is O(u/cs) whatever its weight; f_l = w_l (1 + s_l).
+template <class S, class R>
+struct Codec {
+  template <int L>
+  __device__ static __forceinline__ R dec(S v) { return R(v); }
+  template <int L>
+  __device__ static __forceinline__ S enc(R f) { return S(f); }
+};
+template <>
+struct Codec<__half, float> {
+  template <int L>
+  __device__ static __forceinline__ float dec(__half v) {
+    constexpr float w = float(WeightOf<L>::w);
+    return fmaf(w, __half2float(v), w);
+  }
+  template <int L>
+  __device__ static __forceinline__ __half enc(float f) {
+    constexpr float iw = float(1.0 / WeightOf<L>::w);
+    return __float2half_rn(fmaf(f, iw, -1.0f));
+  }
+};
+template <>
+struct Codec<__nv_bfloat16, float> {
+  template <int L>
+  __device__ static __forceinline__ float dec(__nv_bfloat16 v) {
+    constexpr float w = float(WeightOf<L>::w);
+    return fmaf(w, __bfloat162float(v), w);
+  }
+  template <int L>
+  __device__ static __forceinline__ __nv_bfloat16 enc(float f) {
+    constexpr float iw = float(1.0 / WeightOf<L>::w);
+    return __float2bfloat16_rn(fmaf(f, iw, -1.0f));
+  }
+};
+
 // ---------------------------------------------------------------------------
 // pull streaming
 // ---------------------------------------------------------------------------
@@ -196,9 +245,12 @@ __device__ __forceinline__ bool near_wall(const CellPos& p, const Dims& d) {
 
 // Streamed populations of a node near a wall: every moving population from
 // its (possibly folded) source, read from the post-collision state fin.
-template <typename Real>
-__device__ __forceinline__ void gather_wall(const Real* __restrict__ fin, const CellPos& p,
-                                            const Dims& d, Real (&f)[Q]) {
+// Opposite velocities share their weight, so a folded population decodes
+// with the weight of the pair.
+template <class S, class R>
+__device__ __forceinline__ void gather_wall(const S* __restrict__ fin, const CellPos& p,
+                                            const Dims& d, R (&f)[Q]) {
+  using Cd = Codec<S, R>;
   const int N = d.ncell;
   static_for<0, NPAIR>([&](auto P_) {
     constexpr int P = decltype(P_)::value;
@@ -206,18 +258,19 @@ __device__ __forceinline__ void gather_wall(const Real* __restrict__ fin, const 
     bool fp, fm;
     const int sp = src_wall<C::x, C::y, C::z, C::s>(p, d, fp);
     const int sm = src_wall<-C::x, -C::y, -C::z, C::s>(p, d, fm);
-    f[2 * P + 1] = __ldg(fin + (fp ? 2 * P + 2 : 2 * P + 1) * N + sp);
-    f[2 * P + 2] = __ldg(fin + (fm ? 2 * P + 1 : 2 * P + 2) * N + sm);
+    f[2 * P + 1] = Cd::template dec<2 * P + 1>(__ldg(fin + (fp ? 2 * P + 2 : 2 * P + 1) * N + sp));
+    f[2 * P + 2] = Cd::template dec<2 * P + 2>(__ldg(fin + (fm ? 2 * P + 1 : 2 * P + 2) * N + sm));
   });
 }
 
 // Load the 41 streamed populations of node p from the post-collision state
 // fin (one instance's block: population l of cell c at fin[l * ncell + c]).
-template <typename Real>
-__device__ __forceinline__ void gather(const Real* __restrict__ fin, const CellPos& p,
-                                       const Dims& d, Real (&f)[Q]) {
+template <class S, class R>
+__device__ __forceinline__ void gather(const S* __restrict__ fin, const CellPos& p,
+                                       const Dims& d, R (&f)[Q]) {
+  using Cd = Codec<S, R>;
   const int N = d.ncell;
-  f[0] = __ldg(fin + p.cell);
+  f[0] = Cd::template dec<0>(__ldg(fin + p.cell));
   if (!near_wall(p, d)) {
     Neighbours nb;
     make_neighbours(p, d, nb);
@@ -226,12 +279,22 @@ __device__ __forceinline__ void gather(const Real* __restrict__ fin, const CellP
       using C = Pair<P>;
       const int sp = src_far<C::x, C::y, C::z>(nb, d);
       const int sm = src_far<-C::x, -C::y, -C::z>(nb, d);
-      f[2 * P + 1] = __ldg(fin + (2 * P + 1) * N + sp);
-      f[2 * P + 2] = __ldg(fin + (2 * P + 2) * N + sm);
+      f[2 * P + 1] = Cd::template dec<2 * P + 1>(__ldg(fin + (2 * P + 1) * N + sp));
+      f[2 * P + 2] = Cd::template dec<2 * P + 2>(__ldg(fin + (2 * P + 2) * N + sm));
     });
   } else {
     gather_wall(fin, p, d, f);
   }
+}
+
+// Store the 41 post-collision populations of one node.
+template <class S, class R>
+__device__ __forceinline__ void store_node(S* __restrict__ out, int N, const R (&f)[Q]) {
+  using Cd = Codec<S, R>;
+  static_for<0, Q>([&](auto L_) {
+    constexpr int L = decltype(L_)::value;
+    out[size_t(L) * N] = Cd::template enc<L>(f[L]);
+  });
 }
 
 // ---------------------------------------------------------------------------

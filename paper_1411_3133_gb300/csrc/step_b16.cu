@@ -1,0 +1,13 @@
+// Fused time-step kernel, BF16 population deviations, FP32 arithmetic: instantiations for the flat,
+// cylindrical and ellipsoidal metrics.
+#include "step_launch.cuh"
+
+namespace lbgm {
+
+cudaError_t launch_step_b16(int K, const __nv_bfloat16* fin, __nv_bfloat16* fout, const GeoDev<float>& geo,
+                            const InstParams<float>* inst, const Dims& d, int* flag, int threads,
+                            cudaStream_t s) {
+  return launch_step_t<__nv_bfloat16, float>(K, fin, fout, geo, inst, d, flag, threads, s);
+}
+
+}  // namespace lbgm

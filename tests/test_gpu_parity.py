@@ -342,3 +342,45 @@ def test_tma_kernel_option_validation():
     with pytest.raises(L.LBError):
         tw.ctx.lb_set_option(L.LB_OPT_STEP_KERNEL, 2)
     tw.close()
+
+
+@pytest.mark.parametrize("prec,tol", [("fp16_shifted", 1e-3), ("bf16_shifted", 1e-2)])
+@pytest.mark.parametrize("ch", [Channel("cylindrical", 1.0, 1 / ETA, 16, 4, 64),
+                                Channel("ellipsoidal", 1.0, 1.1, 12, 4, 40, b=0.9, periodic3=False)],
+                         ids=["cyl", "ell"])
+def test_reduced_precision_storage_against_fp64_oracle(ch, prec, tol):
+    """Populations stored as FP16/BF16 deviations (f - w)/w, FP32 arithmetic:
+    u within tol * u_max of the FP64 oracle after 1, 10 and 100 steps for a
+    flow of realistic magnitude (u_max ~ 0.05). FP16 meets the 1e-3 target;
+    BF16's 8-bit mantissa gives about 1e-2."""
+    params = [dict(tau=0.8, G=G_LAMINAR)]
+    tw = Twin(ch, params, prec)
+    rho = np.stack([1.0 / tw.sims[0].sqrtg])
+    u = (_smooth_flow(ch) + noise_field(31, tw.N, 1e-3))[None]
+    tw.init_fields(rho, u)
+    done = 0
+    for n in (1, 10, 100):
+        tw.step(n - done)
+        done = n
+        _compare_macros(tw, tol, tol)
+    tw.close()
+
+
+@pytest.mark.parametrize("prec", ["fp16_shifted", "bf16_shifted"])
+def test_reduced_precision_state_round_trips(prec):
+    L = lib()
+    tw = Twin(CYL1, [dict(tau=0.8, G=1e-4, seed=2, amp=1e-3)], prec)
+    tw.ctx.lb_init(tw.lparams)
+    tw.ctx.lb_step(5)
+    assert tw.ctx.lb_state_bytes() == 41 * tw.N * 2
+    a = tw.ctx.lb_get_populations()
+    tw.ctx.lb_set_populations(a)
+    assert np.array_equal(tw.ctx.lb_get_populations(), a)
+    buf = np.zeros(tw.ctx.lb_state_bytes(), dtype=np.uint8)
+    tw.ctx.lb_get_state(buf)
+    tw.ctx.lb_step(7)
+    b = tw.ctx.lb_get_populations()
+    tw.ctx.lb_set_state(buf)
+    tw.ctx.lb_step(7)
+    assert np.array_equal(tw.ctx.lb_get_populations(), b)
+    tw.close()
