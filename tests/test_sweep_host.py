@@ -1,0 +1,40 @@
+"""Host logic of the critical-Dean finder (no GPU): growth-rate fit and the
+sign-change interpolation on synthetic amplitude series with known answers."""
+import numpy as np
+import pytest
+
+from paper_1411_3133_gb300.sweep import critical_dean, growth_rate
+
+
+def test_growth_rate_recovers_exponent_after_transient():
+    t = np.arange(0, 200001, 2000, dtype=float)
+    for sigma in (-3e-5, -1e-6, 2e-6, 4e-5):
+        # a fast-decaying transient on top of the leading mode
+        A = 1e-6 * np.exp(sigma * t) + 1e-4 * np.exp(-2e-4 * t)
+        assert growth_rate(t, A) == pytest.approx(sigma, rel=0.05, abs=2e-8)
+
+
+def test_growth_rate_stops_before_saturation():
+    t = np.arange(0, 200001, 1000, dtype=float)
+    sigma = 1e-4
+    A = 1e-7 * np.exp(sigma * t)
+    A = A / (1 + A / 1e-2)            # saturates at 1e-2
+    assert growth_rate(t, A) == pytest.approx(sigma, rel=0.05)
+
+
+def test_critical_dean_interpolates_first_sign_change():
+    de = [25, 30, 35, 40, 45]
+    s = [-3.0, -2.0, -1.0, 1.0, 3.0]
+    assert critical_dean(de, s) == pytest.approx(37.5)
+    assert np.isnan(critical_dean(de, [-1, -1, -1, -1, -1]))
+    # unsorted input
+    assert critical_dean(de[::-1], s[::-1]) == pytest.approx(37.5)
+
+
+def test_critical_dean_from_saturated_amplitude():
+    from paper_1411_3133_gb300.sweep import critical_dean_saturation
+    de = np.array([30.0, 34.0, 38.0, 42.0, 46.0, 50.0])
+    dec = 37.0
+    a = np.where(de > dec, np.sqrt(np.clip(2e-7 * (de - dec), 0, None)), 3e-7)
+    assert critical_dean_saturation(de, a) == pytest.approx(dec, rel=1e-9)
+    assert np.isnan(critical_dean_saturation(de, np.full(6, 3e-7)))
