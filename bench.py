@@ -190,6 +190,142 @@ def time_oracle(mode: str, steps: int = 1, reps: int = 1, budget: float = 120.0)
 
 
 # ---------------------------------------------------------------------------
+# workloads
+# ---------------------------------------------------------------------------
+class SweepRunner:
+    """24 instances of the 64 x 4 x 256 cylinder in one context (k_step)."""
+    profiled = True
+    launches_per_step = 1
+
+    def __init__(self, args, L, rank):
+        self.args, self.L = args, L
+        wl = workload_desc(args.precision)
+        self.wl = wl
+        spec = L.ChannelSpec(**wl.geometry_kwargs())
+        desc = spec.desc()
+        params = []
+        for b in range(wl.batch):
+            G = L.lb_force_for_dean("cylindrical", desc, wl.taus[b], wl.deans[b])
+            params.append(L.make_params(wl.taus[b], G, False, wl.seeds[b] + 1000 * rank,
+                                        wl.noise_amp, True))
+        self.ctx = L.LBContext(spec, batch=wl.batch, precision=wl.precision)
+        self.ctx.lb_set_option(L.LB_OPT_USE_GRAPH, 1)
+        self.ctx.lb_set_option(L.LB_OPT_STEP_KERNEL, {"auto": 0, "plain": 1, "tma": 2}[args.step_kernel])
+        self.ctx.lb_init(params)
+        self.cells = wl.batch * wl.ncells
+        self.stream = self.ctx.stream
+        self.kernel = "k_step_tma<KCYL,256>" if args.step_kernel == "tma" else \
+            f"k_step<{args.precision},KCYL>"
+        self.profiled = args.precision == "fp32" and args.step_kernel != "tma"
+
+    def warmup(self, n):
+        self.ctx.lb_step(n)
+
+    def step(self, n):
+        self.ctx.lb_step(n)
+
+    def diagnostics(self):
+        return self.ctx.lb_diagnostics()
+
+    def e2e(self, steps):
+        import torch
+        nbytes = self.ctx.lb_state_bytes()
+        host_in = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+        host_out = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+        self.ctx.lb_get_state(host_in)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            self.ctx.lb_set_state(host_in)
+            self.ctx.lb_step(1)
+            self.ctx.lb_get_state(host_out)
+        torch.cuda.synchronize()
+        self.state_bytes = nbytes
+        return time.perf_counter() - t0, nbytes, nbytes
+
+    def config(self):
+        wl = self.wl
+        return {"workload": f"Dean sweep, cylindrical channel {wl.nr}x{wl.ntheta}x{wl.n3}, "
+                            f"eta=0.975, {wl.batch} instances (12 De in 25..60 x tau 0.55/0.6), "
+                            f"D3Q41, {wl.precision}",
+                "cells_per_instance": wl.ncells, "instances": wl.batch, "precision": wl.precision,
+                "l2": f"inputs larger than L2: state {2 * self.state_bytes / 1e6:.0f} MB, no flush"}
+
+    def extra(self):
+        return {}
+
+    def close(self):
+        self.ctx.close()
+
+
+class MixedRunner:
+    """128 channels of mixed metric and size (cylinders and double-curved
+    channels, N_r in {32, 48, 64}, N_3 in 128..512, De in 20..150) in one
+    lb_batch: one k_step_list launch per metric kind per step, autotuned."""
+    profiled = False
+    launches_per_step = 2
+
+    def __init__(self, args, L, rank):
+        from paper_1411_3133_gb300.sweep import mixed_contexts
+        from paper_1411_3133_gb300.workloads import mixed_batch
+        self.args, self.L = args, L
+        self.insts = mixed_batch(seed=20241111 + 1000 * rank)
+        self.ctxs, self.batch = mixed_contexts(self.insts, args.precision)
+        self.batch.lb_batch_set_option(L.LB_OPT_USE_GRAPH, 1)
+        self.cells = self.batch.lb_batch_nodes()
+        self.stream = self.ctxs[0].stream
+        self.kernel = f"k_step_list<{args.precision},KCYL|KELL>"
+        self.tune = None
+
+    def warmup(self, n):
+        self.tune = self.batch.lb_batch_autotune(self.args.tune_steps)
+        self.batch.lb_batch_step(n)
+
+    def step(self, n):
+        self.batch.lb_batch_step(n)
+
+    def diagnostics(self):
+        return [c.lb_diagnostics()[0] for c in self.ctxs]
+
+    def e2e(self, steps):
+        import torch
+        sizes = [c.lb_state_bytes() for c in self.ctxs]
+        host_in = [torch.empty(n, dtype=torch.uint8, pin_memory=True) for n in sizes]
+        host_out = [torch.empty(n, dtype=torch.uint8, pin_memory=True) for n in sizes]
+        for c, h in zip(self.ctxs, host_in):
+            c.lb_get_state(h)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            for c, h in zip(self.ctxs, host_in):
+                c.lb_set_state(h)
+            self.batch.lb_batch_step(1)
+            for c, h in zip(self.ctxs, host_out):
+                c.lb_get_state(h)
+        torch.cuda.synchronize()
+        self.state_bytes = sum(sizes)
+        return time.perf_counter() - t0, self.state_bytes, self.state_bytes
+
+    def config(self):
+        ncyl = sum(i.metric == "cylindrical" for i in self.insts)
+        return {"workload": f"mixed sweep, {len(self.insts)} channels ({ncyl} cylindrical eta=0.975, "
+                            f"{len(self.insts) - ncyl} double-curved R2/R1 in 0.25..4), N_r in "
+                            "{32,48,64} x 4 x N_3 in 128..512, De in 20..150, tau 0.55, D3Q41, "
+                            f"{self.args.precision}, one lb_batch",
+                "nodes": self.cells, "instances": len(self.insts), "precision": self.args.precision,
+                "l2": f"inputs larger than L2: state {2 * self.state_bytes / 1e6:.0f} MB, no flush"}
+
+    def extra(self):
+        best, trials = self.tune
+        return {"autotune": {"best": best, "trials": trials}}
+
+    def close(self):
+        self.batch.close()
+        for c in self.ctxs:
+            c.close()
+
+
+# ---------------------------------------------------------------------------
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -201,6 +337,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--step-kernel", default="auto", choices=["auto", "plain", "tma"])
     ap.add_argument("--precision", default="fp32", choices=sorted(BYTES_PER_UPDATE))
+    ap.add_argument("--workload", default="sweep", choices=["sweep", "mixed"],
+                    help="sweep: 24-instance 64x4x256 cylinder Dean sweep; mixed: 128 channels "
+                         "of mixed metric and size in one lb_batch")
+    ap.add_argument("--tune-steps", type=int, default=20,
+                    help="mixed: steps per autotuner trial (taken inside the warm-up)")
     args = ap.parse_args()
     assert args.warmup >= 3, "at least 3 warm-up steps"
 
@@ -224,25 +365,15 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
 
-    wl = workload_desc(args.precision)
-    spec = L.ChannelSpec(**wl.geometry_kwargs())
-    desc = spec.desc()
-    params = []
-    for b in range(wl.batch):
-        G = L.lb_force_for_dean("cylindrical", desc, wl.taus[b], wl.deans[b])
-        params.append(L.make_params(wl.taus[b], G, False, wl.seeds[b] + 1000 * rank, wl.noise_amp, True))
-    ctx = L.LBContext(spec, batch=wl.batch, precision=wl.precision)
-    ctx.lb_set_option(L.LB_OPT_USE_GRAPH, 1)
-    ctx.lb_set_option(L.LB_OPT_STEP_KERNEL, {"auto": 0, "plain": 1, "tma": 2}[args.step_kernel])
-    ctx.lb_init(params)
-    cells = wl.batch * wl.ncells
-    stream = ctx.stream
+    runner = (MixedRunner if args.workload == "mixed" else SweepRunner)(args, L, rank)
+    cells = runner.cells
+    stream = runner.stream
 
-    # warm-up
-    ctx.lb_step(args.warmup)
+    # warm-up (the mixed batch's autotuner runs its trials inside it)
+    runner.warmup(args.warmup)
     torch.cuda.synchronize()
 
-    # timed region: K steps = K launches of the fused step kernel
+    # timed region: K steps
     sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
     if sampler:
         sampler.start()
@@ -251,14 +382,14 @@ def main():
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
-    ctx.lb_step(args.steps)
+    runner.step(args.steps)
     ev1.record(stream)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     ms = ev0.elapsed_time(ev1)
     clocks = sampler.stop() if sampler else None
-    d = ctx.lb_diagnostics()
+    d = runner.diagnostics()
     finite = all(x["nonfinite"] == 0 for x in d)
     if dist:
         t = torch.tensor([ms], device="cuda")
@@ -267,33 +398,22 @@ def main():
     sec = ms / 1e3
     value = world * cells * args.steps / sec / 1e6
     per_launch = sec / args.steps
-    bpu = BYTES_PER_UPDATE[wl.precision]
+    bpu = BYTES_PER_UPDATE[args.precision]
     achieved = bpu * cells / per_launch / 1e9
     peak, peak_kind = peaks()
-    traffic = measured_traffic() if wl.precision == "fp32" else None
+    traffic = measured_traffic() if runner.profiled else None
 
     # end to end through the C ABI with host buffers: each step uploads the
     # state from pinned host memory, advances it one step and reads it back
-    nbytes = ctx.lb_state_bytes()
-    host_in = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
-    host_out = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
-    ctx.lb_get_state(host_in)
-    torch.cuda.synchronize()
     if dist:
         dist.barrier()
-    t0 = time.perf_counter()
-    for _ in range(args.e2e_steps):
-        ctx.lb_set_state(host_in)
-        ctx.lb_step(1)
-        ctx.lb_get_state(host_out)
-    torch.cuda.synchronize()
-    e2e_sec = time.perf_counter() - t0
+    e2e_sec, h2d, d2h = runner.e2e(args.e2e_steps)
     if dist:
         t = torch.tensor([e2e_sec], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_sec = float(t.item())
     e2e_value = world * cells * args.e2e_steps / e2e_sec / 1e6
-    ctx.close()
+    runner.close()
 
     if rank == 0:
         cpu = None
@@ -307,27 +427,21 @@ def main():
             "metric": METRIC, "value": round(value, 2), "unit": "MLUPS", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 6),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": DTYPE[wl.precision], "data": "synthetic",
-            "config": {"workload": f"Dean sweep, cylindrical channel {wl.nr}x{wl.ntheta}x{wl.n3}, "
-                                   f"eta=0.975, {wl.batch} instances (12 De in 25..60 x tau 0.55/0.6), "
-                                   f"D3Q41, {wl.precision}",
-                       "cells_per_instance": wl.ncells, "instances": wl.batch,
-                       "precision": wl.precision, "bytes_per_update": bpu,
-                       "l2": f"inputs larger than L2: state {2 * nbytes / 1e6:.0f} MB, no flush",
-                       "parallelism": f"replicas x{world}"},
+            "dtype": DTYPE[args.precision], "data": "synthetic",
+            "config": dict(runner.config(), bytes_per_update=bpu, parallelism=f"replicas x{world}"),
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
                          "unit": "GB/s", "frac": round(achieved / peak, 4),
                          "traffic": traffic, "peak_source": peak_kind,
-                         "kernel": "k_step_tma<KCYL,256>" if args.step_kernel == "tma" else "k_step<float,KCYL>",
-                         "algorithmic_bytes_per_launch": bpu * cells},
-            "e2e": {"value": round(e2e_value, 2), "unit": "MLUPS", "h2d_bytes_per_step": nbytes,
-                    "d2h_bytes_per_step": nbytes, "steps": args.e2e_steps},
-            "gpu_launches": args.steps,
+                         "kernel": runner.kernel, "algorithmic_bytes_per_launch": bpu * cells},
+            "e2e": {"value": round(e2e_value, 2), "unit": "MLUPS", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "steps": args.e2e_steps},
+            "gpu_launches": args.steps * runner.launches_per_step,
             "clocks": clocks,
             "cpu_baseline": cpu,
             "finite": finite,
             "dean_measured": [round(x["dean"], 3) for x in d[:3]],
         }
+        line.update(runner.extra())
         print(json.dumps(line))
     if dist:
         dist.destroy_process_group()

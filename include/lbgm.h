@@ -134,13 +134,27 @@ typedef enum {
                                (64..256, multiple of 32; default 128) */
   LB_OPT_USE_GRAPH = 2,     /* 1: lb_step replays a captured CUDA graph of
                                pairs of steps (default 0) */
-  LB_OPT_STEP_KERNEL = 3    /* 0: automatic (default: the one-node-per-
+  LB_OPT_STEP_KERNEL = 3,   /* 0: automatic (default: the one-node-per-
                                thread kernel, the fastest measured); 1: that
                                kernel, gathering from global memory; 2: the
                                TMA-pipelined kernel (FP32 and n3 in {128,
                                256} only; LB_ERR_ARG otherwise). Both give
                                bitwise identical states. */
+  LB_OPT_SCHEDULE = 4       /* batches only (lb_batch_set_option): 0: one
+                               block per tile of block_threads nodes
+                               (default); 1: a persistent grid of (resident
+                               blocks per SM) x (SMs) blocks that walks the
+                               tile list. Both give bitwise identical
+                               states. */
 } lb_option;
+
+/* One configuration measured by lb_autotune / lb_batch_autotune. */
+typedef struct {
+  int block_threads;   /* LB_OPT_BLOCK_THREADS */
+  int schedule;        /* contexts: LB_OPT_STEP_KERNEL (1 or 2);
+                          batches: LB_OPT_SCHEDULE (0 or 1) */
+  double ms_per_step;  /* measured with CUDA events on the stream */
+} lb_tune;
 
 /* --------------------------------------------------------------------- */
 
@@ -252,12 +266,73 @@ lb_status lb_diagnostics_noalloc(lb_metric metric, const lb_geometry_desc* geom,
                                  const double* tau, const double* rho, const double* u,
                                  void* cuda_stream, lb_diag* out);
 
+/* Autotuner of the step launch. Runs steps_per_trial (>= 1) time steps in
+ * each configuration -- block_threads in {64, 128, 192, 256} with the plain
+ * step kernel, and the TMA kernel where the context supports it -- timed with
+ * CUDA events on the context's stream, then keeps the fastest. Every
+ * configuration computes bitwise the same states, so the trial steps are
+ * real time steps: they advance the simulation and the step count. best
+ * (may be NULL) receives the chosen configuration; trials (may be NULL,
+ * capacity max_trials) every measured one, *n_trials their number.
+ * Synchronises the stream. */
+lb_status lb_autotune(lb_ctx* ctx, int steps_per_trial, lb_tune* best, lb_tune* trials, int max_trials,
+                      int* n_trials);
+
 /* Release everything the context owns. NULL is allowed. */
 void lb_destroy(lb_ctx* ctx);
 
 /* Message of the last failure on ctx (NULL: of the calling thread's last
  * call without a context). Never NULL. */
 const char* lb_last_error(const lb_ctx* ctx);
+
+/* --------------------------------------------------------------------- */
+/* Batches of contexts of different geometry.
+ *
+ * A sweep over Dean numbers, radii and grid sizes (Sec. III and IV vary
+ * the driving force, the radii ratio and the cross-section) has instances
+ * of different metric kind and size. lb_batch_step advances every instance
+ * of every member context by one time step per step with one launch of a
+ * work-list kernel per metric kind present (the kinds run concurrently on
+ * forked streams): the work list holds one entry (instance, first node) per
+ * tile of block_threads consecutive nodes, so instances of any size share
+ * the grid. The update is the one of lb_step (Eq. LB), node for node, and the
+ * resulting states are bitwise those of lb_step on each member.
+ *
+ * Members stay owned by the caller and usable with every lb_* call
+ * (lb_init, lb_diagnostics, lb_get_state, ...) between batch steps; they
+ * must outlive the batch, share one precision, device and stream, and
+ * appear once. The batch reads each member's buffer parity before every
+ * lb_batch_step call, so stepping members on their own in between is
+ * allowed. */
+typedef struct lb_batch lb_batch;
+
+/* members: host array [count] of initialised or not-yet-initialised
+ * contexts. No device work; the work list is built on the first step. */
+lb_status lb_batch_create(lb_ctx* const* members, int count, lb_batch** out);
+
+/* n >= 0 time steps of every member (each must be initialised). Options:
+ * LB_OPT_CHECK_EVERY, LB_OPT_BLOCK_THREADS, LB_OPT_USE_GRAPH (a captured
+ * graph of two batch steps), LB_OPT_SCHEDULE. A non-finite density found by
+ * a check poisons that member and returns LB_ERR_NONFINITE. */
+lb_status lb_batch_step(lb_batch* batch, long long n);
+lb_status lb_batch_set_option(lb_batch* batch, int option, long long value);
+
+/* As lb_autotune over block_threads in {64, 128, 192, 256} x LB_OPT_SCHEDULE
+ * in {0, 1}; the trial steps are real batch steps. */
+lb_status lb_batch_autotune(lb_batch* batch, int steps_per_trial, lb_tune* best, lb_tune* trials,
+                            int max_trials, int* n_trials);
+
+/* Nodes of all instances of all members (one batch step updates them all). */
+long long lb_batch_nodes(const lb_batch* batch);
+
+/* Batch steps taken since creation. */
+long long lb_batch_step_count(const lb_batch* batch);
+
+/* Release the batch's work list, streams and graph (not the members). */
+void lb_batch_destroy(lb_batch* batch);
+
+/* Message of the last failure on the batch (NULL: as lb_last_error(NULL)). */
+const char* lb_batch_last_error(const lb_batch* batch);
 
 #ifdef __cplusplus
 }

@@ -11,66 +11,12 @@
 #include <vector>
 
 #include "../../include/lbgm.h"
+#include "ctx.h"
 #include "geometry.h"
 #include "kernels.cuh"
 #include "launch.h"
 
 using namespace lbgm;
-
-struct lb_ctx {
-  lb_metric metric;
-  lb_geometry_desc geom;
-  int batch = 0;
-  lb_precision prec;
-  int K = 0;
-  int device = 0;
-  cudaStream_t stream = nullptr;
-  bool own_stream = false;
-  lb_allocator alloc{};
-  bool has_alloc = false;
-  std::vector<std::pair<void*, size_t>> allocations;
-
-  Dims dims{};
-  size_t ncell = 0;         // per instance
-  size_t state_elems = 0;   // batch * Q * ncell
-  size_t elem_bytes = 0;
-  void* f[2] = {nullptr, nullptr};
-  int cur = 0;
-
-  void* geo_real = nullptr;        // 9 arrays of nrows in the compute precision
-  GeoDev<double> geo_d{};
-  GeoDev<float> geo_f{};
-  double* geo64 = nullptr;         // [nr * n3][4]: sqrtg, speed, wA, wOmega
-  double* sqrtg = nullptr;         // [nr * n3]
-  double* base_uth = nullptr;      // [batch * nr]
-  InitInst* ini = nullptr;         // [batch]
-  void* inst = nullptr;            // InstParams<Real>[batch]
-  double* rho_s = nullptr;         // macros scratch [batch * N]
-  double* u_s = nullptr;           // [batch * 3 * N]
-  double* rowmean = nullptr;       // [batch * nr * nt]
-  double* partial = nullptr;       // [batch * nblk * DIAG_NQ]
-  double* diag_out = nullptr;      // [batch * DIAG_NQ]
-  double* dbl_stage = nullptr;     // conversion staging (FP32 populations), lazily allocated
-  int* flag = nullptr;
-  int nblk = 0;
-
-  std::vector<double> tau;          // per instance, host copy
-  std::vector<double> host_geo;     // lb_geometry_eval rows
-  long long step = 0;
-  bool initialized = false;
-  bool poisoned = false;
-  std::string err;
-
-  long long check_every = 0;
-  int block_threads = 128;
-  int use_graph = 0;
-  cudaGraphExec_t graph = nullptr;   // two steps, buffer 0 -> 1 -> 0
-  int graph_threads = 0;
-  int graph_kernel = -1;
-  int step_kernel = 0;               // LB_OPT_STEP_KERNEL
-  bool tma_ok = false;               // tensor maps built for both buffers
-  alignas(64) unsigned char tmap[2][128];
-};
 
 namespace {
 
@@ -299,6 +245,8 @@ const void* geo_ptr(lb_ctx* c) {
 }  // namespace
 
 void lbgm::set_last_error_noctx(const std::string& msg) { g_err = msg; }
+lb_status lbgm::ctx_fail(lb_ctx* c, lb_status s, const std::string& msg) { return fail(c, s, msg); }
+bool lbgm::ctx_usable(lb_ctx* c, lb_status* s) { return usable(c, s); }
 
 // ---------------------------------------------------------------------------
 extern "C" {
@@ -723,6 +671,59 @@ lb_status lb_set_option(lb_ctx* c, int option, long long value) {
 }
 
 long long lb_step_count(const lb_ctx* c) { return c ? c->step : -1; }
+
+lb_status lb_autotune(lb_ctx* c, int steps_per_trial, lb_tune* best, lb_tune* trials, int max_trials,
+                      int* n_trials) {
+  lb_status s;
+  if (!usable(c, &s)) return s;
+  if (steps_per_trial < 1) return fail(c, LB_ERR_ARG, "need steps_per_trial >= 1");
+  if (max_trials < 0 || (max_trials > 0 && !trials)) return fail(c, LB_ERR_ARG, "bad trials buffer");
+  std::vector<lb_tune> cand;
+  for (int t : {64, 128, 192, 256}) cand.push_back({t, 1, 0.0});
+  if (c->tma_ok) cand.push_back({0, 2, 0.0});  // the TMA kernel fixes its own block shape
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  LB_CUDA(c, cudaEventCreate(&e0));
+  cudaError_t e = cudaEventCreate(&e1);
+  if (e != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return cuda_fail(c, e, "cudaEventCreate");
+  }
+  const int keep_threads = c->block_threads;
+  lb_status st = LB_OK;
+  for (lb_tune& k : cand) {
+    c->block_threads = k.block_threads > 0 ? k.block_threads : keep_threads;
+    c->step_kernel = k.schedule;
+    for (int i = 0; i <= steps_per_trial && st == LB_OK; ++i) {  // step 0 is the untimed warm-up
+      if (i == 1 && (e = cudaEventRecord(e0, c->stream)) != cudaSuccess) st = cuda_fail(c, e, "cudaEventRecord");
+      if (st == LB_OK) st = launch_step_once(c);
+      if (st == LB_OK) ++c->step;
+    }
+    if (st == LB_OK && (e = cudaEventRecord(e1, c->stream)) != cudaSuccess) st = cuda_fail(c, e, "cudaEventRecord");
+    if (st == LB_OK && (e = cudaEventSynchronize(e1)) != cudaSuccess) st = cuda_fail(c, e, "cudaEventSynchronize");
+    float ms = 0.f;
+    if (st == LB_OK && (e = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess)
+      st = cuda_fail(c, e, "cudaEventElapsedTime");
+    if (st != LB_OK) break;
+    k.ms_per_step = double(ms) / steps_per_trial;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != LB_OK) return st;
+  size_t ib = 0;
+  for (size_t i = 1; i < cand.size(); ++i)
+    if (cand[i].ms_per_step < cand[ib].ms_per_step) ib = i;
+  if (cand[ib].block_threads == 0) cand[ib].block_threads = keep_threads;
+  for (lb_tune& k : cand)
+    if (k.block_threads == 0) k.block_threads = keep_threads;
+  c->block_threads = cand[ib].block_threads;
+  c->step_kernel = cand[ib].schedule;
+  if (best) *best = cand[ib];
+  const int n = int(cand.size());
+  for (int i = 0; i < n && i < max_trials; ++i) trials[i] = cand[i];
+  if (n_trials) *n_trials = n;
+  if (c->check_every > 0) return check_flag(c);
+  return LB_OK;
+}
 
 void lb_destroy(lb_ctx* c) {
   if (!c) return;

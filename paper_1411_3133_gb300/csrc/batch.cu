@@ -1,0 +1,466 @@
+// Batches of contexts of different geometry (lb_batch_* of include/lbgm.h).
+//
+// Every instance of every member becomes one ListInst record; instances are
+// grouped by metric kind and each group gets a work list of (instance, first
+// node) tiles. One batch step is one k_step_list launch per group; groups
+// after the first run on forked streams so that small groups overlap.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "../../include/lbgm.h"
+#include "ctx.h"
+#include "launch.h"
+
+using namespace lbgm;
+
+namespace {
+
+constexpr int kMaxGroups = 3;  // flat, cylinder, ellipsoid
+
+struct Group {
+  int K = 0;
+  int ninst = 0;
+  int nwork = 0;
+  size_t inst_off = 0;   // byte offset of the ListInst records in dmem
+  size_t work_off = 0;   // byte offset of the int2 tiles in dmem
+  int blocks_per_sm = 0; // occupancy of k_step_list<K> at the built block size
+};
+
+}  // namespace
+
+struct lb_batch {
+  std::vector<lb_ctx*> m;
+  lb_precision prec = LB_FP32;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int nsm = 0;
+  long long nodes = 0;
+
+  // work list, valid while built
+  bool built = false;
+  int built_threads = 0;
+  std::vector<int> base_cur;  // member buffer parity when the records were written
+  int parity = 0;             // batch steps since then, mod 2
+  Group g[kMaxGroups];
+  int ngroups = 0;
+  void* dmem = nullptr;
+  size_t dmem_bytes = 0;
+
+  cudaStream_t aux[kMaxGroups - 1] = {};
+  cudaEvent_t ev_fork = nullptr;
+  cudaEvent_t ev_join[kMaxGroups - 1] = {};
+
+  int threads = 128;
+  int schedule = 0;
+  int use_graph = 0;
+  long long check_every = 0;
+  cudaGraphExec_t graph = nullptr;  // two batch steps, parity 0 then 1
+  int graph_threads = 0;
+  int graph_schedule = -1;
+
+  long long step = 0;
+  bool poisoned = false;
+  std::string err;
+};
+
+namespace {
+
+lb_status bfail(lb_batch* b, lb_status s, const std::string& msg) {
+  if (!b) return ctx_fail(nullptr, s, msg);
+  b->err = msg;
+  if (s == LB_ERR_CUDA) b->poisoned = true;
+  return s;
+}
+
+lb_status bcuda(lb_batch* b, cudaError_t e, const char* what) {
+  return bfail(b, LB_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define LB_BCUDA(b, call)                                \
+  do {                                                   \
+    cudaError_t e_ = (call);                             \
+    if (e_ != cudaSuccess) return bcuda(b, e_, #call);   \
+  } while (0)
+
+void drop_graph(lb_batch* b) {
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  b->graph = nullptr;
+}
+
+template <class S, class R>
+ListInst<S, R> record(const lb_ctx* c, int bi, int cur, const GeoDev<R>& geo) {
+  ListInst<S, R> r{};
+  r.d = c->dims;
+  r.d.batch = 1;
+  r.geo = geo;
+  r.ip = static_cast<const InstParams<R>*>(c->inst) + bi;
+  const size_t off = size_t(bi) * Q * c->ncell;
+  r.f0 = static_cast<const S*>(c->f[cur]) + off;
+  r.f1 = static_cast<S*>(c->f[1 - cur]) + off;
+  r.flag = c->flag;
+  return r;
+}
+
+template <class S, class R>
+void append_records(const lb_batch* b, int K, std::vector<unsigned char>& bytes, int* ninst,
+                    const GeoDev<R> lb_ctx::*geo_member) {
+  for (const lb_ctx* c : b->m) {
+    if (c->K != K) continue;
+    for (int bi = 0; bi < c->batch; ++bi) {
+      const ListInst<S, R> r = record<S, R>(c, bi, c->cur, c->*geo_member);
+      const unsigned char* p = reinterpret_cast<const unsigned char*>(&r);
+      bytes.insert(bytes.end(), p, p + sizeof(r));
+      ++*ninst;
+    }
+  }
+}
+
+size_t record_bytes(lb_precision p) {
+  switch (p) {
+    case LB_FP64: return sizeof(ListInst<double, double>);
+    case LB_FP32: return sizeof(ListInst<float, float>);
+    case LB_FP16_SHIFTED: return sizeof(ListInst<__half, float>);
+    default: return sizeof(ListInst<__nv_bfloat16, float>);
+  }
+}
+
+cudaError_t occupancy(lb_precision p, int K, int threads, int* out) {
+  switch (p) {
+    case LB_FP64: return step_list_occupancy_f64(K, threads, out);
+    case LB_FP32: return step_list_occupancy_f32(K, threads, out);
+    case LB_FP16_SHIFTED: return step_list_occupancy_h16(K, threads, out);
+    default: return step_list_occupancy_b16(K, threads, out);
+  }
+}
+
+// Write the instance records (with the members' current buffer parity) and
+// the tile lists for block size b->threads, and upload them.
+lb_status build(lb_batch* b) {
+  drop_graph(b);
+  b->built = false;
+  std::vector<unsigned char> recs;
+  std::vector<int2> work;
+  b->ngroups = 0;
+  size_t rec_total = 0;
+  for (int K : {int(KCYL), int(KELL), int(KFLAT)}) {
+    Group gr;
+    gr.K = K;
+    const size_t before = recs.size();
+    switch (b->prec) {
+      case LB_FP64: append_records<double, double>(b, K, recs, &gr.ninst, &lb_ctx::geo_d); break;
+      case LB_FP32: append_records<float, float>(b, K, recs, &gr.ninst, &lb_ctx::geo_f); break;
+      case LB_FP16_SHIFTED: append_records<__half, float>(b, K, recs, &gr.ninst, &lb_ctx::geo_f); break;
+      default: append_records<__nv_bfloat16, float>(b, K, recs, &gr.ninst, &lb_ctx::geo_f); break;
+    }
+    if (gr.ninst == 0) continue;
+    gr.inst_off = before;
+    // tiles, instance-major; instance ids are local to the group
+    const size_t w0 = work.size();
+    int local = 0;
+    for (const lb_ctx* c : b->m) {
+      if (c->K != K) continue;
+      for (int bi = 0; bi < c->batch; ++bi, ++local)
+        for (size_t t = 0; t < c->ncell; t += size_t(b->threads)) work.push_back(make_int2(local, int(t)));
+    }
+    gr.nwork = int(work.size() - w0);
+    gr.work_off = w0;  // in tiles for now
+    cudaError_t e = occupancy(b->prec, K, b->threads, &gr.blocks_per_sm);
+    if (e != cudaSuccess) return bcuda(b, e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+    b->g[b->ngroups++] = gr;
+    rec_total = recs.size();
+  }
+  const size_t work_base = (rec_total + 255) / 256 * 256;
+  for (int i = 0; i < b->ngroups; ++i) b->g[i].work_off = work_base + b->g[i].work_off * sizeof(int2);
+  const size_t need = work_base + work.size() * sizeof(int2);
+  if (need > b->dmem_bytes) {
+    if (b->dmem) cudaFree(b->dmem);
+    b->dmem = nullptr;
+    b->dmem_bytes = 0;
+    LB_BCUDA(b, cudaMalloc(&b->dmem, need));
+    b->dmem_bytes = need;
+  }
+  unsigned char* base = static_cast<unsigned char*>(b->dmem);
+  LB_BCUDA(b, cudaMemcpyAsync(base, recs.data(), recs.size(), cudaMemcpyHostToDevice, b->stream));
+  LB_BCUDA(b, cudaMemcpyAsync(base + work_base, work.data(), work.size() * sizeof(int2), cudaMemcpyHostToDevice,
+                              b->stream));
+  LB_BCUDA(b, cudaStreamSynchronize(b->stream));  // the host vectors go out of scope
+  b->base_cur.resize(b->m.size());
+  for (size_t i = 0; i < b->m.size(); ++i) b->base_cur[i] = b->m[i]->cur;
+  b->parity = 0;
+  b->built_threads = b->threads;
+  b->built = true;
+  return LB_OK;
+}
+
+// The records hold f0 = the buffer each member read when they were written;
+// they stay valid while every member has taken exactly the batch's steps.
+bool records_current(const lb_batch* b) {
+  if (!b->built || b->built_threads != b->threads) return false;
+  for (size_t i = 0; i < b->m.size(); ++i)
+    if (b->m[i]->cur != (b->base_cur[i] ^ b->parity)) return false;
+  return true;
+}
+
+cudaError_t launch_group(const lb_batch* b, const Group& gr, cudaStream_t s) {
+  const unsigned char* base = static_cast<const unsigned char*>(b->dmem);
+  const void* insts = base + gr.inst_off;
+  const int2* work = reinterpret_cast<const int2*>(base + gr.work_off);
+  const int grid = b->schedule == 1 ? std::max(1, gr.blocks_per_sm) * b->nsm : 0;
+  switch (b->prec) {
+    case LB_FP64: return launch_step_list_f64(gr.K, insts, work, gr.nwork, b->threads, grid, b->parity, s);
+    case LB_FP32: return launch_step_list_f32(gr.K, insts, work, gr.nwork, b->threads, grid, b->parity, s);
+    case LB_FP16_SHIFTED:
+      return launch_step_list_h16(gr.K, insts, work, gr.nwork, b->threads, grid, b->parity, s);
+    default: return launch_step_list_b16(gr.K, insts, work, gr.nwork, b->threads, grid, b->parity, s);
+  }
+}
+
+// One batch step: group 0 on the batch stream, the others forked.
+lb_status step_once(lb_batch* b) {
+  if (b->ngroups > 1) {
+    LB_BCUDA(b, cudaEventRecord(b->ev_fork, b->stream));
+    for (int i = 1; i < b->ngroups; ++i) {
+      LB_BCUDA(b, cudaStreamWaitEvent(b->aux[i - 1], b->ev_fork, 0));
+      LB_BCUDA(b, launch_group(b, b->g[i], b->aux[i - 1]));
+      LB_BCUDA(b, cudaEventRecord(b->ev_join[i - 1], b->aux[i - 1]));
+    }
+  }
+  if (b->ngroups > 0) LB_BCUDA(b, launch_group(b, b->g[0], b->stream));
+  for (int i = 1; i < b->ngroups; ++i) LB_BCUDA(b, cudaStreamWaitEvent(b->stream, b->ev_join[i - 1], 0));
+  b->parity ^= 1;
+  return LB_OK;
+}
+
+void advance_members(lb_batch* b, long long n) {
+  for (lb_ctx* c : b->m) {
+    c->step += n;
+    if (n & 1) c->cur ^= 1;
+  }
+  b->step += n;
+}
+
+lb_status check_members(lb_batch* b) {
+  for (size_t i = 0; i < b->m.size(); ++i) {
+    lb_ctx* c = b->m[i];
+    int h = 0;
+    LB_BCUDA(b, cudaMemcpyAsync(&h, c->flag, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
+    LB_BCUDA(b, cudaStreamSynchronize(b->stream));
+    if (h) {
+      const std::string m = "non-finite density in batch member " + std::to_string(i) + " after step " +
+                            std::to_string(c->step);
+      ctx_fail(c, LB_ERR_NONFINITE, m);
+      return bfail(b, LB_ERR_NONFINITE, m);
+    }
+  }
+  return LB_OK;
+}
+
+lb_status ready(lb_batch* b) {
+  if (!b) return bfail(nullptr, LB_ERR_ARG, "null batch");
+  if (b->poisoned) return bfail(b, LB_ERR_STATE, "batch poisoned by an earlier failure: " + b->err);
+  for (size_t i = 0; i < b->m.size(); ++i) {
+    lb_status s;
+    if (!ctx_usable(b->m[i], &s))
+      return bfail(b, LB_ERR_STATE, "member " + std::to_string(i) + ": " + b->m[i]->err);
+  }
+  return LB_OK;
+}
+
+// n steps; trials of the autotuner pass graph = false.
+lb_status run(lb_batch* b, long long n, bool graph) {
+  if (!records_current(b)) {
+    lb_status s = build(b);
+    if (s != LB_OK) return s;
+  }
+  if (graph && b->use_graph && b->check_every == 0 && n >= 3) {
+    if (b->parity != 0) {  // the captured pair starts at parity 0
+      lb_status s = step_once(b);
+      if (s != LB_OK) return s;
+      advance_members(b, 1);
+      --n;
+    }
+    if (!b->graph || b->graph_threads != b->threads || b->graph_schedule != b->schedule) {
+      drop_graph(b);
+      cudaGraph_t g = nullptr;
+      LB_BCUDA(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+      lb_status s1 = step_once(b);
+      lb_status s2 = s1 == LB_OK ? step_once(b) : s1;
+      cudaError_t e = cudaStreamEndCapture(b->stream, &g);
+      if (s2 != LB_OK) return s2;
+      if (e != cudaSuccess) return bcuda(b, e, "cudaStreamEndCapture");
+      e = cudaGraphInstantiate(&b->graph, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) return bcuda(b, e, "cudaGraphInstantiate");
+      b->graph_threads = b->threads;
+      b->graph_schedule = b->schedule;
+    }
+    const long long pairs = n / 2;
+    for (long long i = 0; i < pairs; ++i) LB_BCUDA(b, cudaGraphLaunch(b->graph, b->stream));
+    advance_members(b, 2 * pairs);
+    n &= 1;
+  }
+  for (long long i = 0; i < n; ++i) {
+    lb_status s = step_once(b);
+    if (s != LB_OK) return s;
+    advance_members(b, 1);
+    if (b->check_every > 0 && (b->step % b->check_every) == 0) {
+      s = check_members(b);
+      if (s != LB_OK) return s;
+    }
+  }
+  return LB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lb_status lb_batch_create(lb_ctx* const* members, int count, lb_batch** out) {
+  if (!members || !out) return bfail(nullptr, LB_ERR_ARG, "null argument");
+  *out = nullptr;
+  if (count < 1) return bfail(nullptr, LB_ERR_ARG, "need count >= 1");
+  lb_batch* b = new lb_batch();
+  auto bail = [&](lb_status s, const std::string& m) {
+    lb_batch_destroy(b);
+    return bfail(nullptr, s, m);
+  };
+  long long nodes = 0;
+  for (int i = 0; i < count; ++i) {
+    lb_ctx* c = members[i];
+    if (!c) return bail(LB_ERR_ARG, "member " + std::to_string(i) + " is NULL");
+    for (int j = 0; j < i; ++j)
+      if (members[j] == c) return bail(LB_ERR_ARG, "member " + std::to_string(i) + " appears twice");
+    if (i > 0 && (c->prec != b->prec || c->device != b->device || c->stream != b->stream))
+      return bail(LB_ERR_ARG, "member " + std::to_string(i) + " differs in precision, device or stream");
+    if (i == 0) {
+      b->prec = c->prec;
+      b->device = c->device;
+      b->stream = c->stream;
+    }
+    b->m.push_back(c);
+    nodes += (long long)c->batch * (long long)c->ncell;
+  }
+  b->nodes = nodes;
+  int cur_dev = 0;
+  cudaError_t e = cudaGetDevice(&cur_dev);
+  if (e == cudaSuccess && cur_dev != b->device) e = cudaErrorInvalidDevice;
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->nsm, cudaDevAttrMultiProcessorCount, b->device);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming);
+  for (int i = 0; i < kMaxGroups - 1 && e == cudaSuccess; ++i) {
+    e = cudaStreamCreateWithFlags(&b->aux[i], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_join[i], cudaEventDisableTiming);
+  }
+  if (e != cudaSuccess) return bail(LB_ERR_CUDA, std::string("batch setup: ") + cudaGetErrorString(e));
+  *out = b;
+  return LB_OK;
+}
+
+lb_status lb_batch_step(lb_batch* b, long long n) {
+  lb_status s = ready(b);
+  if (s != LB_OK) return s;
+  if (n < 0) return bfail(b, LB_ERR_ARG, "need n >= 0");
+  return run(b, n, true);
+}
+
+lb_status lb_batch_set_option(lb_batch* b, int option, long long value) {
+  if (!b) return bfail(nullptr, LB_ERR_ARG, "null batch");
+  switch (option) {
+    case LB_OPT_CHECK_EVERY:
+      if (value < 0) return bfail(b, LB_ERR_ARG, "need k >= 0");
+      b->check_every = value;
+      return LB_OK;
+    case LB_OPT_BLOCK_THREADS:
+      if (value < 64 || value > 256 || value % 32) return bfail(b, LB_ERR_ARG, "need 64..256, multiple of 32");
+      b->threads = int(value);
+      return LB_OK;
+    case LB_OPT_USE_GRAPH:
+      b->use_graph = value ? 1 : 0;
+      return LB_OK;
+    case LB_OPT_SCHEDULE:
+      if (value < 0 || value > 1) return bfail(b, LB_ERR_ARG, "need 0 (tile per block) or 1 (persistent)");
+      b->schedule = int(value);
+      return LB_OK;
+    default:
+      return bfail(b, LB_ERR_ARG, "option not available for batches");
+  }
+}
+
+lb_status lb_batch_autotune(lb_batch* b, int steps_per_trial, lb_tune* best, lb_tune* trials, int max_trials,
+                            int* n_trials) {
+  lb_status s = ready(b);
+  if (s != LB_OK) return s;
+  if (steps_per_trial < 1) return bfail(b, LB_ERR_ARG, "need steps_per_trial >= 1");
+  if (max_trials < 0 || (max_trials > 0 && !trials)) return bfail(b, LB_ERR_ARG, "bad trials buffer");
+  std::vector<lb_tune> cand;
+  for (int t : {64, 128, 192, 256})
+    for (int sc : {0, 1}) cand.push_back({t, sc, 0.0});
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  LB_BCUDA(b, cudaEventCreate(&e0));
+  cudaError_t e = cudaEventCreate(&e1);
+  if (e != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return bcuda(b, e, "cudaEventCreate");
+  }
+  const long long keep_check = b->check_every;
+  b->check_every = 0;
+  for (lb_tune& k : cand) {
+    b->threads = k.block_threads;
+    b->schedule = k.schedule;
+    s = run(b, 1, false);  // rebuilds the tiles for this block size; untimed
+    if (s != LB_OK) break;
+    if ((e = cudaEventRecord(e0, b->stream)) != cudaSuccess) {
+      s = bcuda(b, e, "cudaEventRecord");
+      break;
+    }
+    s = run(b, steps_per_trial, false);
+    if (s != LB_OK) break;
+    float ms = 0.f;
+    e = cudaEventRecord(e1, b->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e != cudaSuccess) {
+      s = bcuda(b, e, "timing a trial");
+      break;
+    }
+    k.ms_per_step = double(ms) / steps_per_trial;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  b->check_every = keep_check;
+  if (s != LB_OK) return s;
+  size_t ib = 0;
+  for (size_t i = 1; i < cand.size(); ++i)
+    if (cand[i].ms_per_step < cand[ib].ms_per_step) ib = i;
+  b->threads = cand[ib].block_threads;
+  b->schedule = cand[ib].schedule;
+  if (best) *best = cand[ib];
+  const int n = int(cand.size());
+  for (int i = 0; i < n && i < max_trials; ++i) trials[i] = cand[i];
+  if (n_trials) *n_trials = n;
+  if (keep_check > 0) return check_members(b);
+  return LB_OK;
+}
+
+long long lb_batch_nodes(const lb_batch* b) { return b ? b->nodes : -1; }
+
+long long lb_batch_step_count(const lb_batch* b) { return b ? b->step : -1; }
+
+void lb_batch_destroy(lb_batch* b) {
+  if (!b) return;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  drop_graph(b);
+  if (b->dmem) cudaFree(b->dmem);
+  for (int i = 0; i < kMaxGroups - 1; ++i) {
+    if (b->aux[i]) cudaStreamDestroy(b->aux[i]);
+    if (b->ev_join[i]) cudaEventDestroy(b->ev_join[i]);
+  }
+  if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+  delete b;
+}
+
+const char* lb_batch_last_error(const lb_batch* b) { return b ? b->err.c_str() : lb_last_error(nullptr); }
+
+}  // extern "C"

@@ -7,10 +7,28 @@
 
 namespace lbgm {
 
-// Fused time step (Eq. LB): pull streaming + walls, moments, equilibrium,
-// non-equilibrium stress, forcing, BGK, store. fin/fout are whole states
-// (batch blocks of Q * ncell populations). flag is set to 1 when a node's
-// density is not finite.
+// Fused time step (Eq. LB) of one node p of one instance whose state blocks
+// start at fin and fout: pull streaming + walls, moments, equilibrium,
+// non-equilibrium stress, forcing, BGK, store. flag is set to 1 when the
+// node's density is not finite.
+template <typename S, typename Real, int K>
+__device__ __forceinline__ void step_node(const S* __restrict__ fin, S* __restrict__ fout,
+                                          const GeoDev<Real>& geo, const InstParams<Real>& ip, const Dims& d,
+                                          const CellPos& p, int* __restrict__ flag) {
+  Real f[Q];
+  gather(fin, p, d, f);
+  const Moments<Real> m = moments(f);
+  if (!finite_v(m.rho)) {  // NaN or Inf
+    if (*flag == 0) atomicExch(flag, 1);
+  }
+  const int row = K == KELL ? p.ir * d.geo_rows3 + p.i3 : p.ir;
+  const NodeGeo<Real, K> g = load_geo<Real, K>(geo, row);
+  const Coef<Real> k = coefficients<Real, K>(m, g, ip.kappa, ip.G);
+  collide<Real, K>(f, k, g, ip.omega);
+  store_node(fout + p.cell, d.ncell, f);
+}
+
+// Uniform batch: fin/fout are whole states (batch blocks of Q * ncell).
 template <typename S, typename Real, int K>
 __global__ void __launch_bounds__(256) k_step(const S* __restrict__ fin, S* __restrict__ fout,
                                               GeoDev<Real> geo, const InstParams<Real>* __restrict__ inst,
@@ -19,18 +37,53 @@ __global__ void __launch_bounds__(256) k_step(const S* __restrict__ fin, S* __re
   if (t >= uint32_t(d.batch) * uint32_t(d.ncell)) return;
   const CellPos p = locate(d, t);
   const size_t base = size_t(p.b) * Q * d.ncell;
-  Real f[Q];
-  gather(fin + base, p, d, f);
-  const Moments<Real> m = moments(f);
-  if (!finite_v(m.rho)) {  // NaN or Inf
-    if (*flag == 0) atomicExch(flag, 1);
+  step_node<S, Real, K>(fin + base, fout + base, geo, inst[p.b], d, p, flag);
+}
+
+// One instance of a batch whose instances differ in geometry and size: its
+// dimensions (batch 1), geometry tables, parameters, two state blocks and
+// the flag that records a non-finite density.
+template <typename S, typename Real>
+struct ListInst {
+  Dims d;
+  GeoDev<Real> geo;
+  const InstParams<Real>* ip;
+  const S* f0;
+  S* f1;
+  int* flag;
+};
+
+// Work-list step over instances of one metric kind. Work item j updates the
+// nodes [work[j].y, work[j].y + blockDim.x) of instance work[j].x; blocks
+// take items j = blockIdx.x, blockIdx.x + gridDim.x, ... (a persistent grid
+// when gridDim.x < nwork). `parity` 0 reads f0 and writes f1, 1 the reverse.
+// The instance record is staged once per item in shared memory.
+template <typename S, typename Real, int K>
+__global__ void __launch_bounds__(256) k_step_list(const ListInst<S, Real>* __restrict__ insts,
+                                                   const int2* __restrict__ work, int nwork, int parity) {
+  constexpr int kWords = sizeof(ListInst<S, Real>) / 4;
+  static_assert(sizeof(ListInst<S, Real>) % 4 == 0, "record must be whole words");
+  static_assert(kWords <= 64, "the smallest block (64 threads) copies the record");
+  __shared__ union {
+    ListInst<S, Real> rec;
+    uint32_t w[kWords];
+  } sh;
+  for (int j = blockIdx.x; j < nwork; j += gridDim.x) {
+    const int2 w = work[j];
+    __syncthreads();  // the previous item's readers are done
+    if (threadIdx.x < kWords)
+      sh.w[threadIdx.x] = reinterpret_cast<const uint32_t*>(insts + w.x)[threadIdx.x];
+    __syncthreads();
+    const ListInst<S, Real>& I = sh.rec;
+    const uint32_t t = uint32_t(w.y) + threadIdx.x;
+    if (t < uint32_t(I.d.ncell)) {
+      const Dims d = I.d;
+      const CellPos p = locate(d, t);
+      const S* fin = parity ? I.f1 : I.f0;
+      S* fout = const_cast<S*>(parity ? I.f0 : I.f1);
+      step_node<S, Real, K>(fin, fout, I.geo, *I.ip, d, p, I.flag);
+    }
   }
-  const int row = K == KELL ? p.ir * d.geo_rows3 + p.i3 : p.ir;
-  const NodeGeo<Real, K> g = load_geo<Real, K>(geo, row);
-  const InstParams<Real> ip = inst[p.b];
-  const Coef<Real> k = coefficients<Real, K>(m, g, ip.kappa, ip.G);
-  collide<Real, K>(f, k, g, ip.omega);
-  store_node(fout + base + p.cell, d.ncell, f);
 }
 
 // rho' and u of the streamed populations (moments only).

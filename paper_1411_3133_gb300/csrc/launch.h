@@ -26,6 +26,21 @@ cudaError_t launch_step_b16(int K, const __nv_bfloat16* fin, __nv_bfloat16* fout
                             const InstParams<float>* inst, const Dims& d, int* flag, int threads,
                             cudaStream_t s);
 
+// Work-list step over instances of different geometry (ListInst<S, R> array);
+// grid 0 launches one block per work item.
+cudaError_t launch_step_list_f64(int K, const void* insts, const int2* work, int nwork, int threads,
+                                 int grid, int parity, cudaStream_t s);
+cudaError_t step_list_occupancy_f64(int K, int threads, int* blocks_per_sm);
+cudaError_t launch_step_list_f32(int K, const void* insts, const int2* work, int nwork, int threads,
+                                 int grid, int parity, cudaStream_t s);
+cudaError_t step_list_occupancy_f32(int K, int threads, int* blocks_per_sm);
+cudaError_t launch_step_list_h16(int K, const void* insts, const int2* work, int nwork, int threads,
+                                 int grid, int parity, cudaStream_t s);
+cudaError_t step_list_occupancy_h16(int K, int threads, int* blocks_per_sm);
+cudaError_t launch_step_list_b16(int K, const void* insts, const int2* work, int nwork, int threads,
+                                 int grid, int parity, cudaStream_t s);
+cudaError_t step_list_occupancy_b16(int K, int threads, int* blocks_per_sm);
+
 // TMA-pipelined FP32 step (n3 in {128, 256}); map is a CUtensorMap over the
 // input state (make_state_tensor_map).
 bool tma_step_supported(const Dims& d);

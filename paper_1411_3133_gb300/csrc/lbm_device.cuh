@@ -306,6 +306,9 @@ __device__ __forceinline__ void store_node(S* __restrict__ out, int N, const R (
 // scalar float instruction. Multiplications by the lattice's integer
 // velocity components are spelled out with compile-time helpers (mac, dot3)
 // so that no multiplication by 0 or +-1 is issued for any type.
+// Every multiply-add is an explicit fmav and the library is compiled with
+// -fmad=false, so the compiler fuses no other product into an add: every
+// kernel that inlines these functions (plain, TMA, work-list) rounds alike.
 struct PF2 {
   float2 v;
   PF2() = default;
@@ -546,8 +549,9 @@ __device__ __forceinline__ void collide_pair(V& fp, V& fm, const Coef<V>& k, con
   V Ft = k.fext_t;
   if constexpr (curv && cx * cy != 0) Ft = mac<2 * cx * cy>(Ft, g.n_trt);
   if constexpr (ell && cy * cz != 0) Ft = mac<2 * cy * cz>(Ft, g.n_ttp);
-  if constexpr (ell && cx * cz != 0) Fz = mulc<2 * cx * cz>(g.n_prp);
-  if constexpr (ell && cy != 0) Fz = (cx * cz != 0) ? mac<cy * cy>(Fz, g.n_ptt) : mulc<cy * cy>(g.n_ptt);
+  if constexpr (ell && cx * cz != 0 && cy != 0) Fz = mac<2 * cx * cz>(mulc<cy * cy>(g.n_ptt), g.n_prp);
+  else if constexpr (ell && cx * cz != 0) Fz = mulc<2 * cx * cz>(g.n_prp);
+  else if constexpr (ell && cy != 0) Fz = mulc<cy * cy>(g.n_ptt);
   // F.c and u.F
   constexpr bool hasFc = cy != 0 || (cx != 0 && hasFr) || (cz != 0 && hasFz);
   V Fc = V(0.0);
@@ -574,10 +578,10 @@ __device__ __forceinline__ void collide_pair(V& fp, V& fm, const Coef<V>& k, con
     Fo = fmav(Fc, fmav(V(-0.5 / CS2), ncAc, k.t0), FnA);
   }
   const V w = V(C::w);
-  const V A = fmav(omega, E, Fe) * w;
-  const V B = fmav(omega, O, Fo) * w;
-  fp = fmav(om1, fp, A + B);
-  fm = fmav(om1, fm, A - B);
+  const V Bw = fmav(omega, O, Fo) * w;
+  const V a = fmav(omega, E, Fe);
+  fp = fmav(om1, fp, fmav(a, w, Bw));
+  fm = fmav(om1, fm, fmav(a, w, -Bw));
 }
 
 template <typename V, int K>

@@ -10,4 +10,13 @@ cudaError_t launch_step_f64(int K, const double* fin, double* fout, const GeoDev
   return launch_step_t<double, double>(K, fin, fout, geo, inst, d, flag, threads, s);
 }
 
+cudaError_t launch_step_list_f64(int K, const void* insts, const int2* work, int nwork, int threads,
+                                 int grid, int parity, cudaStream_t s) {
+  return launch_step_list_t<double, double>(K, insts, work, nwork, threads, grid, parity, s);
+}
+
+cudaError_t step_list_occupancy_f64(int K, int threads, int* blocks_per_sm) {
+  return step_list_occupancy_t<double, double>(K, threads, blocks_per_sm);
+}
+
 }  // namespace lbgm

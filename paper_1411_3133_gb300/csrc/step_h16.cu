@@ -10,4 +10,13 @@ cudaError_t launch_step_h16(int K, const __half* fin, __half* fout, const GeoDev
   return launch_step_t<__half, float>(K, fin, fout, geo, inst, d, flag, threads, s);
 }
 
+cudaError_t launch_step_list_h16(int K, const void* insts, const int2* work, int nwork, int threads,
+                                 int grid, int parity, cudaStream_t s) {
+  return launch_step_list_t<__half, float>(K, insts, work, nwork, threads, grid, parity, s);
+}
+
+cudaError_t step_list_occupancy_h16(int K, int threads, int* blocks_per_sm) {
+  return step_list_occupancy_t<__half, float>(K, threads, blocks_per_sm);
+}
+
 }  // namespace lbgm

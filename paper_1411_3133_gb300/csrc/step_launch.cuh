@@ -22,4 +22,35 @@ cudaError_t launch_step_t(int K, const S* fin, S* fout, const GeoDev<R>& geo, co
   return cudaGetLastError();
 }
 
+// grid 0: one block per work item; otherwise `grid` persistent blocks.
+template <class S, class R>
+cudaError_t launch_step_list_t(int K, const void* insts, const int2* work, int nwork, int threads, int grid,
+                               int parity, cudaStream_t s) {
+  if (nwork == 0) return cudaSuccess;
+  const auto* I = static_cast<const ListInst<S, R>*>(insts);
+  const int g = grid > 0 && grid < nwork ? grid : nwork;
+  switch (K) {
+    case KFLAT: k_step_list<S, R, KFLAT><<<g, threads, 0, s>>>(I, work, nwork, parity); break;
+    case KCYL: k_step_list<S, R, KCYL><<<g, threads, 0, s>>>(I, work, nwork, parity); break;
+    case KELL: k_step_list<S, R, KELL><<<g, threads, 0, s>>>(I, work, nwork, parity); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+// Resident blocks per SM of the work-list kernel at `threads` per block.
+template <class S, class R>
+cudaError_t step_list_occupancy_t(int K, int threads, int* blocks_per_sm) {
+  switch (K) {
+    case KFLAT:
+      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_step_list<S, R, KFLAT>, threads, 0);
+    case KCYL:
+      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_step_list<S, R, KCYL>, threads, 0);
+    case KELL:
+      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_step_list<S, R, KELL>, threads, 0);
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
+
 }  // namespace lbgm

@@ -26,6 +26,7 @@ STATUS_NAMES = {0: "LB_OK", 1: "LB_ERR_ARG", 2: "LB_ERR_CUDA", 3: "LB_ERR_NONFIN
 METRICS = {"flat": 0, "cylindrical": 1, "ellipsoidal": 2}
 PRECISIONS = {"fp64": 0, "fp32": 1, "fp16_shifted": 2, "bf16_shifted": 3}
 LB_OPT_CHECK_EVERY, LB_OPT_BLOCK_THREADS, LB_OPT_USE_GRAPH, LB_OPT_STEP_KERNEL = 0, 1, 2, 3
+LB_OPT_SCHEDULE = 4
 
 
 class lb_geometry_desc(ctypes.Structure):
@@ -47,6 +48,14 @@ class lb_diag(ctypes.Structure):
                 ("mean_vorticity", ctypes.c_double), ("vortex_amp", ctypes.c_double),
                 ("vortex_amp_x3", ctypes.c_double), ("max_speed", ctypes.c_double),
                 ("nonfinite", ctypes.c_longlong), ("step", ctypes.c_longlong)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class lb_tune(ctypes.Structure):
+    _fields_ = [("block_threads", ctypes.c_int), ("schedule", ctypes.c_int),
+                ("ms_per_step", ctypes.c_double)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -87,8 +96,20 @@ SIGNATURES = {
     "lb_diagnostics_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(lb_geometry_desc),
                                               ctypes.c_int, _D, _P, _P, _P,
                                               ctypes.POINTER(lb_diag)]),
+    "lb_autotune": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(lb_tune), ctypes.POINTER(lb_tune),
+                                   ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     "lb_destroy": (None, [_P]),
     "lb_last_error": (ctypes.c_char_p, [_P]),
+    "lb_batch_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.POINTER(_P)]),
+    "lb_batch_step": (ctypes.c_int, [_P, ctypes.c_longlong]),
+    "lb_batch_set_option": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_longlong]),
+    "lb_batch_autotune": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(lb_tune),
+                                         ctypes.POINTER(lb_tune), ctypes.c_int,
+                                         ctypes.POINTER(ctypes.c_int)]),
+    "lb_batch_nodes": (ctypes.c_longlong, [_P]),
+    "lb_batch_step_count": (ctypes.c_longlong, [_P]),
+    "lb_batch_destroy": (None, [_P]),
+    "lb_batch_last_error": (ctypes.c_char_p, [_P]),
 }
 
 _lib = None
@@ -120,6 +141,19 @@ def _check(status, ctx=None):
     if status != LB_OK:
         msg = load_library().lb_last_error(ctx).decode()
         raise LBError(status, msg)
+
+
+def _check_batch(status, batch):
+    if status != LB_OK:
+        raise LBError(status, load_library().lb_batch_last_error(batch).decode())
+
+
+def _tune_call(fn, handle, steps_per_trial, check):
+    best = lb_tune()
+    trials = (lb_tune * 16)()
+    n = ctypes.c_int()
+    check(fn(handle, int(steps_per_trial), ctypes.byref(best), trials, 16, ctypes.byref(n)), handle)
+    return best.as_dict(), [trials[i].as_dict() for i in range(min(n.value, 16))]
 
 
 def _ptr(a):
@@ -340,3 +374,55 @@ class LBContext:
 
     def lb_step_count(self):
         return int(load_library().lb_step_count(self.ctx))
+
+    def lb_autotune(self, steps_per_trial=20):
+        """(best, trials): measured launch configurations; the trial steps
+        advance the simulation."""
+        return _tune_call(load_library().lb_autotune, self.ctx, steps_per_trial, _check)
+
+
+class LBBatch:
+    """One lb_batch over LBContext members that share precision and stream
+    (see include/lbgm.h); the members stay usable on their own."""
+
+    def __init__(self, members):
+        lib = load_library()
+        self.members = list(members)
+        arr = (_P * len(self.members))(*[m.ctx.value for m in self.members])
+        h = ctypes.c_void_p()
+        _check_batch(lib.lb_batch_create(arr, len(self.members), ctypes.byref(h)), None)
+        self.handle = h
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load_library().lb_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def lb_batch_step(self, n=1):
+        _check_batch(load_library().lb_batch_step(self.handle, int(n)), self.handle)
+
+    def lb_batch_set_option(self, option, value):
+        _check_batch(load_library().lb_batch_set_option(self.handle, int(option), int(value)),
+                     self.handle)
+
+    def lb_batch_autotune(self, steps_per_trial=20):
+        return _tune_call(load_library().lb_batch_autotune, self.handle, steps_per_trial,
+                          _check_batch)
+
+    def lb_batch_nodes(self):
+        return int(load_library().lb_batch_nodes(self.handle))
+
+    def lb_batch_step_count(self):
+        return int(load_library().lb_batch_step_count(self.handle))

@@ -120,6 +120,30 @@ def run_sweep(spec: L.ChannelSpec, taus, deans, steps: int, sample_every: int = 
     return res
 
 
+def mixed_contexts(instances, precision="fp32", stream=None, init=True):
+    """One context (batch 1) per workloads.Instance, all on one stream, and
+    the lb_batch over them. Instances start from rest (rho' = 1/sqrt(g)) plus
+    their seeded noise, driven by the force of the target Dean number (the
+    closed form of the cylinder named by workloads.force_reference_cylinder).
+    Returns (contexts, batch)."""
+    import torch
+
+    from .workloads import force_reference_cylinder
+
+    stream = stream if stream is not None else torch.cuda.Stream()
+    ctxs = []
+    for inst in instances:
+        spec = L.ChannelSpec(**inst.geometry_kwargs())
+        ctx = L.LBContext(spec, batch=1, precision=precision, stream=stream)
+        if init:
+            ref = force_reference_cylinder(inst)
+            rdesc = L.make_desc(ref["r_inner"], ref["r_outer"], ref["nr"], ref["ntheta"], ref["n3"])
+            G = L.lb_force_for_dean("cylindrical", rdesc, inst.tau, inst.dean)
+            ctx.lb_init([L.make_params(inst.tau, G, False, inst.seed, inst.noise_amp, False)])
+        ctxs.append(ctx)
+    return ctxs, L.LBBatch(ctxs)
+
+
 def critical_dean_saturation(deans, a_final, floor=None, npoints=4, sat_factor=100.0):
     """De_c from saturated amplitudes: least-squares line A^2 = a (De - De_c)
     through the first `npoints` Dean numbers whose final amplitude exceeds

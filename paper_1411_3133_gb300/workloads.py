@@ -115,3 +115,69 @@ def ellipsoid_cross_section(R2_over_R1=1.0, nr=64, ntheta=4, n3=256, tau=0.55, p
     return Workload(f"ellipsoid_R2_{R2_over_R1:g}", "ellipsoidal", ri, ri + d, nr, ntheta, n3,
                     precision, taus=[tau], deans=[0.0], b=b, periodic3=False,
                     dtheta_scale=1.0 / (b * ri), d3_scale=1.0 / ri, seeds=[BASE_SEED])
+
+
+@dataclass
+class Instance:
+    """One channel of a mixed batch (one context of batch 1)."""
+    metric: str
+    r_inner: float
+    r_outer: float
+    nr: int
+    ntheta: int
+    n3: int
+    tau: float
+    dean: float
+    seed: int
+    b: float = 1.0
+    periodic3: bool = True
+    dtheta_scale: float = 1.0
+    d3_scale: float = 1.0
+    R2_over_R1: float = 0.0
+    noise_amp: float = 1e-4
+
+    @property
+    def ncells(self):
+        return self.nr * self.ntheta * self.n3
+
+    def geometry_kwargs(self):
+        return dict(metric=self.metric, r_inner=self.r_inner, r_outer=self.r_outer, nr=self.nr,
+                    ntheta=self.ntheta, n3=self.n3, b=self.b, periodic3=self.periodic3,
+                    dtheta_scale=self.dtheta_scale, d3_scale=self.d3_scale)
+
+
+def mixed_batch(n=128, seed=BASE_SEED, tau=0.55, eta=0.975, ntheta=4, nr_choices=(32, 48, 64),
+                n3_lo=128, n3_hi=512, de_lo=20.0, de_hi=150.0, ratio_lo=0.25, ratio_hi=4.0):
+    """Mixed sweep of `n` channels: alternately a cylinder (eta = 0.975, as in
+    Sec. III) and a double-curved channel (Sec. IV.B recipe of
+    ellipsoid_cross_section with R2/R1 log-uniform in [ratio_lo, ratio_hi]);
+    N_r uniform over nr_choices, N_3 uniform in [n3_lo, n3_hi], target De
+    uniform in [de_lo, de_hi]. Draws come from numpy's PCG64 seeded with
+    `seed`; instance i gets noise seed BASE_SEED + i."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for i in range(n):
+        nr = int(rng.choice(nr_choices))
+        n3 = int(rng.integers(n3_lo, n3_hi + 1))
+        de = float(rng.uniform(de_lo, de_hi))
+        ratio = float(math.exp(rng.uniform(math.log(ratio_lo), math.log(ratio_hi))))
+        if i % 2 == 0:
+            out.append(Instance("cylindrical", 1.0, 1.0 / eta, nr, ntheta, n3, tau, de, BASE_SEED + i))
+        else:
+            w = ellipsoid_cross_section(ratio, nr, ntheta, n3, tau)
+            out.append(Instance("ellipsoidal", w.r_inner, w.r_outer, nr, ntheta, n3, tau, de,
+                                BASE_SEED + i, b=w.b, periodic3=False, dtheta_scale=w.dtheta_scale,
+                                d3_scale=w.d3_scale, R2_over_R1=ratio))
+    return out
+
+
+def force_reference_cylinder(inst: Instance):
+    """Cylinder whose closed-form force-to-Dean map (lb_force_for_dean) sets
+    the drive of `inst`: the instance itself, or for a double-curved channel
+    the cylinder of the same streamwise radius R1 = 1, width and N_r."""
+    if inst.metric == "cylindrical":
+        return dict(metric="cylindrical", r_inner=inst.r_inner, r_outer=inst.r_outer, nr=inst.nr,
+                    ntheta=inst.ntheta, n3=inst.n3)
+    d = inst.r_outer - inst.r_inner
+    return dict(metric="cylindrical", r_inner=1.0, r_outer=1.0 + d, nr=inst.nr, ntheta=inst.ntheta,
+                n3=inst.n3)

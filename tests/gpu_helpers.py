@@ -32,13 +32,13 @@ class Twin:
     params: list of dicts with keys tau, G, old, seed, amp, base.
     """
 
-    def __init__(self, ch: Channel, params, precision="fp64"):
+    def __init__(self, ch: Channel, params, precision="fp64", stream=None):
         L = lib()
         self.ch = ch
         self.params = params
         self.B = len(params)
         self.N = ch.ncells
-        self.ctx = L.LBContext(spec_of(ch), batch=self.B, precision=precision)
+        self.ctx = L.LBContext(spec_of(ch), batch=self.B, precision=precision, stream=stream)
         self.geo = channel_geometry(ch)
         smap = StreamMap(ch)
         self.sims = [Simulation(ch, Params(p["tau"], p.get("G", 0.0), p.get("old", False)),

@@ -2,6 +2,7 @@
 function include/lbgm.h declares, and its host-side logic (velocity table,
 FP64 geometry precompute, force for a Dean number, argument validation)
 agrees with the oracle and the closed forms."""
+import ctypes
 import math
 import os
 import re
@@ -128,3 +129,19 @@ def test_splitmix64_reference_recurrence():
         seq.append(z ^ (z >> 31))
     got = splitmix64_at(seed, np.arange(6, dtype=np.uint64))
     assert [int(v) for v in got] == seq
+
+
+def test_batch_entry_points_reject_bad_arguments_without_a_gpu(L):
+    lib = L.load_library()
+    out = ctypes.c_void_p(123)
+    assert lib.lb_batch_create(None, 0, ctypes.byref(out)) == L.LB_ERR_ARG
+    arr = (ctypes.c_void_p * 1)(None)
+    assert lib.lb_batch_create(arr, 0, ctypes.byref(out)) == L.LB_ERR_ARG
+    assert out.value is None                      # cleared on failure
+    assert lib.lb_batch_create(arr, 1, ctypes.byref(out)) == L.LB_ERR_ARG
+    assert b"NULL" in lib.lb_batch_last_error(None)
+    assert lib.lb_batch_step(None, 1) == L.LB_ERR_ARG
+    assert lib.lb_batch_set_option(None, 0, 0) == L.LB_ERR_ARG
+    assert lib.lb_batch_nodes(None) == -1 and lib.lb_batch_step_count(None) == -1
+    lib.lb_batch_destroy(None)
+    assert lib.lb_autotune(None, 1, None, None, 0, None) == L.LB_ERR_ARG

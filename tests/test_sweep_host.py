@@ -38,3 +38,26 @@ def test_critical_dean_from_saturated_amplitude():
     a = np.where(de > dec, np.sqrt(np.clip(2e-7 * (de - dec), 0, None)), 3e-7)
     assert critical_dean_saturation(de, a) == pytest.approx(dec, rel=1e-9)
     assert np.isnan(critical_dean_saturation(de, np.full(6, 3e-7)))
+
+
+def test_mixed_batch_recipe_is_seeded_and_in_range():
+    from paper_1411_3133_gb300.workloads import BASE_SEED, force_reference_cylinder, mixed_batch
+    a, b = mixed_batch(), mixed_batch()
+    assert a == b                                          # seeded
+    assert len(a) == 128
+    assert sum(i.metric == "cylindrical" for i in a) == 64
+    for k, inst in enumerate(a):
+        assert inst.nr in (32, 48, 64) and 128 <= inst.n3 <= 512 and inst.ntheta == 4
+        assert 20.0 <= inst.dean <= 150.0 and inst.tau == 0.55 and inst.seed == BASE_SEED + k
+        ref = force_reference_cylinder(inst)
+        assert ref["metric"] == "cylindrical" and ref["nr"] == inst.nr
+        if inst.metric == "ellipsoidal":
+            assert 0.25 <= inst.R2_over_R1 <= 4.0 and not inst.periodic3
+            # Sec. IV.B recipe: R_theta = r_i b^2 = 1, d = R1/40
+            assert inst.r_inner * inst.b ** 2 == pytest.approx(1.0)
+            assert inst.r_outer - inst.r_inner == pytest.approx(1 / 40)
+            assert ref["r_outer"] - ref["r_inner"] == pytest.approx(1 / 40)
+    total = sum(i.ncells for i in a)
+    assert 7.0e6 < total < 9.5e6                           # about 7.9 M nodes expected
+    ratios = np.log([i.R2_over_R1 for i in a if i.metric == "ellipsoidal"])
+    assert ratios.min() < np.log(0.5) and ratios.max() > np.log(2.0)   # spans the range
