@@ -131,28 +131,38 @@ typedef enum {
   LB_OPT_CHECK_EVERY = 0,   /* lb_step checks for non-finite values every k
                                steps (k >= 0; 0: never; default 0) */
   LB_OPT_BLOCK_THREADS = 1, /* threads per block of the step kernel
-                               (64..256, multiple of 32; default 128) */
+                               (64..256, multiple of 32; default 128). The
+                               one-node-per-thread kernel with FP32
+                               arithmetic runs at most 128 per block (its
+                               register cap); larger values run as 128 */
   LB_OPT_USE_GRAPH = 2,     /* 1: lb_step replays a captured CUDA graph of
                                pairs of steps (default 0) */
   LB_OPT_STEP_KERNEL = 3,   /* 0: automatic (default: the one-node-per-
-                               thread kernel, the fastest measured); 1: that
-                               kernel, gathering from global memory; 2: the
-                               TMA-pipelined kernel (FP32 and n3 in {128,
-                               256} only; LB_ERR_ARG otherwise). Both give
-                               bitwise identical states. */
-  LB_OPT_SCHEDULE = 4       /* batches only (lb_batch_set_option): 0: one
+                               thread kernel); 1: that kernel, gathering
+                               from global memory; 2: the TMA-pipelined
+                               kernel (FP32 and n3 in {128, 256} only);
+                               3: the prefetching kernel: each thread updates
+                               LB_OPT_NODES_PER_THREAD nodes and copies the
+                               next node's sources into shared memory
+                               (cp.async) while it computes the current one.
+                               Unsupported choices return LB_ERR_ARG. All
+                               give bitwise identical states. */
+  LB_OPT_SCHEDULE = 4,      /* batches only (lb_batch_set_option): 0: one
                                block per tile of block_threads nodes
                                (default); 1: a persistent grid of (resident
                                blocks per SM) x (SMs) blocks that walks the
                                tile list. Both give bitwise identical
                                states. */
+  LB_OPT_NODES_PER_THREAD = 5 /* nodes per thread of the prefetching step
+                               kernel (1..64; default 4) */
 } lb_option;
 
 /* One configuration measured by lb_autotune / lb_batch_autotune. */
 typedef struct {
   int block_threads;   /* LB_OPT_BLOCK_THREADS */
-  int schedule;        /* contexts: LB_OPT_STEP_KERNEL (1 or 2);
+  int schedule;        /* contexts: LB_OPT_STEP_KERNEL (1, 2 or 3);
                           batches: LB_OPT_SCHEDULE (0 or 1) */
+  int nodes_per_thread; /* LB_OPT_NODES_PER_THREAD (prefetching kernel) */
   double ms_per_step;  /* measured with CUDA events on the stream */
 } lb_tune;
 
@@ -188,7 +198,9 @@ lb_status lb_force_for_dean(lb_metric metric, const lb_geometry_desc* geom,
  * `cuda_stream` (a cudaStream_t; NULL: the library creates its own stream).
  * Evaluates the geometry on the host in FP64 (lb_geometry_eval) and uploads
  * it. `alloc` may be NULL (cudaMalloc). On success *out owns its memory
- * until lb_destroy. */
+ * until lb_destroy. Limits (LB_ERR_ARG beyond them): batch <= 65535,
+ * batch * nodes < 2^32, and one instance's populations (41 * nodes * bytes
+ * per population) below 4 GiB. */
 lb_status lb_create_geometry(lb_metric metric, const lb_geometry_desc* geom,
                              int batch, lb_precision prec, void* cuda_stream,
                              const lb_allocator* alloc, lb_ctx** out);
@@ -267,8 +279,11 @@ lb_status lb_diagnostics_noalloc(lb_metric metric, const lb_geometry_desc* geom,
                                  void* cuda_stream, lb_diag* out);
 
 /* Autotuner of the step launch. Runs steps_per_trial (>= 1) time steps in
- * each configuration -- block_threads in {64, 128, 192, 256} with the plain
- * step kernel, and the TMA kernel where the context supports it -- timed with
+ * each configuration -- block_threads in {64, 96, 128} (FP64: {64, 128, 192,
+ * 256}) with the plain step kernel, the TMA kernel where the context
+ * supports it, and the
+ * prefetching kernel with block_threads in {128, 256} x
+ * nodes_per_thread in {2, 4, 8} -- timed with
  * CUDA events on the context's stream, then keeps the fastest. Every
  * configuration computes bitwise the same states, so the trial steps are
  * real time steps: they advance the simulation and the step count. best

@@ -193,7 +193,24 @@ bool use_tma(const lb_ctx* c) { return c->prec == LB_FP32 && c->tma_ok && c->ste
 lb_status launch_step_once(lb_ctx* c) {
   const int src = c->cur, dst = 1 - c->cur;
   cudaError_t e;
-  if (use_tma(c))
+  if (c->step_kernel == 3 && c->prec == LB_FP32)
+    e = launch_step_async_f32(c->K, static_cast<const float*>(c->f[src]), static_cast<float*>(c->f[dst]),
+                              c->geo_f, static_cast<const InstParams<float>*>(c->inst), c->dims, c->flag,
+                              c->block_threads, c->nodes_per_thread, c->stream);
+  else if (c->step_kernel == 3 && c->prec == LB_FP64)
+    e = launch_step_async_f64(c->K, static_cast<const double*>(c->f[src]), static_cast<double*>(c->f[dst]),
+                              c->geo_d, static_cast<const InstParams<double>*>(c->inst), c->dims, c->flag,
+                              c->block_threads, c->nodes_per_thread, c->stream);
+  else if (c->step_kernel == 3 && c->prec == LB_FP16_SHIFTED)
+    e = launch_step_async_h16(c->K, static_cast<const __half*>(c->f[src]), static_cast<__half*>(c->f[dst]),
+                              c->geo_f, static_cast<const InstParams<float>*>(c->inst), c->dims, c->flag,
+                              c->block_threads, c->nodes_per_thread, c->stream);
+  else if (c->step_kernel == 3)
+    e = launch_step_async_b16(c->K, static_cast<const __nv_bfloat16*>(c->f[src]),
+                              static_cast<__nv_bfloat16*>(c->f[dst]), c->geo_f,
+                              static_cast<const InstParams<float>*>(c->inst), c->dims, c->flag,
+                              c->block_threads, c->nodes_per_thread, c->stream);
+  else if (use_tma(c))
     e = launch_step_tma_f32(c->K, c->tmap[src], static_cast<const float*>(c->f[src]),
                             static_cast<float*>(c->f[dst]), c->geo_f,
                             static_cast<const InstParams<float>*>(c->inst), c->dims, c->flag, c->stream);
@@ -308,6 +325,10 @@ lb_status lb_create_geometry(lb_metric metric, const lb_geometry_desc* geom, int
   if (alloc && (!alloc->alloc || !alloc->free)) return fail(nullptr, LB_ERR_ARG, "allocator needs alloc and free");
   const double total = double(batch) * geom->nr * geom->ntheta * geom->n3;
   if (total >= 4294967295.0) return fail(nullptr, LB_ERR_ARG, "batch * nodes must fit in uint32");
+  if (batch > 65535) return fail(nullptr, LB_ERR_ARG, "need batch <= 65535 (one grid row per instance)");
+  const double inst_bytes = double(Q) * geom->nr * geom->ntheta * geom->n3 * (prec == LB_FP64 ? 8 : prec == LB_FP32 ? 4 : 2);
+  if (inst_bytes >= 4294967296.0)
+    return fail(nullptr, LB_ERR_ARG, "one instance's populations must stay below 4 GiB (32-bit offsets)");
   if (std::fabs(SQRT10 * SQRT10 - 10.0) > 1e-14 || std::fabs(SQRT10 - std::sqrt(10.0)) > 1e-15)
     return fail(nullptr, LB_ERR_ARG, "internal constant check failed");
 
@@ -366,8 +387,9 @@ lb_status lb_create_geometry(lb_metric metric, const lb_geometry_desc* geom, int
   const size_t nrows = size_t(geom->nr) * d.geo_rows3;
   const size_t nrow64 = size_t(geom->nr) * geom->n3;
   c->nblk = int(std::min<size_t>(1024, (c->ncell + 255) / 256));
-  c->f[0] = dalloc(c, c->state_elems * c->elem_bytes);
-  c->f[1] = dalloc(c, c->state_elems * c->elem_bytes);
+  // 16 bytes of padding: the prefetching kernel copies whole 4-byte words
+  c->f[0] = dalloc(c, c->state_elems * c->elem_bytes + 16);
+  c->f[1] = dalloc(c, c->state_elems * c->elem_bytes + 16);
   c->geo_real = dalloc(c, 9 * nrows * (prec == LB_FP64 ? sizeof(double) : sizeof(float)));
   c->geo64 = static_cast<double*>(dalloc(c, nrow64 * 4 * sizeof(double)));
   c->sqrtg = static_cast<double*>(dalloc(c, nrow64 * sizeof(double)));
@@ -491,7 +513,8 @@ lb_status lb_step(lb_ctx* c, long long n) {
       ++c->step;
       --n;
     }
-    if (!c->graph || c->graph_threads != c->block_threads || c->graph_kernel != c->step_kernel) {
+    if (!c->graph || c->graph_threads != c->block_threads || c->graph_kernel != c->step_kernel ||
+        c->graph_npt != c->nodes_per_thread) {
       if (c->graph) cudaGraphExecDestroy(c->graph);
       c->graph = nullptr;
       cudaGraph_t g = nullptr;
@@ -506,6 +529,7 @@ lb_status lb_step(lb_ctx* c, long long n) {
       if (e != cudaSuccess) return cuda_fail(c, e, "cudaGraphInstantiate");
       c->graph_threads = c->block_threads;
       c->graph_kernel = c->step_kernel;
+      c->graph_npt = c->nodes_per_thread;
     }
     for (long long i = 0; i + 1 < n; i += 2) {
       LB_CUDA(c, cudaGraphLaunch(c->graph, c->stream));
@@ -660,10 +684,15 @@ lb_status lb_set_option(lb_ctx* c, int option, long long value) {
       c->use_graph = value ? 1 : 0;
       return LB_OK;
     case LB_OPT_STEP_KERNEL:
-      if (value < 0 || value > 2) return fail(c, LB_ERR_ARG, "need 0 (auto), 1 (plain) or 2 (TMA)");
+      if (value < 0 || value > 3)
+        return fail(c, LB_ERR_ARG, "need 0 (auto), 1 (plain), 2 (TMA) or 3 (prefetching)");
       if (value == 2 && !c->tma_ok)
         return fail(c, LB_ERR_ARG, "the TMA step kernel needs FP32 and n3 in {128, 256}");
       c->step_kernel = int(value);
+      return LB_OK;
+    case LB_OPT_NODES_PER_THREAD:
+      if (value < 1 || value > 64) return fail(c, LB_ERR_ARG, "need 1..64 nodes per thread");
+      c->nodes_per_thread = int(value);
       return LB_OK;
     default:
       return fail(c, LB_ERR_ARG, "unknown option");
@@ -679,8 +708,13 @@ lb_status lb_autotune(lb_ctx* c, int steps_per_trial, lb_tune* best, lb_tune* tr
   if (steps_per_trial < 1) return fail(c, LB_ERR_ARG, "need steps_per_trial >= 1");
   if (max_trials < 0 || (max_trials > 0 && !trials)) return fail(c, LB_ERR_ARG, "bad trials buffer");
   std::vector<lb_tune> cand;
-  for (int t : {64, 128, 192, 256}) cand.push_back({t, 1, 0.0});
-  if (c->tma_ok) cand.push_back({0, 2, 0.0});  // the TMA kernel fixes its own block shape
+  if (c->prec == LB_FP64)
+    for (int t : {64, 128, 192, 256}) cand.push_back({t, 1, 0, 0.0});
+  else
+    for (int t : {64, 96, 128}) cand.push_back({t, 1, 0, 0.0});
+  if (c->tma_ok) cand.push_back({0, 2, 0, 0.0});  // the TMA kernel fixes its own block shape
+  for (int t : {128, 256})
+    for (int npt : {2, 4, 8}) cand.push_back({t, 3, npt, 0.0});
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   LB_CUDA(c, cudaEventCreate(&e0));
   cudaError_t e = cudaEventCreate(&e1);
@@ -688,11 +722,12 @@ lb_status lb_autotune(lb_ctx* c, int steps_per_trial, lb_tune* best, lb_tune* tr
     cudaEventDestroy(e0);
     return cuda_fail(c, e, "cudaEventCreate");
   }
-  const int keep_threads = c->block_threads;
+  const int keep_threads = c->block_threads, keep_npt = c->nodes_per_thread;
   lb_status st = LB_OK;
   for (lb_tune& k : cand) {
     c->block_threads = k.block_threads > 0 ? k.block_threads : keep_threads;
     c->step_kernel = k.schedule;
+    c->nodes_per_thread = k.nodes_per_thread > 0 ? k.nodes_per_thread : keep_npt;
     for (int i = 0; i <= steps_per_trial && st == LB_OK; ++i) {  // step 0 is the untimed warm-up
       if (i == 1 && (e = cudaEventRecord(e0, c->stream)) != cudaSuccess) st = cuda_fail(c, e, "cudaEventRecord");
       if (st == LB_OK) st = launch_step_once(c);
@@ -713,10 +748,13 @@ lb_status lb_autotune(lb_ctx* c, int steps_per_trial, lb_tune* best, lb_tune* tr
   for (size_t i = 1; i < cand.size(); ++i)
     if (cand[i].ms_per_step < cand[ib].ms_per_step) ib = i;
   if (cand[ib].block_threads == 0) cand[ib].block_threads = keep_threads;
-  for (lb_tune& k : cand)
+  for (lb_tune& k : cand) {
     if (k.block_threads == 0) k.block_threads = keep_threads;
+    if (k.nodes_per_thread == 0) k.nodes_per_thread = keep_npt;
+  }
   c->block_threads = cand[ib].block_threads;
   c->step_kernel = cand[ib].schedule;
+  c->nodes_per_thread = cand[ib].nodes_per_thread;
   if (best) *best = cand[ib];
   const int n = int(cand.size());
   for (int i = 0; i < n && i < max_trials; ++i) trials[i] = cand[i];

@@ -118,15 +118,6 @@ void append_records(const lb_batch* b, int K, std::vector<unsigned char>& bytes,
   }
 }
 
-size_t record_bytes(lb_precision p) {
-  switch (p) {
-    case LB_FP64: return sizeof(ListInst<double, double>);
-    case LB_FP32: return sizeof(ListInst<float, float>);
-    case LB_FP16_SHIFTED: return sizeof(ListInst<__half, float>);
-    default: return sizeof(ListInst<__nv_bfloat16, float>);
-  }
-}
-
 cudaError_t occupancy(lb_precision p, int K, int threads, int* out) {
   switch (p) {
     case LB_FP64: return step_list_occupancy_f64(K, threads, out);
@@ -396,7 +387,7 @@ lb_status lb_batch_autotune(lb_batch* b, int steps_per_trial, lb_tune* best, lb_
   if (max_trials < 0 || (max_trials > 0 && !trials)) return bfail(b, LB_ERR_ARG, "bad trials buffer");
   std::vector<lb_tune> cand;
   for (int t : {64, 128, 192, 256})
-    for (int sc : {0, 1}) cand.push_back({t, sc, 0.0});
+    for (int sc : {0, 1}) cand.push_back({t, sc, 0, 0.0});
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   LB_BCUDA(b, cudaEventCreate(&e0));
   cudaError_t e = cudaEventCreate(&e1);

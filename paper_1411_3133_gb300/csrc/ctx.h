@@ -62,6 +62,8 @@ struct lb_ctx {
   int graph_threads = 0;
   int graph_kernel = -1;
   int step_kernel = 0;               // LB_OPT_STEP_KERNEL
+  int nodes_per_thread = 4;          // LB_OPT_NODES_PER_THREAD
+  int graph_npt = 0;
   bool tma_ok = false;               // tensor maps built for both buffers
   alignas(64) unsigned char tmap[2][128];
 };

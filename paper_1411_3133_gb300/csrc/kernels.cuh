@@ -7,16 +7,14 @@
 
 namespace lbgm {
 
-// Fused time step (Eq. LB) of one node p of one instance whose state blocks
-// start at fin and fout: pull streaming + walls, moments, equilibrium,
-// non-equilibrium stress, forcing, BGK, store. flag is set to 1 when the
-// node's density is not finite.
+// Collision half of the fused step (Eq. LB) for node p whose streamed
+// populations are in f: moments, equilibrium, non-equilibrium stress,
+// forcing, BGK, store into the instance block fout. flag is set to 1 when
+// the node's density is not finite.
 template <typename S, typename Real, int K>
-__device__ __forceinline__ void step_node(const S* __restrict__ fin, S* __restrict__ fout,
-                                          const GeoDev<Real>& geo, const InstParams<Real>& ip, const Dims& d,
-                                          const CellPos& p, int* __restrict__ flag) {
-  Real f[Q];
-  gather(fin, p, d, f);
+__device__ __forceinline__ void collide_store(Real (&f)[Q], S* __restrict__ fout, const GeoDev<Real>& geo,
+                                              const InstParams<Real>& ip, const Dims& d, const CellPos& p,
+                                              int* __restrict__ flag) {
   const Moments<Real> m = moments(f);
   if (!finite_v(m.rho)) {  // NaN or Inf
     if (*flag == 0) atomicExch(flag, 1);
@@ -25,19 +23,58 @@ __device__ __forceinline__ void step_node(const S* __restrict__ fin, S* __restri
   const NodeGeo<Real, K> g = load_geo<Real, K>(geo, row);
   const Coef<Real> k = coefficients<Real, K>(m, g, ip.kappa, ip.G);
   collide<Real, K>(f, k, g, ip.omega);
-  store_node(fout + p.cell, d.ncell, f);
+  store_node(fout, uint32_t(p.cell), uint32_t(d.ncell), f);
 }
 
-// Uniform batch: fin/fout are whole states (batch blocks of Q * ncell).
+// Fused time step of one node p of one instance whose state blocks start at
+// fin and fout: pull streaming + walls, then collide_store.
 template <typename S, typename Real, int K>
-__global__ void __launch_bounds__(256) k_step(const S* __restrict__ fin, S* __restrict__ fout,
+__device__ __forceinline__ void step_node(const S* __restrict__ fin, S* __restrict__ fout,
+                                          const GeoDev<Real>& geo, const InstParams<Real>& ip, const Dims& d,
+                                          const CellPos& p, int* __restrict__ flag) {
+  Real f[Q];
+  gather(fin, p, d, f);
+  collide_store<S, Real, K>(f, fout, geo, ip, d, p, flag);
+}
+
+// Uniform batch: fin/fout are whole states (batch blocks of Q * ncell);
+// block (x, y) updates nodes [x blockDim, (x + 1) blockDim) of instance y, so
+// the instance's block base is uniform across the thread block.
+// Launch bounds of k_step per storage / compute type. FP32 arithmetic: at
+// most 128 threads per block and 6 (FP32 storage) or 7 (2-byte storage)
+// resident blocks per SM, i.e. a register cap that trades a few spilled
+// values for more resident warps (the kernel is bound by latency and issue,
+// not by HBM alone; measured best of 5..8). FP64 keeps its registers (bound
+// by the FP64 units). LBGM_STEP32_MAXT / LBGM_STEP32_MINB / LBGM_STEP16_MINB
+// override the FP32 values for tuning builds.
+#ifndef LBGM_STEP32_MAXT
+#define LBGM_STEP32_MAXT 128
+#endif
+#ifndef LBGM_STEP32_MINB
+#define LBGM_STEP32_MINB 6
+#endif
+#ifndef LBGM_STEP16_MINB
+#define LBGM_STEP16_MINB 7
+#endif
+template <class S, class Real>
+struct StepBounds {
+  static constexpr int maxt = LBGM_STEP32_MAXT;
+  static constexpr int minb = sizeof(S) == 2 ? LBGM_STEP16_MINB : LBGM_STEP32_MINB;
+};
+template <>
+struct StepBounds<double, double> {
+  static constexpr int maxt = 256, minb = 1;
+};
+template <typename S, typename Real, int K>
+__global__ void __launch_bounds__(StepBounds<S, Real>::maxt, StepBounds<S, Real>::minb) k_step(const S* __restrict__ fin, S* __restrict__ fout,
                                               GeoDev<Real> geo, const InstParams<Real>* __restrict__ inst,
                                               Dims d, int* __restrict__ flag) {
-  const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= uint32_t(d.batch) * uint32_t(d.ncell)) return;
-  const CellPos p = locate(d, t);
-  const size_t base = size_t(p.b) * Q * d.ncell;
-  step_node<S, Real, K>(fin + base, fout + base, geo, inst[p.b], d, p, flag);
+  const uint32_t cell = blockIdx.x * blockDim.x + threadIdx.x;
+  if (cell >= uint32_t(d.ncell)) return;
+  const int b = int(blockIdx.y);
+  const CellPos p = locate_cell(d, b, cell);
+  const size_t base = size_t(b) * Q * uint32_t(d.ncell);
+  step_node<S, Real, K>(fin + base, fout + base, geo, inst[b], d, p, flag);
 }
 
 // One instance of a batch whose instances differ in geometry and size: its
@@ -84,6 +121,111 @@ __global__ void __launch_bounds__(256) k_step_list(const ListInst<S, Real>* __re
       step_node<S, Real, K>(fin, fout, I.geo, *I.ip, d, p, I.flag);
     }
   }
+}
+
+// cp.async of one 4- or 8-byte element from global into shared memory.
+template <class Real>
+__device__ __forceinline__ void cp_async_elem(Real* smem_dst, const Real* gsrc) {
+  static_assert(sizeof(Real) == 4 || sizeof(Real) == 8, "cp.async copies 4, 8 or 16 bytes");
+  const uint32_t dst = uint32_t(__cvta_generic_to_shared(smem_dst));
+  if constexpr (sizeof(Real) == 4)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(gsrc) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Unit copied per population by the prefetching kernel: the element itself
+// (4 or 8 bytes), or for 2-byte storage the aligned 4-byte word holding it
+// (cp.async has no 2-byte form); the state buffers carry 16 bytes of padding
+// so that the word of the last element stays inside the allocation.
+template <class S>
+struct AsyncUnit {
+  using T = S;
+  static constexpr bool half = false;
+};
+template <>
+struct AsyncUnit<__half> {
+  using T = uint32_t;
+  static constexpr bool half = true;
+  __device__ static __forceinline__ __half from_bits(unsigned short b) { return __ushort_as_half(b); }
+};
+template <>
+struct AsyncUnit<__nv_bfloat16> {
+  using T = uint32_t;
+  static constexpr bool half = true;
+  __device__ static __forceinline__ __nv_bfloat16 from_bits(unsigned short b) { return __ushort_as_bfloat16(b); }
+};
+
+// Prefetching step: thread j of block B updates the nodes
+// (B npt + k) blockDim + j, k = 0 .. npt - 1. While node k is computed, the 41
+// sources of node k + 1 are already being copied (cp.async) into the thread's
+// own shared-memory slots [buffer][l][j], so the next node's loads are in
+// flight during the arithmetic without holding registers. A thread reads only
+// slots it filled itself after its own wait_group: no block barrier. For
+// 2-byte storage a 64-bit mask records which half of each copied word holds
+// the population. Shared memory: 2 * Q * blockDim * sizeof(unit) bytes.
+template <typename S, typename Real, int K>
+__global__ void __launch_bounds__(256) k_step_async(const S* __restrict__ fin, S* __restrict__ fout,
+                                                    GeoDev<Real> geo, const InstParams<Real>* __restrict__ inst,
+                                                    Dims d, int npt, int* __restrict__ flag) {
+  using U = typename AsyncUnit<S>::T;
+  using Cd = Codec<S, Real>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  U* sm = reinterpret_cast<U*>(smem_raw);
+  const uint32_t bd = blockDim.x, tid = threadIdx.x;
+  const uint32_t total = uint32_t(d.batch) * uint32_t(d.ncell);
+  const uint32_t first = blockIdx.x * uint32_t(npt) * bd + tid;
+  uint64_t sel_next = 0;
+  auto issue = [&](uint32_t t, uint32_t buf) {
+    if (t >= total) return;
+    const CellPos p = locate(d, t);
+    U* slot = sm + buf * Q * bd + tid;
+    for_each_source(fin + size_t(p.b) * Q * d.ncell, p, d, [&](auto L_, const S* src) {
+      constexpr int L = decltype(L_)::value;
+      if constexpr (AsyncUnit<S>::half) {
+        const uintptr_t a = reinterpret_cast<uintptr_t>(src);
+        sel_next |= uint64_t((a >> 1) & 1u) << L;
+        cp_async_elem(slot + L * bd, reinterpret_cast<const uint32_t*>(a & ~uintptr_t(3)));
+      } else {
+        cp_async_elem(slot + L * bd, src);
+      }
+    });
+  };
+  issue(first, 0);
+  cp_async_commit();
+  for (int k = 0; k < npt; ++k) {
+    const uint32_t t = first + uint32_t(k) * bd;
+    if (t >= total) break;  // later nodes of this thread are out of range too
+    const uint64_t sel = sel_next;
+    sel_next = 0;
+    if (k + 1 < npt) {
+      issue(t + bd, uint32_t(k + 1) & 1u);
+      cp_async_commit();
+      cp_async_wait<1>();  // node k's group has landed
+    } else {
+      cp_async_wait<0>();
+    }
+    const CellPos p = locate(d, t);
+    const U* slot = sm + (uint32_t(k) & 1u) * Q * bd + tid;
+    Real f[Q];
+    static_for<0, Q>([&](auto L_) {
+      constexpr int L = decltype(L_)::value;
+      const U w = slot[L * bd];
+      if constexpr (AsyncUnit<S>::half) {
+        const unsigned short h = (sel >> L) & 1u ? (unsigned short)(w >> 16) : (unsigned short)(w & 0xffffu);
+        f[L] = Cd::template dec<L>(AsyncUnit<S>::from_bits(h));
+      } else {
+        f[L] = Cd::template dec<L>(w);
+      }
+    });
+    collide_store<S, Real, K>(f, fout + size_t(p.b) * Q * d.ncell, geo, inst[p.b], d, p, flag);
+  }
+  cp_async_wait<0>();  // nothing of this thread stays in flight at exit
 }
 
 // rho' and u of the streamed populations (moments only).
@@ -155,7 +297,7 @@ __global__ void __launch_bounds__(256) k_init(S* __restrict__ f, GeoDev<Real> ge
   const NodeGeo<Real, K> g = load_geo<Real, K>(geo, row);
   Real fe[Q];
   equilibrium<Real, K>(Real(rho), Real(u[0]), Real(u[1]), Real(u[2]), g, fe);
-  store_node(f + size_t(p.b) * Q * d.ncell + p.cell, d.ncell, fe);
+  store_node(f + size_t(p.b) * Q * d.ncell, uint32_t(p.cell), uint32_t(d.ncell), fe);
 }
 
 }  // namespace lbgm

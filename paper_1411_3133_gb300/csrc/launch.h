@@ -41,6 +41,21 @@ cudaError_t launch_step_list_b16(int K, const void* insts, const int2* work, int
                                  int grid, int parity, cudaStream_t s);
 cudaError_t step_list_occupancy_b16(int K, int threads, int* blocks_per_sm);
 
+// Prefetching step kernel (cp.async into shared memory); each thread updates
+// npt nodes.
+cudaError_t launch_step_async_f32(int K, const float* fin, float* fout, const GeoDev<float>& geo,
+                                  const InstParams<float>* inst, const Dims& d, int* flag, int threads,
+                                  int npt, cudaStream_t s);
+cudaError_t launch_step_async_f64(int K, const double* fin, double* fout, const GeoDev<double>& geo,
+                                  const InstParams<double>* inst, const Dims& d, int* flag, int threads,
+                                  int npt, cudaStream_t s);
+cudaError_t launch_step_async_h16(int K, const __half* fin, __half* fout, const GeoDev<float>& geo,
+                                  const InstParams<float>* inst, const Dims& d, int* flag, int threads,
+                                  int npt, cudaStream_t s);
+cudaError_t launch_step_async_b16(int K, const __nv_bfloat16* fin, __nv_bfloat16* fout,
+                                  const GeoDev<float>& geo, const InstParams<float>* inst, const Dims& d,
+                                  int* flag, int threads, int npt, cudaStream_t s);
+
 // TMA-pipelined FP32 step (n3 in {128, 256}); map is a CUtensorMap over the
 // input state (make_state_tensor_map).
 bool tma_step_supported(const Dims& d);

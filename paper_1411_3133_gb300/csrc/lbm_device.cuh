@@ -78,6 +78,18 @@ struct CellPos {
   int b, cell, ir, it, i3;
 };
 
+// Position of node `cell` of instance b.
+__device__ __forceinline__ CellPos locate_cell(const Dims& d, int b, uint32_t cell) {
+  CellPos p;
+  p.b = b;
+  p.cell = int(cell);
+  uint32_t row = d.div_n3.div(cell);
+  p.i3 = p.cell - int(row) * d.n3;
+  p.ir = int(d.div_nt.div(row));
+  p.it = int(row) - p.ir * d.nt;
+  return p;
+}
+
 __device__ __forceinline__ CellPos locate(const Dims& d, uint32_t t) {
   CellPos p;
   p.b = int(d.div_ncell.div(t));
@@ -243,57 +255,63 @@ __device__ __forceinline__ bool near_wall(const CellPos& p, const Dims& d) {
   return p.ir < 3 || p.ir > d.nr - 4 || (!d.periodic3 && (p.i3 < 3 || p.i3 > d.n3 - 4));
 }
 
-// Streamed populations of a node near a wall: every moving population from
-// its (possibly folded) source, read from the post-collision state fin.
-// Opposite velocities share their weight, so a folded population decodes
+// Visit the sources of the 41 streamed populations of node p: fn(L, src)
+// with L a std::integral_constant (the population received) and src the
+// address in fin (one instance's block: population l of cell c at
+// fin[l * ncell + c]) of the post-collision value it is streamed from. Near a
+// wall every moving population comes from its (possibly folded) source;
+// opposite velocities share their weight, so a folded population decodes
 // with the weight of the pair.
-template <class S, class R>
-__device__ __forceinline__ void gather_wall(const S* __restrict__ fin, const CellPos& p,
-                                            const Dims& d, R (&f)[Q]) {
-  using Cd = Codec<S, R>;
-  const int N = d.ncell;
-  static_for<0, NPAIR>([&](auto P_) {
-    constexpr int P = decltype(P_)::value;
-    using C = Pair<P>;
-    bool fp, fm;
-    const int sp = src_wall<C::x, C::y, C::z, C::s>(p, d, fp);
-    const int sm = src_wall<-C::x, -C::y, -C::z, C::s>(p, d, fm);
-    f[2 * P + 1] = Cd::template dec<2 * P + 1>(__ldg(fin + (fp ? 2 * P + 2 : 2 * P + 1) * N + sp));
-    f[2 * P + 2] = Cd::template dec<2 * P + 2>(__ldg(fin + (fm ? 2 * P + 1 : 2 * P + 2) * N + sm));
-  });
-}
-
-// Load the 41 streamed populations of node p from the post-collision state
-// fin (one instance's block: population l of cell c at fin[l * ncell + c]).
-template <class S, class R>
-__device__ __forceinline__ void gather(const S* __restrict__ fin, const CellPos& p,
-                                       const Dims& d, R (&f)[Q]) {
-  using Cd = Codec<S, R>;
-  const int N = d.ncell;
-  f[0] = Cd::template dec<0>(__ldg(fin + p.cell));
+// Offsets are 32-bit: an instance block holds fewer than 2^32 bytes
+// (checked when the context is created).
+template <class S, class Fn>
+__device__ __forceinline__ void for_each_source(const S* __restrict__ fin, const CellPos& p, const Dims& d,
+                                                Fn&& fn) {
+  const uint32_t N = uint32_t(d.ncell);
+  fn(std::integral_constant<int, 0>{}, fin + uint32_t(p.cell));
   if (!near_wall(p, d)) {
     Neighbours nb;
     make_neighbours(p, d, nb);
     static_for<0, NPAIR>([&](auto P_) {
       constexpr int P = decltype(P_)::value;
       using C = Pair<P>;
-      const int sp = src_far<C::x, C::y, C::z>(nb, d);
-      const int sm = src_far<-C::x, -C::y, -C::z>(nb, d);
-      f[2 * P + 1] = Cd::template dec<2 * P + 1>(__ldg(fin + (2 * P + 1) * N + sp));
-      f[2 * P + 2] = Cd::template dec<2 * P + 2>(__ldg(fin + (2 * P + 2) * N + sm));
+      const uint32_t sp = uint32_t(src_far<C::x, C::y, C::z>(nb, d));
+      const uint32_t sm = uint32_t(src_far<-C::x, -C::y, -C::z>(nb, d));
+      fn(std::integral_constant<int, 2 * P + 1>{}, fin + ((2 * P + 1) * N + sp));
+      fn(std::integral_constant<int, 2 * P + 2>{}, fin + ((2 * P + 2) * N + sm));
     });
   } else {
-    gather_wall(fin, p, d, f);
+    static_for<0, NPAIR>([&](auto P_) {
+      constexpr int P = decltype(P_)::value;
+      using C = Pair<P>;
+      bool fp, fm;
+      const uint32_t sp = uint32_t(src_wall<C::x, C::y, C::z, C::s>(p, d, fp));
+      const uint32_t sm = uint32_t(src_wall<-C::x, -C::y, -C::z, C::s>(p, d, fm));
+      fn(std::integral_constant<int, 2 * P + 1>{}, fin + ((fp ? 2 * P + 2 : 2 * P + 1) * N + sp));
+      fn(std::integral_constant<int, 2 * P + 2>{}, fin + ((fm ? 2 * P + 1 : 2 * P + 2) * N + sm));
+    });
   }
 }
 
-// Store the 41 post-collision populations of one node.
+// Load the 41 streamed populations of node p from the post-collision state.
 template <class S, class R>
-__device__ __forceinline__ void store_node(S* __restrict__ out, int N, const R (&f)[Q]) {
+__device__ __forceinline__ void gather(const S* __restrict__ fin, const CellPos& p,
+                                       const Dims& d, R (&f)[Q]) {
+  using Cd = Codec<S, R>;
+  for_each_source(fin, p, d, [&](auto L_, const S* src) {
+    constexpr int L = decltype(L_)::value;
+    f[L] = Cd::template dec<L>(__ldg(src));
+  });
+}
+
+// Store the 41 post-collision populations of node `cell` into the instance
+// block `out` (32-bit offsets, as for_each_source).
+template <class S, class R>
+__device__ __forceinline__ void store_node(S* __restrict__ out, uint32_t cell, uint32_t N, const R (&f)[Q]) {
   using Cd = Codec<S, R>;
   static_for<0, Q>([&](auto L_) {
     constexpr int L = decltype(L_)::value;
-    out[size_t(L) * N] = Cd::template enc<L>(f[L]);
+    out[uint32_t(L) * N + cell] = Cd::template enc<L>(f[L]);
   });
 }
 

@@ -11,8 +11,9 @@ namespace lbgm {
 template <class S, class R>
 cudaError_t launch_step_t(int K, const S* fin, S* fout, const GeoDev<R>& geo, const InstParams<R>* inst,
                           const Dims& d, int* flag, int threads, cudaStream_t s) {
-  const uint32_t total = uint32_t(d.batch) * uint32_t(d.ncell);
-  const uint32_t blocks = (total + threads - 1) / threads;
+  if (d.batch < 1 || d.batch > 65535) return cudaErrorInvalidValue;
+  threads = threads < StepBounds<S, R>::maxt ? threads : StepBounds<S, R>::maxt;
+  const dim3 blocks((uint32_t(d.ncell) + threads - 1) / threads, uint32_t(d.batch));
   switch (K) {
     case KFLAT: k_step<S, R, KFLAT><<<blocks, threads, 0, s>>>(fin, fout, geo, inst, d, flag); break;
     case KCYL: k_step<S, R, KCYL><<<blocks, threads, 0, s>>>(fin, fout, geo, inst, d, flag); break;

@@ -170,9 +170,7 @@ __global__ void __launch_bounds__(NX, 512 / NX) k_step_tma(const __grid_constant
         f[2 * P + 2] = st[(2 * P + 2) * NX + xs[-C::z + 3]];
       });
     } else {
-      const float* fb = fin + size_t(p.b) * Q * d.ncell;
-      f[0] = __ldg(fb + p.cell);
-      gather_wall(fb, p, d, f);
+      gather(fin + size_t(p.b) * Q * d.ncell, p, d, f);
     }
     __syncwarp();
     if (lane == 0) mbar_arrive(&empty[s]);

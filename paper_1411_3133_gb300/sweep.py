@@ -144,19 +144,37 @@ def mixed_contexts(instances, precision="fp32", stream=None, init=True):
     return ctxs, L.LBBatch(ctxs)
 
 
-def critical_dean_saturation(deans, a_final, floor=None, npoints=4, sat_factor=100.0):
+def is_saturated(A, floor, sat_factor=100.0, window=0.2, tol=0.05):
+    """True when the amplitude series A (samples in time order) ends above
+    sat_factor x the round-off floor and changed by less than tol (relative)
+    over its last `window` fraction: the vortex has reached its nonlinear
+    amplitude. An instance just above threshold grows slowly (growth rate
+    ~ De - De_c) and may still be growing at the end of the run; it is not
+    saturated and must not enter the A^2 line."""
+    A = np.asarray(A, float)
+    A = A[np.isfinite(A)]
+    if len(A) < 4:
+        return False
+    k = max(2, int(round(len(A) * window)))
+    tail = A[-k:]
+    return bool(tail[-1] > sat_factor * floor and abs(tail[-1] / tail[0] - 1.0) < tol)
+
+
+def critical_dean_saturation(deans, a_final, floor=None, npoints=4, sat_factor=100.0, saturated=None):
     """De_c from saturated amplitudes: least-squares line A^2 = a (De - De_c)
-    through the first `npoints` Dean numbers whose final amplitude exceeds
-    sat_factor x the round-off floor (the median final amplitude of the
-    instances that did not grow, if not given). NaN if fewer than two."""
+    through the first `npoints` Dean numbers that saturated -- `saturated` (a
+    boolean per instance, e.g. from is_saturated) or, if not given, those whose
+    final amplitude exceeds sat_factor x the round-off floor (the median final
+    amplitude of the instances that did not grow, if not given). NaN if fewer
+    than two."""
     d = np.asarray(deans, float)
     a = np.asarray(a_final, float)
-    order = np.argsort(d)
-    d, a = d[order], a[order]
     if floor is None:
         quiet = a[a < 1e-5]
         floor = float(np.median(quiet)) if len(quiet) else 1e-7
-    sat = a > sat_factor * floor
+    sat = np.asarray(saturated, bool) if saturated is not None else a > sat_factor * floor
+    order = np.argsort(d)
+    d, a, sat = d[order], a[order], sat[order]
     x, y = d[sat][:npoints], (a[sat] ** 2)[:npoints]
     if len(x) < 2:
         return float("nan")
@@ -165,8 +183,9 @@ def critical_dean_saturation(deans, a_final, floor=None, npoints=4, sat_factor=1
 
 
 def summarize(res: SweepResult):
-    """{tau: {"dean": measured De, "a_final": ..., "sigma": ..., "De_c": ...,
-    "De_c_growth": ...}} from one sweep holding several tau values."""
+    """{tau: {"dean": measured De, "a_final": ..., "saturated": ..., "sigma":
+    ..., "De_c": ..., "De_c_growth": ...}} from one sweep holding several tau
+    values."""
     out = {}
     S = len(res.times)
     for tau in sorted(set(res.taus)):
@@ -174,8 +193,90 @@ def summarize(res: SweepResult):
         # measured (not target) Dean numbers, laminar phase (first quarter)
         de = np.array([float(np.nanmean(res.dean_measured[: max(2, S // 4), b])) for b in idx])
         a_fin = np.array([float(np.nanmean(res.amp[-max(2, S // 8):, b])) for b in idx])
+        quiet = a_fin[a_fin < 1e-5]
+        floor = float(np.median(quiet)) if len(quiet) else 1e-7
+        sat = np.array([is_saturated(res.amp[:, b], floor) for b in idx])
         sig = res.sigma[idx]
-        out[tau] = {"dean": de.tolist(), "a_final": a_fin.tolist(), "sigma": sig.tolist(),
-                    "De_c": critical_dean_saturation(de, a_fin),
+        out[tau] = {"dean": de.tolist(), "a_final": a_fin.tolist(), "saturated": sat.tolist(),
+                    "sigma": sig.tolist(),
+                    "De_c": critical_dean_saturation(de, a_fin, floor, saturated=sat),
                     "De_c_growth": critical_dean(de, sig)}
     return out
+
+
+def run_sweep_sequential(spec: L.ChannelSpec, taus, deans, steps: int, sample_every: int = 1000,
+                         precision: str = "fp64", seed: int = 20241111, noise_amp: float = 1e-4,
+                         use_graph: bool = True) -> SweepResult:
+    """The unbatched sweep: instance b runs alone in its own context, one
+    after the other, with the same inputs as instance b of run_sweep."""
+    import time
+
+    import torch
+
+    parts = []
+    t0 = time.perf_counter()
+    for b, (tau, de) in enumerate(zip(taus, deans)):
+        parts.append(run_sweep(spec, [tau], [de], steps, sample_every, precision, seed + b, noise_amp,
+                               use_graph))
+    torch.cuda.synchronize()
+    sec = time.perf_counter() - t0
+    res = SweepResult(list(deans), list(taus), parts[0].times,
+                      np.concatenate([p.amp for p in parts], axis=1),
+                      np.concatenate([p.dean_measured for p in parts], axis=1),
+                      np.concatenate([p.vorticity for p in parts], axis=1), seconds=sec)
+    res.sigma = np.concatenate([p.sigma for p in parts])
+    return res
+
+
+def compare_time_to_critical_dean(steps=300_000, sample_every=2000, modes=None):
+    """Wall time and De_c of the 24-instance sweep (64 x 4 x 256 cylinder,
+    eta = 0.975, 12 De in [25, 60] x tau in {0.55, 0.6}) run as the plain FP64
+    sweep (instances one after another) and as one batched launch per step in
+    each storage precision. Returns {mode: {"seconds", "De_c": {tau: ...}, ...}}
+    with each mode's speed-up and De_c error against the plain FP64 sweep."""
+    spec = L.ChannelSpec("cylindrical", 1.0, 1 / 0.975, 64, 4, 256)
+    deans = list(np.linspace(25.0, 60.0, 12))
+    taus = [0.55] * 12 + [0.6] * 12
+    deans2 = deans + deans
+    modes = modes or ["fp64_sequential", "fp64", "fp32", "fp16_shifted", "bf16_shifted"]
+    out = {}
+    for mode in modes:
+        if mode == "fp64_sequential":
+            res = run_sweep_sequential(spec, taus, deans2, steps, sample_every, "fp64")
+        else:
+            res = run_sweep(spec, taus, deans2, steps, sample_every, mode)
+        summ = summarize(res)
+        out[mode] = {"seconds": res.seconds,
+                     "De_c": {str(t): summ[t]["De_c"] for t in summ},
+                     "De_c_growth": {str(t): summ[t]["De_c_growth"] for t in summ},
+                     "dean": {str(t): summ[t]["dean"] for t in summ},
+                     "a_final": {str(t): summ[t]["a_final"] for t in summ},
+                     "saturated": {str(t): summ[t]["saturated"] for t in summ},
+                     "times": res.times.tolist(), "amp": res.amp.tolist()}
+    ref = out.get("fp64_sequential")
+    if ref:
+        for mode, r in out.items():
+            r["speedup_vs_fp64_sequential"] = ref["seconds"] / r["seconds"]
+            r["De_c_rel_err_vs_fp64_sequential"] = {
+                t: abs(r["De_c"][t] / ref["De_c"][t] - 1.0) for t in r["De_c"]}
+    return out
+
+
+if __name__ == "__main__":
+    import argparse
+    import json
+
+    ap = argparse.ArgumentParser(description="time-to-critical-Dean comparison of sweep modes")
+    ap.add_argument("--steps", type=int, default=300_000)
+    ap.add_argument("--sample-every", type=int, default=2000)
+    ap.add_argument("--modes", default="fp64_sequential,fp64,fp32,fp16_shifted,bf16_shifted")
+    ap.add_argument("--out", default=None)
+    a = ap.parse_args()
+    L.load_library()
+    r = compare_time_to_critical_dean(a.steps, a.sample_every, a.modes.split(","))
+    text = json.dumps(r)
+    print(json.dumps({m: {k: v for k, v in x.items() if k not in ("amp", "times")} for m, x in r.items()},
+                     indent=1))
+    if a.out:
+        with open(a.out, "w") as f:
+            f.write(text)

@@ -40,6 +40,31 @@ def test_critical_dean_from_saturated_amplitude():
     assert np.isnan(critical_dean_saturation(de, np.full(6, 3e-7)))
 
 
+def test_saturation_test_excludes_slowly_growing_instances():
+    from paper_1411_3133_gb300.sweep import critical_dean_saturation, is_saturated
+    t = np.arange(0, 300001, 2000, dtype=float)
+    floor = 1e-8
+    de = np.array([30.0, 34.0, 38.0, 39.0, 42.0, 46.0, 50.0, 54.0])
+    dec = 37.5
+    series = []
+    for x in de:
+        if x < dec:                                  # decays to the floor
+            A = floor * (1 + 1e-2 * np.sin(t / 7e3))
+        elif x < 40.0:                               # just above threshold: still growing
+            A = 1e-6 * np.exp(2e-5 * t)
+        else:                                        # logistic growth to sqrt(a (De - De_c))
+            Asat = np.sqrt(2e-7 * (x - dec))
+            A0 = 1e-6
+            A = Asat / np.sqrt(1 + (Asat ** 2 / A0 ** 2 - 1) * np.exp(-2 * 1e-4 * t))
+        series.append(A)
+    sat = np.array([is_saturated(A, floor) for A in series])
+    assert sat.tolist() == [False, False, False, False, True, True, True, True]
+    a_fin = np.array([A[-1] for A in series])
+    assert critical_dean_saturation(de, a_fin, floor, saturated=sat) == pytest.approx(dec, rel=1e-3)
+    # a floor-only test would take the growing instance at De = 39 as saturated and be biased
+    assert abs(critical_dean_saturation(de, a_fin, floor) - dec) > 0.1
+
+
 def test_mixed_batch_recipe_is_seeded_and_in_range():
     from paper_1411_3133_gb300.workloads import BASE_SEED, force_reference_cylinder, mixed_batch
     a, b = mixed_batch(), mixed_batch()
