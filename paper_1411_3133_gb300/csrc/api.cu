@@ -190,26 +190,79 @@ std::string check_sparsity(const std::vector<double>& rows, const lb_geometry_de
 
 bool use_tma(const lb_ctx* c) { return c->prec == LB_FP32 && c->tma_ok && c->step_kernel == 2; }
 
+
+// Region-split step: the wall layers run on the context's second stream,
+// concurrently with the interior on the main stream (fork and join by events,
+// which a graph capture records as branches).
+cudaError_t launch_split(lb_ctx* c, int src, int dst) {
+  cudaError_t e = cudaSuccess;
+  if (!c->aux) {
+    e = cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
+    if (e != cudaSuccess) return e;
+  }
+  e = cudaEventRecord(c->ev_fork, c->stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(c->aux, c->ev_fork, 0);
+  if (e != cudaSuccess) return e;
+  switch (c->prec) {
+    case LB_FP64:
+      e = launch_step_split_f64(c->K, static_cast<const double*>(c->f[src]), static_cast<double*>(c->f[dst]),
+                                c->geo_d, static_cast<const InstParams<double>*>(c->inst), c->dims, c->flag,
+                                c->block_threads, c->stream, c->aux);
+      break;
+    case LB_FP32:
+      e = launch_step_split_f32(c->K, static_cast<const float*>(c->f[src]), static_cast<float*>(c->f[dst]),
+                                c->geo_f, static_cast<const InstParams<float>*>(c->inst), c->dims, c->flag,
+                                c->block_threads, c->stream, c->aux);
+      break;
+    case LB_FP16_SHIFTED:
+      e = launch_step_split_h16(c->K, static_cast<const __half*>(c->f[src]), static_cast<__half*>(c->f[dst]),
+                                c->geo_f, static_cast<const InstParams<float>*>(c->inst), c->dims, c->flag,
+                                c->block_threads, c->stream, c->aux);
+      break;
+    default:
+      e = launch_step_split_b16(c->K, static_cast<const __nv_bfloat16*>(c->f[src]),
+                                static_cast<__nv_bfloat16*>(c->f[dst]), c->geo_f,
+                                static_cast<const InstParams<float>*>(c->inst), c->dims, c->flag,
+                                c->block_threads, c->stream, c->aux);
+      break;
+  }
+  cudaError_t e2 = cudaEventRecord(c->ev_join, c->aux);  // join even after a failed launch
+  if (e2 == cudaSuccess) e2 = cudaStreamWaitEvent(c->stream, c->ev_join, 0);
+  return e != cudaSuccess ? e : e2;
+}
+
+// LB_OPT_STEP_KERNEL 0 (auto): the region split where x3 is periodic and the
+// arithmetic is FP32 (measured fastest there), the one-kernel step otherwise.
+int resolved_kernel(const lb_ctx* c) {
+  if (c->step_kernel != 0) return c->step_kernel;
+  return (c->geom.periodic3 && c->prec != LB_FP64) ? 4 : 1;
+}
+
 lb_status launch_step_once(lb_ctx* c) {
   const int src = c->cur, dst = 1 - c->cur;
+  const int kern = resolved_kernel(c);
   cudaError_t e;
-  if (c->step_kernel == 3 && c->prec == LB_FP32)
+  if (kern == 3 && c->prec == LB_FP32)
     e = launch_step_async_f32(c->K, static_cast<const float*>(c->f[src]), static_cast<float*>(c->f[dst]),
                               c->geo_f, static_cast<const InstParams<float>*>(c->inst), c->dims, c->flag,
                               c->block_threads, c->nodes_per_thread, c->stream);
-  else if (c->step_kernel == 3 && c->prec == LB_FP64)
+  else if (kern == 3 && c->prec == LB_FP64)
     e = launch_step_async_f64(c->K, static_cast<const double*>(c->f[src]), static_cast<double*>(c->f[dst]),
                               c->geo_d, static_cast<const InstParams<double>*>(c->inst), c->dims, c->flag,
                               c->block_threads, c->nodes_per_thread, c->stream);
-  else if (c->step_kernel == 3 && c->prec == LB_FP16_SHIFTED)
+  else if (kern == 3 && c->prec == LB_FP16_SHIFTED)
     e = launch_step_async_h16(c->K, static_cast<const __half*>(c->f[src]), static_cast<__half*>(c->f[dst]),
                               c->geo_f, static_cast<const InstParams<float>*>(c->inst), c->dims, c->flag,
                               c->block_threads, c->nodes_per_thread, c->stream);
-  else if (c->step_kernel == 3)
+  else if (kern == 3)
     e = launch_step_async_b16(c->K, static_cast<const __nv_bfloat16*>(c->f[src]),
                               static_cast<__nv_bfloat16*>(c->f[dst]), c->geo_f,
                               static_cast<const InstParams<float>*>(c->inst), c->dims, c->flag,
                               c->block_threads, c->nodes_per_thread, c->stream);
+  else if (kern == 4)
+    e = launch_split(c, src, dst);
   else if (use_tma(c))
     e = launch_step_tma_f32(c->K, c->tmap[src], static_cast<const float*>(c->f[src]),
                             static_cast<float*>(c->f[dst]), c->geo_f,
@@ -684,8 +737,10 @@ lb_status lb_set_option(lb_ctx* c, int option, long long value) {
       c->use_graph = value ? 1 : 0;
       return LB_OK;
     case LB_OPT_STEP_KERNEL:
-      if (value < 0 || value > 3)
-        return fail(c, LB_ERR_ARG, "need 0 (auto), 1 (plain), 2 (TMA) or 3 (prefetching)");
+      if (value < 0 || value > 4)
+        return fail(c, LB_ERR_ARG, "need 0 (auto), 1 (plain), 2 (TMA), 3 (prefetching) or 4 (region split)");
+      if (value == 4 && !c->geom.periodic3)
+        return fail(c, LB_ERR_ARG, "the region-split step kernel needs a periodic x3 axis");
       if (value == 2 && !c->tma_ok)
         return fail(c, LB_ERR_ARG, "the TMA step kernel needs FP32 and n3 in {128, 256}");
       c->step_kernel = int(value);
@@ -712,6 +767,8 @@ lb_status lb_autotune(lb_ctx* c, int steps_per_trial, lb_tune* best, lb_tune* tr
     for (int t : {64, 128, 192, 256}) cand.push_back({t, 1, 0, 0.0});
   else
     for (int t : {64, 96, 128}) cand.push_back({t, 1, 0, 0.0});
+  if (c->geom.periodic3)
+    for (int t : {64, 96, 128}) cand.push_back({t, 4, 0, 0.0});
   if (c->tma_ok) cand.push_back({0, 2, 0, 0.0});  // the TMA kernel fixes its own block shape
   for (int t : {128, 256})
     for (int npt : {2, 4, 8}) cand.push_back({t, 3, npt, 0.0});
@@ -766,6 +823,12 @@ lb_status lb_autotune(lb_ctx* c, int steps_per_trial, lb_tune* best, lb_tune* tr
 void lb_destroy(lb_ctx* c) {
   if (!c) return;
   cudaStreamSynchronize(c->stream);
+  if (c->aux) {
+    cudaStreamSynchronize(c->aux);
+    cudaStreamDestroy(c->aux);
+  }
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
   free_all(c);
   if (c->own_stream) cudaStreamDestroy(c->stream);
   delete c;

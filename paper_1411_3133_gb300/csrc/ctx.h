@@ -64,6 +64,8 @@ struct lb_ctx {
   int step_kernel = 0;               // LB_OPT_STEP_KERNEL
   int nodes_per_thread = 4;          // LB_OPT_NODES_PER_THREAD
   int graph_npt = 0;
+  cudaStream_t aux = nullptr;        // second stream of the region-split step
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   bool tma_ok = false;               // tensor maps built for both buffers
   alignas(64) unsigned char tmap[2][128];
 };

@@ -28,12 +28,12 @@ __device__ __forceinline__ void collide_store(Real (&f)[Q], S* __restrict__ fout
 
 // Fused time step of one node p of one instance whose state blocks start at
 // fin and fout: pull streaming + walls, then collide_store.
-template <typename S, typename Real, int K>
+template <typename S, typename Real, int K, int WALLS = 2>
 __device__ __forceinline__ void step_node(const S* __restrict__ fin, S* __restrict__ fout,
                                           const GeoDev<Real>& geo, const InstParams<Real>& ip, const Dims& d,
                                           const CellPos& p, int* __restrict__ flag) {
   Real f[Q];
-  gather(fin, p, d, f);
+  gather<S, Real, WALLS>(fin, p, d, f);
   collide_store<S, Real, K>(f, fout, geo, ip, d, p, flag);
 }
 
@@ -75,6 +75,38 @@ __global__ void __launch_bounds__(StepBounds<S, Real>::maxt, StepBounds<S, Real>
   const CellPos p = locate_cell(d, b, cell);
   const size_t base = size_t(b) * Q * uint32_t(d.ncell);
   step_node<S, Real, K>(fin + base, fout + base, geo, inst[b], d, p, flag);
+}
+
+// The same update split by region for channels periodic in x3, where only
+// the three node layers next to each r-wall need the wall rule: k_step_bulk
+// covers the contiguous interior layers 3 .. nr - 4 with the far-from-wall
+// gather alone, k_step_edge the 6 wall layers with the wall gather alone, so
+// neither kernel carries the other's code or registers.
+template <typename S, typename Real, int K>
+__global__ void __launch_bounds__(StepBounds<S, Real>::maxt, StepBounds<S, Real>::minb)
+    k_step_bulk(const S* __restrict__ fin, S* __restrict__ fout, GeoDev<Real> geo,
+                const InstParams<Real>* __restrict__ inst, Dims d, int* __restrict__ flag) {
+  const uint32_t layer = uint32_t(d.nt) * uint32_t(d.n3);
+  const uint32_t cell = 3u * layer + blockIdx.x * blockDim.x + threadIdx.x;
+  if (cell >= uint32_t(d.nr - 3) * layer) return;
+  const int b = int(blockIdx.y);
+  const CellPos p = locate_cell(d, b, cell);
+  const size_t base = size_t(b) * Q * uint32_t(d.ncell);
+  step_node<S, Real, K, 0>(fin + base, fout + base, geo, inst[b], d, p, flag);
+}
+
+template <typename S, typename Real, int K>
+__global__ void __launch_bounds__(StepBounds<S, Real>::maxt, StepBounds<S, Real>::minb)
+    k_step_edge(const S* __restrict__ fin, S* __restrict__ fout, GeoDev<Real> geo,
+                const InstParams<Real>* __restrict__ inst, Dims d, int* __restrict__ flag) {
+  const uint32_t layer = uint32_t(d.nt) * uint32_t(d.n3);
+  const uint32_t e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= 6u * layer) return;
+  const uint32_t cell = e < 3u * layer ? e : e + uint32_t(d.nr - 6) * layer;
+  const int b = int(blockIdx.y);
+  const CellPos p = locate_cell(d, b, cell);
+  const size_t base = size_t(b) * Q * uint32_t(d.ncell);
+  step_node<S, Real, K, 1>(fin + base, fout + base, geo, inst[b], d, p, flag);
 }
 
 // One instance of a batch whose instances differ in geometry and size: its

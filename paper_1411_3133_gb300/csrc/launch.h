@@ -26,6 +26,20 @@ cudaError_t launch_step_b16(int K, const __nv_bfloat16* fin, __nv_bfloat16* fout
                             const InstParams<float>* inst, const Dims& d, int* flag, int threads,
                             cudaStream_t s);
 
+// Region-split step (periodic x3): wall layers on stream se, interior on s.
+cudaError_t launch_step_split_f64(int K, const double* fin, double* fout, const GeoDev<double>& geo,
+                                  const InstParams<double>* inst, const Dims& d, int* flag, int threads,
+                                  cudaStream_t s, cudaStream_t se);
+cudaError_t launch_step_split_f32(int K, const float* fin, float* fout, const GeoDev<float>& geo,
+                                  const InstParams<float>* inst, const Dims& d, int* flag, int threads,
+                                  cudaStream_t s, cudaStream_t se);
+cudaError_t launch_step_split_h16(int K, const __half* fin, __half* fout, const GeoDev<float>& geo,
+                                  const InstParams<float>* inst, const Dims& d, int* flag, int threads,
+                                  cudaStream_t s, cudaStream_t se);
+cudaError_t launch_step_split_b16(int K, const __nv_bfloat16* fin, __nv_bfloat16* fout, const GeoDev<float>& geo,
+                                  const InstParams<float>* inst, const Dims& d, int* flag, int threads,
+                                  cudaStream_t s, cudaStream_t se);
+
 // Work-list step over instances of different geometry (ListInst<S, R> array);
 // grid 0 launches one block per work item.
 cudaError_t launch_step_list_f64(int K, const void* insts, const int2* work, int nwork, int threads,

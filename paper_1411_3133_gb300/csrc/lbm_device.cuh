@@ -265,40 +265,62 @@ __device__ __forceinline__ bool near_wall(const CellPos& p, const Dims& d) {
 // Offsets are 32-bit: an instance block holds fewer than 2^32 bytes
 // (checked when the context is created).
 template <class S, class Fn>
+__device__ __forceinline__ void for_each_source_far(const S* __restrict__ fin, const CellPos& p, const Dims& d,
+                                                    Fn&& fn) {
+  const uint32_t N = uint32_t(d.ncell);
+  Neighbours nb;
+  make_neighbours(p, d, nb);
+  static_for<0, NPAIR>([&](auto P_) {
+    constexpr int P = decltype(P_)::value;
+    using C = Pair<P>;
+    const uint32_t sp = uint32_t(src_far<C::x, C::y, C::z>(nb, d));
+    const uint32_t sm = uint32_t(src_far<-C::x, -C::y, -C::z>(nb, d));
+    fn(std::integral_constant<int, 2 * P + 1>{}, fin + ((2 * P + 1) * N + sp));
+    fn(std::integral_constant<int, 2 * P + 2>{}, fin + ((2 * P + 2) * N + sm));
+  });
+}
+
+template <class S, class Fn>
+__device__ __forceinline__ void for_each_source_wall(const S* __restrict__ fin, const CellPos& p, const Dims& d,
+                                                     Fn&& fn) {
+  const uint32_t N = uint32_t(d.ncell);
+  static_for<0, NPAIR>([&](auto P_) {
+    constexpr int P = decltype(P_)::value;
+    using C = Pair<P>;
+    bool fp, fm;
+    const uint32_t sp = uint32_t(src_wall<C::x, C::y, C::z, C::s>(p, d, fp));
+    const uint32_t sm = uint32_t(src_wall<-C::x, -C::y, -C::z, C::s>(p, d, fm));
+    fn(std::integral_constant<int, 2 * P + 1>{}, fin + ((fp ? 2 * P + 2 : 2 * P + 1) * N + sp));
+    fn(std::integral_constant<int, 2 * P + 2>{}, fin + ((fm ? 2 * P + 1 : 2 * P + 2) * N + sm));
+  });
+}
+
+// Offsets are 32-bit: an instance block holds fewer than 2^32 bytes
+// (checked when the context is created). WALLS selects the code paths
+// compiled in: 0 far from every wall only, 1 near a wall only, 2 both (the
+// node decides).
+template <class S, int WALLS = 2, class Fn>
 __device__ __forceinline__ void for_each_source(const S* __restrict__ fin, const CellPos& p, const Dims& d,
                                                 Fn&& fn) {
-  const uint32_t N = uint32_t(d.ncell);
   fn(std::integral_constant<int, 0>{}, fin + uint32_t(p.cell));
-  if (!near_wall(p, d)) {
-    Neighbours nb;
-    make_neighbours(p, d, nb);
-    static_for<0, NPAIR>([&](auto P_) {
-      constexpr int P = decltype(P_)::value;
-      using C = Pair<P>;
-      const uint32_t sp = uint32_t(src_far<C::x, C::y, C::z>(nb, d));
-      const uint32_t sm = uint32_t(src_far<-C::x, -C::y, -C::z>(nb, d));
-      fn(std::integral_constant<int, 2 * P + 1>{}, fin + ((2 * P + 1) * N + sp));
-      fn(std::integral_constant<int, 2 * P + 2>{}, fin + ((2 * P + 2) * N + sm));
-    });
+  if constexpr (WALLS == 0) {
+    for_each_source_far(fin, p, d, fn);
+  } else if constexpr (WALLS == 1) {
+    for_each_source_wall(fin, p, d, fn);
   } else {
-    static_for<0, NPAIR>([&](auto P_) {
-      constexpr int P = decltype(P_)::value;
-      using C = Pair<P>;
-      bool fp, fm;
-      const uint32_t sp = uint32_t(src_wall<C::x, C::y, C::z, C::s>(p, d, fp));
-      const uint32_t sm = uint32_t(src_wall<-C::x, -C::y, -C::z, C::s>(p, d, fm));
-      fn(std::integral_constant<int, 2 * P + 1>{}, fin + ((fp ? 2 * P + 2 : 2 * P + 1) * N + sp));
-      fn(std::integral_constant<int, 2 * P + 2>{}, fin + ((fm ? 2 * P + 1 : 2 * P + 2) * N + sm));
-    });
+    if (!near_wall(p, d))
+      for_each_source_far(fin, p, d, fn);
+    else
+      for_each_source_wall(fin, p, d, fn);
   }
 }
 
 // Load the 41 streamed populations of node p from the post-collision state.
-template <class S, class R>
+template <class S, class R, int WALLS = 2>
 __device__ __forceinline__ void gather(const S* __restrict__ fin, const CellPos& p,
                                        const Dims& d, R (&f)[Q]) {
   using Cd = Codec<S, R>;
-  for_each_source(fin, p, d, [&](auto L_, const S* src) {
+  for_each_source<S, WALLS>(fin, p, d, [&](auto L_, const S* src) {
     constexpr int L = decltype(L_)::value;
     f[L] = Cd::template dec<L>(__ldg(src));
   });

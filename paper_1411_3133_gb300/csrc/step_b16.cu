@@ -19,4 +19,10 @@ cudaError_t step_list_occupancy_b16(int K, int threads, int* blocks_per_sm) {
   return step_list_occupancy_t<__nv_bfloat16, float>(K, threads, blocks_per_sm);
 }
 
+cudaError_t launch_step_split_b16(int K, const __nv_bfloat16* fin, __nv_bfloat16* fout, const GeoDev<float>& geo,
+                                  const InstParams<float>* inst, const Dims& d, int* flag, int threads,
+                                  cudaStream_t s, cudaStream_t se) {
+  return launch_step_split_t<__nv_bfloat16, float>(K, fin, fout, geo, inst, d, flag, threads, s, se);
+}
+
 }  // namespace lbgm

@@ -19,4 +19,10 @@ cudaError_t step_list_occupancy_f64(int K, int threads, int* blocks_per_sm) {
   return step_list_occupancy_t<double, double>(K, threads, blocks_per_sm);
 }
 
+cudaError_t launch_step_split_f64(int K, const double* fin, double* fout, const GeoDev<double>& geo,
+                                  const InstParams<double>* inst, const Dims& d, int* flag, int threads,
+                                  cudaStream_t s, cudaStream_t se) {
+  return launch_step_split_t<double, double>(K, fin, fout, geo, inst, d, flag, threads, s, se);
+}
+
 }  // namespace lbgm

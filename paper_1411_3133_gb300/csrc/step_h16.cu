@@ -19,4 +19,10 @@ cudaError_t step_list_occupancy_h16(int K, int threads, int* blocks_per_sm) {
   return step_list_occupancy_t<__half, float>(K, threads, blocks_per_sm);
 }
 
+cudaError_t launch_step_split_h16(int K, const __half* fin, __half* fout, const GeoDev<float>& geo,
+                                  const InstParams<float>* inst, const Dims& d, int* flag, int threads,
+                                  cudaStream_t s, cudaStream_t se) {
+  return launch_step_split_t<__half, float>(K, fin, fout, geo, inst, d, flag, threads, s, se);
+}
+
 }  // namespace lbgm

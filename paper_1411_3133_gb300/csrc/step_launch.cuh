@@ -23,6 +23,35 @@ cudaError_t launch_step_t(int K, const S* fin, S* fout, const GeoDev<R>& geo, co
   return cudaGetLastError();
 }
 
+// Region-split step (periodic x3 only): the 6 wall layers on stream se, the
+// interior on stream s (the caller orders the two streams around the step).
+template <class S, class R>
+cudaError_t launch_step_split_t(int K, const S* fin, S* fout, const GeoDev<R>& geo, const InstParams<R>* inst,
+                                const Dims& d, int* flag, int threads, cudaStream_t s, cudaStream_t se) {
+  if (d.batch < 1 || d.batch > 65535 || !d.periodic3 || d.nr < 7) return cudaErrorInvalidValue;
+  threads = threads < StepBounds<S, R>::maxt ? threads : StepBounds<S, R>::maxt;
+  const uint32_t layer = uint32_t(d.nt) * uint32_t(d.n3);
+  const dim3 ge((6u * layer + threads - 1) / threads, uint32_t(d.batch));
+  const dim3 gb((uint32_t(d.nr - 6) * layer + threads - 1) / threads, uint32_t(d.batch));
+  switch (K) {
+    case KFLAT:
+      k_step_edge<S, R, KFLAT><<<ge, threads, 0, se>>>(fin, fout, geo, inst, d, flag);
+      k_step_bulk<S, R, KFLAT><<<gb, threads, 0, s>>>(fin, fout, geo, inst, d, flag);
+      break;
+    case KCYL:
+      k_step_edge<S, R, KCYL><<<ge, threads, 0, se>>>(fin, fout, geo, inst, d, flag);
+      k_step_bulk<S, R, KCYL><<<gb, threads, 0, s>>>(fin, fout, geo, inst, d, flag);
+      break;
+    case KELL:
+      k_step_edge<S, R, KELL><<<ge, threads, 0, se>>>(fin, fout, geo, inst, d, flag);
+      k_step_bulk<S, R, KELL><<<gb, threads, 0, s>>>(fin, fout, geo, inst, d, flag);
+      break;
+    default:
+      return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
 // grid 0: one block per work item; otherwise `grid` persistent blocks.
 template <class S, class R>
 cudaError_t launch_step_list_t(int K, const void* insts, const int2* work, int nwork, int threads, int grid,

@@ -358,11 +358,41 @@ def test_prefetching_kernel_is_bitwise_equal_to_plain_kernel(ch, batch, precisio
         assert np.array_equal(outs[0], o)
 
 
+@pytest.mark.parametrize("precision", ["fp32", "fp64", "bf16_shifted"])
+@pytest.mark.parametrize("ch,batch", [
+    (Channel("cylindrical", 1.0, 1 / ETA, 16, 4, 256), 2),
+    (Channel("cylindrical", 1.0, 1 / 0.9, 9, 3, 13), 3),
+    (Channel("cylindrical", 1.0, 1 / ETA, 7, 1, 40), 1),
+    (Channel("ellipsoidal", 1.0, 1.1, 8, 3, 35, b=1.2), 1),
+], ids=["cyl256", "cyl_ragged", "cyl_nr7", "ell_periodic"])
+def test_region_split_kernel_is_bitwise_equal_to_plain_kernel(ch, batch, precision):
+    """Wall layers and interior in two kernels give the one-kernel states."""
+    L = lib()
+    params = [dict(tau=0.6 + 0.1 * b, G=2e-4, seed=60 + b, amp=1e-2) for b in range(batch)]
+    outs = []
+    for kern, threads in ((1, 128), (4, 128), (4, 64)):
+        tw = Twin(ch, params, precision)
+        tw.ctx.lb_set_option(L.LB_OPT_STEP_KERNEL, kern)
+        tw.ctx.lb_set_option(L.LB_OPT_BLOCK_THREADS, threads)
+        tw.ctx.lb_set_option(L.LB_OPT_USE_GRAPH, 1)
+        tw.ctx.lb_init(tw.lparams)
+        tw.ctx.lb_step(17)
+        outs.append(tw.ctx.lb_get_populations())
+        tw.close()
+    for o in outs[1:]:
+        assert np.array_equal(outs[0], o)
+    tw = Twin(Channel("flat", 0.0, 1.0, 8, 2, 9, periodic3=False), params[:1], precision)
+    with pytest.raises(L.LBError) as e:
+        tw.ctx.lb_set_option(L.LB_OPT_STEP_KERNEL, 4)        # walls on x3: not supported
+    assert e.value.status == L.LB_ERR_ARG
+    tw.close()
+
+
 def test_prefetching_kernel_option_validation():
     L = lib()
     tw = Twin(CYL1, [dict(tau=0.8)], "fp16_shifted")
     with pytest.raises(L.LBError) as e:
-        tw.ctx.lb_set_option(L.LB_OPT_STEP_KERNEL, 4)
+        tw.ctx.lb_set_option(L.LB_OPT_STEP_KERNEL, 5)
     assert e.value.status == L.LB_ERR_ARG
     for bad in (0, 65):
         with pytest.raises(L.LBError):
