@@ -80,8 +80,8 @@ __global__ void __launch_bounds__(StepBounds<S, Real>::maxt, StepBounds<S, Real>
 // The same update split by region for channels periodic in x3, where only
 // the three node layers next to each r-wall need the wall rule: k_step_bulk
 // covers the contiguous interior layers 3 .. nr - 4 with the far-from-wall
-// gather alone, k_step_edge the 6 wall layers with the wall gather alone, so
-// neither kernel carries the other's code or registers.
+// gather alone, k_step_edge the 6 wall layers with the per-layer constant
+// folds (gather_edge), so neither kernel carries the other's code.
 template <typename S, typename Real, int K>
 __global__ void __launch_bounds__(StepBounds<S, Real>::maxt, StepBounds<S, Real>::minb)
     k_step_bulk(const S* __restrict__ fin, S* __restrict__ fout, GeoDev<Real> geo,
@@ -106,7 +106,9 @@ __global__ void __launch_bounds__(StepBounds<S, Real>::maxt, StepBounds<S, Real>
   const int b = int(blockIdx.y);
   const CellPos p = locate_cell(d, b, cell);
   const size_t base = size_t(b) * Q * uint32_t(d.ncell);
-  step_node<S, Real, K, 1>(fin + base, fout + base, geo, inst[b], d, p, flag);
+  Real f[Q];
+  gather_edge(fin + base, p, d, f);
+  collide_store<S, Real, K>(f, fout + base, geo, inst[b], d, p, flag);
 }
 
 // One instance of a batch whose instances differ in geometry and size: its

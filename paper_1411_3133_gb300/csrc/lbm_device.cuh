@@ -262,8 +262,6 @@ __device__ __forceinline__ bool near_wall(const CellPos& p, const Dims& d) {
 // wall every moving population comes from its (possibly folded) source;
 // opposite velocities share their weight, so a folded population decodes
 // with the weight of the pair.
-// Offsets are 32-bit: an instance block holds fewer than 2^32 bytes
-// (checked when the context is created).
 template <class S, class Fn>
 __device__ __forceinline__ void for_each_source_far(const S* __restrict__ fin, const CellPos& p, const Dims& d,
                                                     Fn&& fn) {
@@ -312,6 +310,62 @@ __device__ __forceinline__ void for_each_source(const S* __restrict__ fin, const
       for_each_source_far(fin, p, d, fn);
     else
       for_each_source_wall(fin, p, d, fn);
+  }
+}
+
+// Sources for a node J = 0, 1, 2 layers from the r-wall on side SIDE (0:
+// inner, 1: outer) of a channel periodic in x3 with nr >= 7: only that wall
+// can lie on a population's one-step path, so the wall rule of src_wall
+// reduces to constants. A population whose backward path (along -c, length
+// s = |c|_inf) meets the wall 2 J + 1 half-nodes away folds once: its source
+// is x + (s - 1 - 2 J) sigma (sigma = c / s) and it arrives flipped; every
+// other population comes from x - c as away from walls.
+template <int SIDE, int J, int CX, int CY, int CZ, int S>
+struct LayerFold {
+  static constexpr int sx = (CX > 0) - (CX < 0), sy = (CY > 0) - (CY < 0), sz = (CZ > 0) - (CZ < 0);
+  static constexpr bool hit = ((SIDE == 0 && sx > 0) || (SIDE == 1 && sx < 0)) && (2 * S > 1 + 2 * J);
+  static constexpr int q = hit ? S - 1 - 2 * J : -S;
+  static constexpr int dx = q * sx, dy = q * sy, dz = q * sz;  // source - node
+};
+
+template <int SIDE, int J, class S, class Fn>
+__device__ __forceinline__ void for_each_source_layer(const S* __restrict__ fin, const CellPos& p,
+                                                      const Dims& d, Fn&& fn) {
+  const uint32_t N = uint32_t(d.ncell);
+  Neighbours nb;
+  make_neighbours(p, d, nb);
+  static_for<0, NPAIR>([&](auto P_) {
+    constexpr int P = decltype(P_)::value;
+    using C = Pair<P>;
+    using Fp = LayerFold<SIDE, J, C::x, C::y, C::z, C::s>;
+    using Fm = LayerFold<SIDE, J, -C::x, -C::y, -C::z, C::s>;
+    const uint32_t sp = uint32_t((nb.rrow[3 - Fp::dx] + nb.tcol[3 - Fp::dy]) * d.n3 + nb.zcol[3 - Fp::dz]);
+    const uint32_t sm = uint32_t((nb.rrow[3 - Fm::dx] + nb.tcol[3 - Fm::dy]) * d.n3 + nb.zcol[3 - Fm::dz]);
+    fn(std::integral_constant<int, 2 * P + 1>{}, fin + ((Fp::hit ? 2 * P + 2 : 2 * P + 1) * N + sp));
+    fn(std::integral_constant<int, 2 * P + 2>{}, fin + ((Fm::hit ? 2 * P + 1 : 2 * P + 2) * N + sm));
+  });
+}
+
+// Streamed populations of a node within 3 layers of an r-wall of a channel
+// periodic in x3 (nr >= 7), through the per-layer constant folds.
+template <class S, class R>
+__device__ __forceinline__ void gather_edge(const S* __restrict__ fin, const CellPos& p, const Dims& d,
+                                            R (&f)[Q]) {
+  using Cd = Codec<S, R>;
+  auto put = [&](auto L_, const S* src) {
+    constexpr int L = decltype(L_)::value;
+    f[L] = Cd::template dec<L>(__ldg(src));
+  };
+  put(std::integral_constant<int, 0>{}, fin + uint32_t(p.cell));
+  const int side = p.ir < 3 ? 0 : 1;
+  const int j = side == 0 ? p.ir : d.nr - 1 - p.ir;
+  switch (side * 3 + j) {
+    case 0: for_each_source_layer<0, 0>(fin, p, d, put); break;
+    case 1: for_each_source_layer<0, 1>(fin, p, d, put); break;
+    case 2: for_each_source_layer<0, 2>(fin, p, d, put); break;
+    case 3: for_each_source_layer<1, 0>(fin, p, d, put); break;
+    case 4: for_each_source_layer<1, 1>(fin, p, d, put); break;
+    default: for_each_source_layer<1, 2>(fin, p, d, put); break;
   }
 }
 
