@@ -35,7 +35,7 @@ BYTES_PER_UPDATE = {"fp64": 2 * 41 * 8, "fp32": 2 * 41 * 4, "fp16_shifted": 2 * 
                     "bf16_shifted": 2 * 41 * 2}
 DTYPE = {"fp64": "f64", "fp32": "f32", "fp16_shifted": "f16 storage / f32 math",
          "bf16_shifted": "bf16 storage / f32 math"}
-PROFILE_FILE = os.path.join(ROOT, "profiles", "k_step_fp32_cyl64x4x256_b24.md")
+PROFILE_FILE = os.path.join(ROOT, "profiles", "k_step_split_fp32_cyl64x4x256_b24.md")
 KERNEL_SOURCES = ["paper_1411_3133_gb300/csrc/lbm_device.cuh", "paper_1411_3133_gb300/csrc/kernels.cuh",
                   "paper_1411_3133_gb300/csrc/step_launch.cuh", "paper_1411_3133_gb300/csrc/step_f32.cu",
                   "paper_1411_3133_gb300/csrc/lattice.cuh"]
