@@ -65,8 +65,10 @@ typedef enum {
   LB_FP64 = 0,          /* populations and arithmetic in FP64 */
   LB_FP32 = 1,          /* populations and arithmetic in FP32 */
   LB_FP16_SHIFTED = 2,  /* populations stored in FP16 as the scaled deviation
-                           (f_l - w_l) / w_l from the rest state at rho' = 1;
-                           FP32 arithmetic */
+                           (f_l - r_l) / w_l from a reference population r_l
+                           per geometry row (LB_OPT_STORAGE_REFERENCE: the
+                           initial rows' equilibria, or w_l); FP32
+                           arithmetic */
   LB_BF16_SHIFTED = 3   /* the same deviation stored in BF16; FP32 arithmetic */
 } lb_precision;
 
@@ -158,8 +160,23 @@ typedef enum {
                                blocks per SM) x (SMs) blocks that walks the
                                tile list. Both give bitwise identical
                                states. */
-  LB_OPT_NODES_PER_THREAD = 5 /* nodes per thread of the prefetching step
+  LB_OPT_NODES_PER_THREAD = 5, /* nodes per thread of the prefetching step
                                kernel (1..64; default 4) */
+  LB_OPT_STORAGE_REFERENCE = 6 /* FP16/BF16 storage only: the reference
+                               r_l of the stored deviation (f_l - r_l)/w_l.
+                               0: r_l = w_l (the rest state of unit
+                               density); 1 (default): the equilibrium of
+                               each geometry row's initial state -- lb_init:
+                               rho' = 1/sqrt(g) and the laminar profile where
+                               init_base_flow is set, rest otherwise;
+                               lb_init_fields: the row means of the given
+                               fields. The
+                               small perturbations of an instability are
+                               then stored as small numbers. Changing it
+                               requires lb_init again (LB_ERR_STATE until
+                               then); state bytes (lb_get_state) are
+                               deviations from the reference of the last
+                               initialisation. */
 } lb_option;
 
 /* One configuration measured by lb_autotune / lb_batch_autotune. */

@@ -455,6 +455,11 @@ lb_status lb_create_geometry(lb_metric metric, const lb_geometry_desc* geom, int
   c->partial = static_cast<double*>(dalloc(c, size_t(batch) * c->nblk * DIAG_NQ * sizeof(double)));
   c->diag_out = static_cast<double*>(dalloc(c, size_t(batch) * DIAG_NQ * sizeof(double)));
   c->flag = static_cast<int*>(dalloc(c, sizeof(int)));
+  if (c->elem_bytes == 2) {
+    c->ref_tab = static_cast<float*>(dalloc(c, size_t(batch) * Q * nrows * sizeof(float)));
+    if (!c->ref_tab) return bail(LB_ERR_CUDA, "device allocation failed");
+    d.ref = c->ref_tab;
+  }
   if (!c->f[0] || !c->f[1] || !c->geo_real || !c->geo64 || !c->sqrtg || !c->base_uth || !c->ini ||
       !c->inst || !c->rho_s || !c->u_s || !c->rowmean || !c->partial || !c->diag_out || !c->flag)
     return bail(LB_ERR_CUDA, "device allocation failed");
@@ -531,6 +536,9 @@ lb_status lb_init(lb_ctx* c, const lb_params* p) {
   LB_CUDA(c, cudaMemcpyAsync(c->ini, ini.data(), ini.size() * sizeof(InitInst), cudaMemcpyHostToDevice,
                              c->stream));
   c->cur = 0;
+  if (c->ref_tab)
+    LB_CUDA(c, launch_ref_table(c->K, c->ref_tab, c->geo_f, c->sqrtg, any_base ? c->base_uth : nullptr, nullptr,
+                                nullptr, c->dims, c->ref_mode, c->stream));
   LB_CUDA(c, launch_init(int(c->prec), c->K, c->f[0], geo_ptr(c), c->sqrtg,
                          any_base ? c->base_uth : nullptr, c->ini, nullptr, nullptr, c->dims, c->stream));
   return reset_after_init(c);
@@ -550,6 +558,9 @@ lb_status lb_init_fields(lb_ctx* c, const lb_params* p, const double* rho, const
     du = c->u_s;
   }
   c->cur = 0;
+  if (c->ref_tab)
+    LB_CUDA(c, launch_ref_table(c->K, c->ref_tab, c->geo_f, c->sqrtg, nullptr, drho, du, c->dims, c->ref_mode,
+                                c->stream));
   LB_CUDA(c, launch_init(int(c->prec), c->K, c->f[0], geo_ptr(c), c->sqrtg, nullptr, c->ini,
                          drho, du, c->dims, c->stream));
   return reset_after_init(c);
@@ -665,7 +676,7 @@ lb_status lb_get_populations(lb_ctx* c, double* f, int on_device) {
       if (!c->dbl_stage) return fail(c, LB_ERR_CUDA, "staging allocation failed");
       dst = c->dbl_stage;
     }
-    LB_CUDA(c, launch_convert(int(c->prec), 1, c->f[c->cur], dst, n, c->ncell, c->stream));
+    LB_CUDA(c, launch_convert(int(c->prec), 1, c->f[c->cur], dst, n, c->dims, c->stream));
     if (!on_device)
       LB_CUDA(c, cudaMemcpyAsync(f, dst, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   }
@@ -689,7 +700,7 @@ lb_status lb_set_populations(lb_ctx* c, const double* f, int on_device) {
       LB_CUDA(c, cudaMemcpyAsync(c->dbl_stage, f, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
       src = c->dbl_stage;
     }
-    LB_CUDA(c, launch_convert(int(c->prec), 0, c->f[0], const_cast<double*>(src), n, c->ncell, c->stream));
+    LB_CUDA(c, launch_convert(int(c->prec), 0, c->f[0], const_cast<double*>(src), n, c->dims, c->stream));
   }
   const long long keep = c->step;
   lb_status s = reset_after_init(c);
@@ -748,6 +759,12 @@ lb_status lb_set_option(lb_ctx* c, int option, long long value) {
     case LB_OPT_NODES_PER_THREAD:
       if (value < 1 || value > 64) return fail(c, LB_ERR_ARG, "need 1..64 nodes per thread");
       c->nodes_per_thread = int(value);
+      return LB_OK;
+    case LB_OPT_STORAGE_REFERENCE:
+      if (value < 0 || value > 1) return fail(c, LB_ERR_ARG, "need 0 (weights) or 1 (initial rows)");
+      if (c->elem_bytes != 2) return fail(c, LB_ERR_ARG, "only the 2-byte storage formats have a reference");
+      if (int(value) != c->ref_mode) c->initialized = false;  // the stored deviations change meaning
+      c->ref_mode = int(value);
       return LB_OK;
     default:
       return fail(c, LB_ERR_ARG, "unknown option");

@@ -42,29 +42,41 @@ cudaError_t init_t(int K, S* f, const GeoDev<Real>& geo, const double* sqrtg, co
 // weights by population index, for the element-wise conversions
 __constant__ double c_weight[Q];
 
-__device__ __forceinline__ double to_f(double v, double) { return v; }
-__device__ __forceinline__ double to_f(float v, double) { return v; }
-__device__ __forceinline__ double to_f(__half v, double w) { return w * (1.0 + double(__half2float(v))); }
-__device__ __forceinline__ double to_f(__nv_bfloat16 v, double w) {
-  return w * (1.0 + double(__bfloat162float(v)));
+// stored value <-> f_l (2-byte formats: f = w s + r, Codec)
+__device__ __forceinline__ double to_f(double v, double, double) { return v; }
+__device__ __forceinline__ double to_f(float v, double, double) { return v; }
+__device__ __forceinline__ double to_f(__half v, double w, double r) { return w * double(__half2float(v)) + r; }
+__device__ __forceinline__ double to_f(__nv_bfloat16 v, double w, double r) {
+  return w * double(__bfloat162float(v)) + r;
 }
-__device__ __forceinline__ void from_f(double& o, double f, double) { o = f; }
-__device__ __forceinline__ void from_f(float& o, double f, double) { o = float(f); }
-__device__ __forceinline__ void from_f(__half& o, double f, double w) { o = __double2half(f / w - 1.0); }
-__device__ __forceinline__ void from_f(__nv_bfloat16& o, double f, double w) {
-  o = __double2bfloat16(f / w - 1.0);
+__device__ __forceinline__ void from_f(double& o, double f, double, double) { o = f; }
+__device__ __forceinline__ void from_f(float& o, double f, double, double) { o = float(f); }
+__device__ __forceinline__ void from_f(__half& o, double f, double w, double r) { o = __double2half((f - r) / w); }
+__device__ __forceinline__ void from_f(__nv_bfloat16& o, double f, double w, double r) {
+  o = __double2bfloat16((f - r) / w);
 }
 
 // state (documented population layout) <-> FP64 populations
 template <typename S>
-__global__ void k_convert(S* state, double* dbl, size_t n, size_t ncell, int to_double) {
+__global__ void k_convert(S* state, double* dbl, size_t n, Dims d, int to_double) {
+  const size_t N = size_t(d.ncell), layer = size_t(d.nt) * size_t(d.n3);
+  const size_t nrows = size_t(d.nr) * size_t(d.geo_rows3);
   for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n;
        i += size_t(gridDim.x) * blockDim.x) {
-    const double w = c_weight[(i / ncell) % Q];
+    const size_t bl = i / N;  // b * Q + l
+    const double w = c_weight[bl % Q];
+    double r = 0.0;
+    if (d.ref) {  // the reference table's layout of ref_index
+      const size_t cell = i - bl * N, b = bl / Q, l = bl % Q;
+      const size_t ir = cell / layer;
+      const float* rb = d.ref + b * Q * nrows;
+      r = d.geo_rows3 > 1 ? double(rb[l * nrows + ir * size_t(d.geo_rows3) + cell % size_t(d.n3)])
+                          : double(rb[ir * Q + l]);
+    }
     if (to_double)
-      dbl[i] = to_f(state[i], w);
+      dbl[i] = to_f(state[i], w, r);
     else
-      from_f(state[i], dbl[i], w);
+      from_f(state[i], dbl[i], w, r);
   }
 }
 
@@ -219,7 +231,7 @@ cudaError_t launch_init(int prec, int K, void* f, const void* geo, const double*
   }
 }
 
-cudaError_t launch_convert(int prec, int to_double, void* state, double* dbl, size_t n, size_t ncell,
+cudaError_t launch_convert(int prec, int to_double, void* state, double* dbl, size_t n, const Dims& d,
                            cudaStream_t s) {
   static bool weights_set = false;
   if (!weights_set) {
@@ -233,13 +245,27 @@ cudaError_t launch_convert(int prec, int to_double, void* state, double* dbl, si
   const size_t want = (n + threads - 1) / threads;
   const int blocks = int(want < 152 * 16 ? (want ? want : 1) : 152 * 16);
   switch (prec) {
-    case 0: k_convert<double><<<blocks, threads, 0, s>>>(static_cast<double*>(state), dbl, n, ncell, to_double); break;
-    case 1: k_convert<float><<<blocks, threads, 0, s>>>(static_cast<float*>(state), dbl, n, ncell, to_double); break;
-    case 2: k_convert<__half><<<blocks, threads, 0, s>>>(static_cast<__half*>(state), dbl, n, ncell, to_double); break;
+    case 0: k_convert<double><<<blocks, threads, 0, s>>>(static_cast<double*>(state), dbl, n, d, to_double); break;
+    case 1: k_convert<float><<<blocks, threads, 0, s>>>(static_cast<float*>(state), dbl, n, d, to_double); break;
+    case 2: k_convert<__half><<<blocks, threads, 0, s>>>(static_cast<__half*>(state), dbl, n, d, to_double); break;
     case 3:
-      k_convert<__nv_bfloat16><<<blocks, threads, 0, s>>>(static_cast<__nv_bfloat16*>(state), dbl, n, ncell,
+      k_convert<__nv_bfloat16><<<blocks, threads, 0, s>>>(static_cast<__nv_bfloat16*>(state), dbl, n, d,
                                                           to_double);
       break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ref_table(int K, float* ref, const GeoDev<float>& geo, const double* sqrtg,
+                             const double* base_uth, const double* rho_in, const double* u_in, const Dims& d,
+                             int mode, cudaStream_t s) {
+  const uint32_t n = uint32_t(d.batch) * uint32_t(d.nr) * uint32_t(d.geo_rows3);
+  const uint32_t nb = (n + 255) / 256;
+  switch (K) {
+    case KFLAT: k_ref_table<KFLAT><<<nb, 256, 0, s>>>(ref, geo, sqrtg, base_uth, rho_in, u_in, d, mode); break;
+    case KCYL: k_ref_table<KCYL><<<nb, 256, 0, s>>>(ref, geo, sqrtg, base_uth, rho_in, u_in, d, mode); break;
+    case KELL: k_ref_table<KELL><<<nb, 256, 0, s>>>(ref, geo, sqrtg, base_uth, rho_in, u_in, d, mode); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

@@ -95,6 +95,7 @@ ListInst<S, R> record(const lb_ctx* c, int bi, int cur, const GeoDev<R>& geo) {
   ListInst<S, R> r{};
   r.d = c->dims;
   r.d.batch = 1;
+  if (c->dims.ref) r.d.ref = c->dims.ref + size_t(bi) * Q * size_t(c->dims.nr) * size_t(c->dims.geo_rows3);
   r.geo = geo;
   r.ip = static_cast<const InstParams<R>*>(c->inst) + bi;
   const size_t off = size_t(bi) * Q * c->ncell;

@@ -45,6 +45,8 @@ struct lb_ctx {
   double* partial = nullptr;       // [batch * nblk * DIAG_NQ]
   double* diag_out = nullptr;      // [batch * DIAG_NQ]
   double* dbl_stage = nullptr;     // conversion staging (FP32 populations), lazily allocated
+  float* ref_tab = nullptr;        // 2-byte storage: reference populations [batch][Q][rows]
+  int ref_mode = 1;                // LB_OPT_STORAGE_REFERENCE
   int* flag = nullptr;
   int nblk = 0;
 

@@ -12,9 +12,9 @@ namespace lbgm {
 // forcing, BGK, store into the instance block fout. flag is set to 1 when
 // the node's density is not finite.
 template <typename S, typename Real, int K>
-__device__ __forceinline__ void collide_store(Real (&f)[Q], S* __restrict__ fout, const GeoDev<Real>& geo,
-                                              const InstParams<Real>& ip, const Dims& d, const CellPos& p,
-                                              int* __restrict__ flag) {
+__device__ __forceinline__ void collide_store(Real (&f)[Q], S* __restrict__ fout, const float* ref,
+                                              const GeoDev<Real>& geo, const InstParams<Real>& ip, const Dims& d,
+                                              const CellPos& p, int* __restrict__ flag) {
   const Moments<Real> m = moments(f);
   if (!finite_v(m.rho)) {  // NaN or Inf
     if (*flag == 0) atomicExch(flag, 1);
@@ -23,28 +23,27 @@ __device__ __forceinline__ void collide_store(Real (&f)[Q], S* __restrict__ fout
   const NodeGeo<Real, K> g = load_geo<Real, K>(geo, row);
   const Coef<Real> k = coefficients<Real, K>(m, g, ip.kappa, ip.G);
   collide<Real, K>(f, k, g, ip.omega);
-  store_node(fout, uint32_t(p.cell), uint32_t(d.ncell), f);
+  store_node<K>(fout, ref, p, d, f);
 }
 
 // Fused time step of one node p of one instance whose state blocks start at
-// fin and fout: pull streaming + walls, then collide_store.
+// fin and fout (reference table ref): pull streaming + walls, then
+// collide_store.
 template <typename S, typename Real, int K, int WALLS = 2>
-__device__ __forceinline__ void step_node(const S* __restrict__ fin, S* __restrict__ fout,
+__device__ __forceinline__ void step_node(const S* __restrict__ fin, S* __restrict__ fout, const float* ref,
                                           const GeoDev<Real>& geo, const InstParams<Real>& ip, const Dims& d,
                                           const CellPos& p, int* __restrict__ flag) {
   Real f[Q];
-  gather<S, Real, WALLS>(fin, p, d, f);
-  collide_store<S, Real, K>(f, fout, geo, ip, d, p, flag);
+  gather<K, S, Real, WALLS>(fin, ref, p, d, f);
+  collide_store<S, Real, K>(f, fout, ref, geo, ip, d, p, flag);
 }
 
-// Uniform batch: fin/fout are whole states (batch blocks of Q * ncell);
-// block (x, y) updates nodes [x blockDim, (x + 1) blockDim) of instance y, so
-// the instance's block base is uniform across the thread block.
 // Launch bounds of k_step per storage / compute type. FP32 arithmetic: at
-// most 128 threads per block and 6 (FP32 storage) or 7 (2-byte storage)
-// resident blocks per SM, i.e. a register cap that trades a few spilled
-// values for more resident warps (the kernel is bound by latency and issue,
-// not by HBM alone; measured best of 5..8). FP64 keeps its registers (bound
+// most 128 threads per block and 6 (FP32 storage) or 5 (2-byte storage,
+// which also reads reference populations) resident blocks per SM, i.e. a
+// register cap that trades a few spilled values for more resident warps
+// (the kernel is bound by latency and issue, not by HBM alone; measured best
+// of 5..8). FP64 keeps its registers (bound
 // by the FP64 units). LBGM_STEP32_MAXT / LBGM_STEP32_MINB / LBGM_STEP16_MINB
 // override the FP32 values for tuning builds.
 #ifndef LBGM_STEP32_MAXT
@@ -54,7 +53,7 @@ __device__ __forceinline__ void step_node(const S* __restrict__ fin, S* __restri
 #define LBGM_STEP32_MINB 6
 #endif
 #ifndef LBGM_STEP16_MINB
-#define LBGM_STEP16_MINB 7
+#define LBGM_STEP16_MINB 5
 #endif
 template <class S, class Real>
 struct StepBounds {
@@ -65,16 +64,19 @@ template <>
 struct StepBounds<double, double> {
   static constexpr int maxt = 256, minb = 1;
 };
+// Uniform batch: fin/fout are whole states (batch blocks of Q * ncell);
+// block (x, y) updates nodes [x blockDim, (x + 1) blockDim) of instance y, so
+// the instance's block base is uniform across the thread block.
 template <typename S, typename Real, int K>
-__global__ void __launch_bounds__(StepBounds<S, Real>::maxt, StepBounds<S, Real>::minb) k_step(const S* __restrict__ fin, S* __restrict__ fout,
-                                              GeoDev<Real> geo, const InstParams<Real>* __restrict__ inst,
-                                              Dims d, int* __restrict__ flag) {
+__global__ void __launch_bounds__(StepBounds<S, Real>::maxt, StepBounds<S, Real>::minb)
+    k_step(const S* __restrict__ fin, S* __restrict__ fout, GeoDev<Real> geo,
+           const InstParams<Real>* __restrict__ inst, Dims d, int* __restrict__ flag) {
   const uint32_t cell = blockIdx.x * blockDim.x + threadIdx.x;
   if (cell >= uint32_t(d.ncell)) return;
   const int b = int(blockIdx.y);
   const CellPos p = locate_cell(d, b, cell);
   const size_t base = size_t(b) * Q * uint32_t(d.ncell);
-  step_node<S, Real, K>(fin + base, fout + base, geo, inst[b], d, p, flag);
+  step_node<S, Real, K>(fin + base, fout + base, ref_of(d, b), geo, inst[b], d, p, flag);
 }
 
 // The same update split by region for channels periodic in x3, where only
@@ -92,7 +94,7 @@ __global__ void __launch_bounds__(StepBounds<S, Real>::maxt, StepBounds<S, Real>
   const int b = int(blockIdx.y);
   const CellPos p = locate_cell(d, b, cell);
   const size_t base = size_t(b) * Q * uint32_t(d.ncell);
-  step_node<S, Real, K, 0>(fin + base, fout + base, geo, inst[b], d, p, flag);
+  step_node<S, Real, K, 0>(fin + base, fout + base, ref_of(d, b), geo, inst[b], d, p, flag);
 }
 
 template <typename S, typename Real, int K>
@@ -106,9 +108,10 @@ __global__ void __launch_bounds__(StepBounds<S, Real>::maxt, StepBounds<S, Real>
   const int b = int(blockIdx.y);
   const CellPos p = locate_cell(d, b, cell);
   const size_t base = size_t(b) * Q * uint32_t(d.ncell);
+  const float* ref = ref_of(d, b);
   Real f[Q];
-  gather_edge(fin + base, p, d, f);
-  collide_store<S, Real, K>(f, fout + base, geo, inst[b], d, p, flag);
+  gather_edge<K>(fin + base, ref, p, d, f);
+  collide_store<S, Real, K>(f, fout + base, ref, geo, inst[b], d, p, flag);
 }
 
 // One instance of a batch whose instances differ in geometry and size: its
@@ -152,7 +155,7 @@ __global__ void __launch_bounds__(256) k_step_list(const ListInst<S, Real>* __re
       const CellPos p = locate(d, t);
       const S* fin = parity ? I.f1 : I.f0;
       S* fout = const_cast<S*>(parity ? I.f0 : I.f1);
-      step_node<S, Real, K>(fin, fout, I.geo, *I.ip, d, p, I.flag);
+      step_node<S, Real, K>(fin, fout, d.ref, I.geo, *I.ip, d, p, I.flag);
     }
   }
 }
@@ -186,13 +189,15 @@ template <>
 struct AsyncUnit<__half> {
   using T = uint32_t;
   static constexpr bool half = true;
-  __device__ static __forceinline__ __half from_bits(unsigned short b) { return __ushort_as_half(b); }
+  __device__ static __forceinline__ float to_float(unsigned short b) { return __half2float(__ushort_as_half(b)); }
 };
 template <>
 struct AsyncUnit<__nv_bfloat16> {
   using T = uint32_t;
   static constexpr bool half = true;
-  __device__ static __forceinline__ __nv_bfloat16 from_bits(unsigned short b) { return __ushort_as_bfloat16(b); }
+  __device__ static __forceinline__ float to_float(unsigned short b) {
+    return __bfloat162float(__ushort_as_bfloat16(b));
+  }
 };
 
 // Prefetching step: thread j of block B updates the nodes
@@ -202,7 +207,9 @@ struct AsyncUnit<__nv_bfloat16> {
 // flight during the arithmetic without holding registers. A thread reads only
 // slots it filled itself after its own wait_group: no block barrier. For
 // 2-byte storage a 64-bit mask records which half of each copied word holds
-// the population. Shared memory: 2 * Q * blockDim * sizeof(unit) bytes.
+// the population, and the reference population of each source row is copied
+// alongside. Shared memory: (2-byte storage: 2 x) 2 * Q * blockDim *
+// sizeof(unit) bytes.
 template <typename S, typename Real, int K>
 __global__ void __launch_bounds__(256) k_step_async(const S* __restrict__ fin, S* __restrict__ fout,
                                                     GeoDev<Real> geo, const InstParams<Real>* __restrict__ inst,
@@ -212,6 +219,7 @@ __global__ void __launch_bounds__(256) k_step_async(const S* __restrict__ fin, S
   extern __shared__ __align__(16) unsigned char smem_raw[];
   U* sm = reinterpret_cast<U*>(smem_raw);
   const uint32_t bd = blockDim.x, tid = threadIdx.x;
+  float* sref = reinterpret_cast<float*>(sm + 2 * Q * bd);  // 2-byte storage: [buffer][l][j] references
   const uint32_t total = uint32_t(d.batch) * uint32_t(d.ncell);
   const uint32_t first = blockIdx.x * uint32_t(npt) * bd + tid;
   uint64_t sel_next = 0;
@@ -219,12 +227,15 @@ __global__ void __launch_bounds__(256) k_step_async(const S* __restrict__ fin, S
     if (t >= total) return;
     const CellPos p = locate(d, t);
     U* slot = sm + buf * Q * bd + tid;
-    for_each_source(fin + size_t(p.b) * Q * d.ncell, p, d, [&](auto L_, const S* src) {
+    float* rslot = sref + buf * Q * bd + tid;
+    const float* ref = ref_of(d, p.b);
+    for_each_source<K>(fin + size_t(p.b) * Q * d.ncell, p, d, [&](auto L_, const S* src, int sl, int row) {
       constexpr int L = decltype(L_)::value;
       if constexpr (AsyncUnit<S>::half) {
         const uintptr_t a = reinterpret_cast<uintptr_t>(src);
         sel_next |= uint64_t((a >> 1) & 1u) << L;
         cp_async_elem(slot + L * bd, reinterpret_cast<const uint32_t*>(a & ~uintptr_t(3)));
+        cp_async_elem(rslot + L * bd, ref + ref_index<K>(d, sl, row));
       } else {
         cp_async_elem(slot + L * bd, src);
       }
@@ -246,18 +257,20 @@ __global__ void __launch_bounds__(256) k_step_async(const S* __restrict__ fin, S
     }
     const CellPos p = locate(d, t);
     const U* slot = sm + (uint32_t(k) & 1u) * Q * bd + tid;
+    const float* rslot = sref + (uint32_t(k) & 1u) * Q * bd + tid;
     Real f[Q];
     static_for<0, Q>([&](auto L_) {
       constexpr int L = decltype(L_)::value;
       const U w = slot[L * bd];
       if constexpr (AsyncUnit<S>::half) {
         const unsigned short h = (sel >> L) & 1u ? (unsigned short)(w >> 16) : (unsigned short)(w & 0xffffu);
-        f[L] = Cd::template dec<L>(AsyncUnit<S>::from_bits(h));
+        // the reference was copied into shared memory: decode from there
+        f[L] = fmaf(float(WeightOf<L>::w), float(AsyncUnit<S>::to_float(h)), rslot[L * bd]);
       } else {
-        f[L] = Cd::template dec<L>(w);
+        f[L] = Cd::template dec<L>(w, nullptr);
       }
     });
-    collide_store<S, Real, K>(f, fout + size_t(p.b) * Q * d.ncell, geo, inst[p.b], d, p, flag);
+    collide_store<S, Real, K>(f, fout + size_t(p.b) * Q * d.ncell, ref_of(d, p.b), geo, inst[p.b], d, p, flag);
   }
   cp_async_wait<0>();  // nothing of this thread stays in flight at exit
 }
@@ -270,7 +283,7 @@ __global__ void __launch_bounds__(256) k_macros(const S* __restrict__ fin, doubl
   if (t >= uint32_t(d.batch) * uint32_t(d.ncell)) return;
   const CellPos p = locate(d, t);
   Real f[Q];
-  gather(fin + size_t(p.b) * Q * d.ncell, p, d, f);
+  gather<K>(fin + size_t(p.b) * Q * d.ncell, ref_of(d, p.b), p, d, f);
   const Moments<Real> m = moments(f);
   const double r = double(m.rho);
   if (rho) rho[t] = r;
@@ -331,7 +344,59 @@ __global__ void __launch_bounds__(256) k_init(S* __restrict__ f, GeoDev<Real> ge
   const NodeGeo<Real, K> g = load_geo<Real, K>(geo, row);
   Real fe[Q];
   equilibrium<Real, K>(Real(rho), Real(u[0]), Real(u[1]), Real(u[2]), g, fe);
-  store_node(f + size_t(p.b) * Q * d.ncell, uint32_t(p.cell), uint32_t(d.ncell), fe);
+  store_node<K>(f + size_t(p.b) * Q * d.ncell, ref_of(d, p.b), p, d, fe);
+}
+
+// Reference populations of 2-byte storage (Codec): for instance b and
+// geometry row r, mode 0: r_l = w_l (the rest state of unit density);
+// mode 1: the equilibrium f^eq(rho', u) of the row's initial state: with
+// caller fields (rho_in, u_in non-NULL) their mean over the row's nodes,
+// else rho' = 1/sqrt(g) and u = (0, base(b, i_r), 0) (rest where base is
+// NULL). Written at ref_index<K> of instance b's table.
+template <int K>
+__global__ void __launch_bounds__(256) k_ref_table(float* __restrict__ ref, GeoDev<float> geo,
+                                                   const double* __restrict__ sqrtg,
+                                                   const double* __restrict__ base_uth,
+                                                   const double* __restrict__ rho_in,
+                                                   const double* __restrict__ u_in, Dims d, int mode) {
+  const uint32_t nrows = uint32_t(d.nr) * uint32_t(d.geo_rows3);
+  const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= uint32_t(d.batch) * nrows) return;
+  const uint32_t b = t / nrows, row = t - b * nrows;
+  const int ir = int(row) / d.geo_rows3, i3 = int(row) - ir * d.geo_rows3;
+  float fe[Q];
+  if (mode == 0) {
+    static_for<0, Q>([&](auto L_) {
+      constexpr int L = decltype(L_)::value;
+      fe[L] = float(WeightOf<L>::w);
+    });
+  } else if (rho_in) {
+    // mean over the row's nodes: all (i_theta, i_3) of layer i_r, or all
+    // i_theta of (i_r, i_3) for the ellipsoid's rows
+    double rs = 0.0, us[3] = {0.0, 0.0, 0.0};
+    const int n3s = d.geo_rows3 > 1 ? 1 : d.n3;
+    int cnt = 0;
+    for (int it = 0; it < d.nt; ++it)
+      for (int k3 = 0; k3 < n3s; ++k3) {
+        const size_t cell = (size_t(ir) * d.nt + it) * d.n3 + (d.geo_rows3 > 1 ? i3 : k3);
+        rs += rho_in[size_t(b) * d.ncell + cell];
+        const size_t ub = size_t(b) * 3 * d.ncell + cell;
+        us[0] += u_in[ub];
+        us[1] += u_in[ub + d.ncell];
+        us[2] += u_in[ub + 2 * size_t(d.ncell)];
+        ++cnt;
+      }
+    const NodeGeo<float, K> g = load_geo<float, K>(geo, int(row));
+    equilibrium<float, K>(float(rs / cnt), float(us[0] / cnt), float(us[1] / cnt), float(us[2] / cnt), g, fe);
+  } else {
+    const double rho = 1.0 / sqrtg[ir * d.n3 + i3];
+    const double uth = base_uth ? base_uth[size_t(b) * d.nr + ir] : 0.0;
+    const NodeGeo<float, K> g = load_geo<float, K>(geo, int(row));
+    equilibrium<float, K>(float(rho), 0.0f, float(uth), 0.0f, g, fe);
+  }
+  float* rb = ref + size_t(b) * Q * nrows;
+#pragma unroll
+  for (int l = 0; l < Q; ++l) rb[ref_index<K>(d, l, int(row))] = fe[l];
 }
 
 }  // namespace lbgm

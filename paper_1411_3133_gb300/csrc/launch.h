@@ -86,8 +86,14 @@ cudaError_t launch_macros(int prec, int K, const void* fin, double* rho, double*
 cudaError_t launch_init(int prec, int K, void* f, const void* geo, const double* sqrtg,
                         const double* base_uth, const InitInst* ini, const double* rho_in,
                         const double* u_in, const Dims& d, cudaStream_t s);
-cudaError_t launch_convert(int prec, int to_double, void* state, double* dbl, size_t n, size_t ncell,
+cudaError_t launch_convert(int prec, int to_double, void* state, double* dbl, size_t n, const Dims& d,
                            cudaStream_t s);
+// Reference populations of 2-byte storage (k_ref_table): mode 0 weights,
+// 1 the initial rows' equilibria (from the row means of rho_in / u_in if
+// given, else base_uth, which may be NULL: rest).
+cudaError_t launch_ref_table(int K, float* ref, const GeoDev<float>& geo, const double* sqrtg,
+                             const double* base_uth, const double* rho_in, const double* u_in, const Dims& d,
+                             int mode, cudaStream_t s);
 
 // Observables: NQ sums per instance written to out[batch * DIAG_NQ].
 constexpr int DIAG_NQ = 9;

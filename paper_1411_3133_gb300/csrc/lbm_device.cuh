@@ -48,7 +48,34 @@ struct Dims {
   int batch;
   int geo_rows3;   // n3 for the ellipsoid's (r, x3) rows, 1 otherwise
   FastDiv div_ncell, div_n3, div_nt;
+  // 2-byte storage: reference populations over the nr * geo_rows3 geometry
+  // rows, per instance (ref_index; NULL for FP32 / FP64 storage)
+  const float* ref;
 };
+
+// Index of reference population l of geometry row r in an instance's table:
+// row-major [r][l] where rows are i_r only (cylinder, flat: a warp shares
+// the row, and the offsets of a node's 41 entries are compile-time
+// constants), population-major [l][r] for the ellipsoid's (i_r, i_3) rows
+// (consecutive nodes read consecutive rows).
+template <int K>
+__device__ __forceinline__ uint32_t ref_index(const Dims& d, int l, int row) {
+  if constexpr (K == KELL) return uint32_t(l) * uint32_t(d.nr) * uint32_t(d.geo_rows3) + uint32_t(row);
+  else return uint32_t(row) * 41u + uint32_t(l);
+}
+
+// Geometry row of node (i_r, i_3): i_r * n3 + i_3 for the ellipsoid, i_r
+// otherwise.
+template <int K>
+__device__ __forceinline__ int geo_row(const Dims& d, int ir, int i3) {
+  if constexpr (K == KELL) return ir * d.geo_rows3 + i3;
+  else return ir;
+}
+
+// Reference table of instance b (see Dims::ref).
+__device__ __forceinline__ const float* ref_of(const Dims& d, int b) {
+  return d.ref ? d.ref + size_t(b) * 41 * size_t(d.nr) * size_t(d.geo_rows3) : nullptr;
+}
 
 // Geometry rows in the compute precision. A row is i_r * geo_rows3 + i_3 (or
 // i_r). Only the components that are non-zero for the metric kind are read:
@@ -129,39 +156,44 @@ struct WeightOf {
 // ---------------------------------------------------------------------------
 // Codec<S, R> reads populations stored as S into the compute type R and back.
 // For the reduced-precision formats the stored value is the scaled deviation
-// (f_l - w_l rho_ref) / w_l with rho_ref = 1, so every population's stored
-// number is O(u/cs) whatever its weight; f_l = w_l (1 + s_l).
+// (f_l - r_l) / w_l from a reference population r_l of the storing node's
+// geometry row (a table entry, passed as a pointer), so every stored number
+// is small whatever its weight: f_l = w_l s_l + r_l. With r_l = w_l this is
+// the deviation from the rest state of unit density.
 template <class S, class R>
 struct Codec {
+  static constexpr bool uses_ref = false;
   template <int L>
-  __device__ static __forceinline__ R dec(S v) { return R(v); }
+  __device__ static __forceinline__ R dec(S v, const float*) { return R(v); }
   template <int L>
-  __device__ static __forceinline__ S enc(R f) { return S(f); }
+  __device__ static __forceinline__ S enc(R f, const float*) { return S(f); }
 };
 template <>
 struct Codec<__half, float> {
+  static constexpr bool uses_ref = true;
   template <int L>
-  __device__ static __forceinline__ float dec(__half v) {
+  __device__ static __forceinline__ float dec(__half v, const float* ref) {
     constexpr float w = float(WeightOf<L>::w);
-    return fmaf(w, __half2float(v), w);
+    return fmaf(w, __half2float(v), __ldg(ref));
   }
   template <int L>
-  __device__ static __forceinline__ __half enc(float f) {
+  __device__ static __forceinline__ __half enc(float f, const float* ref) {
     constexpr float iw = float(1.0 / WeightOf<L>::w);
-    return __float2half_rn(fmaf(f, iw, -1.0f));
+    return __float2half_rn((f - __ldg(ref)) * iw);
   }
 };
 template <>
 struct Codec<__nv_bfloat16, float> {
+  static constexpr bool uses_ref = true;
   template <int L>
-  __device__ static __forceinline__ float dec(__nv_bfloat16 v) {
+  __device__ static __forceinline__ float dec(__nv_bfloat16 v, const float* ref) {
     constexpr float w = float(WeightOf<L>::w);
-    return fmaf(w, __bfloat162float(v), w);
+    return fmaf(w, __bfloat162float(v), __ldg(ref));
   }
   template <int L>
-  __device__ static __forceinline__ __nv_bfloat16 enc(float f) {
+  __device__ static __forceinline__ __nv_bfloat16 enc(float f, const float* ref) {
     constexpr float iw = float(1.0 / WeightOf<L>::w);
-    return __float2bfloat16_rn(fmaf(f, iw, -1.0f));
+    return __float2bfloat16_rn((f - __ldg(ref)) * iw);
   }
 };
 
@@ -210,7 +242,7 @@ __device__ __forceinline__ int src_far(const Neighbours& n, const Dims& d) {
 // one time step means moving 2 s towards negative Q; each fold flips the
 // population to its opposite.
 template <int CX, int CY, int CZ, int S>
-__device__ __forceinline__ int src_wall(const CellPos& p, const Dims& d, bool& flip) {
+__device__ __forceinline__ int src_wall(const CellPos& p, const Dims& d, bool& flip, int& src_ir, int& src_i3) {
   constexpr int sx = (CX > 0) - (CX < 0), sy = (CY > 0) - (CY < 0), sz = (CZ > 0) - (CZ < 0);
   int lo = -(1 << 30), hi = (1 << 30);
   if constexpr (sx != 0) {
@@ -248,6 +280,8 @@ __device__ __forceinline__ int src_wall(const CellPos& p, const Dims& d, bool& f
   const int yt = wrap_small(p.it + q * sy, d.nt);
   int yz = p.i3 + q * sz;
   if (d.periodic3) yz = wrap_small(yz, d.n3);
+  src_ir = yr;
+  src_i3 = yz;
   return (yr * d.nt + yt) * d.n3 + yz;
 }
 
@@ -255,14 +289,18 @@ __device__ __forceinline__ bool near_wall(const CellPos& p, const Dims& d) {
   return p.ir < 3 || p.ir > d.nr - 4 || (!d.periodic3 && (p.i3 < 3 || p.i3 > d.n3 - 4));
 }
 
-// Visit the sources of the 41 streamed populations of node p: fn(L, src)
-// with L a std::integral_constant (the population received) and src the
-// address in fin (one instance's block: population l of cell c at
-// fin[l * ncell + c]) of the post-collision value it is streamed from. Near a
-// wall every moving population comes from its (possibly folded) source;
-// opposite velocities share their weight, so a folded population decodes
-// with the weight of the pair.
-template <class S, class Fn>
+// Visit the sources of the 41 streamed populations of node p: fn(L, src,
+// sl, row) with L a std::integral_constant (the population received), src
+// the address in fin (one instance's block: population l of cell c at
+// fin[l * ncell + c]) of the post-collision value it is streamed from, sl
+// the population index stored there (L, or its opposite after a fold) and
+// row the geometry row of the node that stored it (sl and row select the
+// reference population of 2-byte storage). Near a wall every moving
+// population comes from its (possibly folded) source; opposite velocities
+// share their weight. Offsets are
+// 32-bit: an instance block holds fewer than 2^32 bytes (checked when the
+// context is created).
+template <int K, class S, class Fn>
 __device__ __forceinline__ void for_each_source_far(const S* __restrict__ fin, const CellPos& p, const Dims& d,
                                                     Fn&& fn) {
   const uint32_t N = uint32_t(d.ncell);
@@ -273,12 +311,14 @@ __device__ __forceinline__ void for_each_source_far(const S* __restrict__ fin, c
     using C = Pair<P>;
     const uint32_t sp = uint32_t(src_far<C::x, C::y, C::z>(nb, d));
     const uint32_t sm = uint32_t(src_far<-C::x, -C::y, -C::z>(nb, d));
-    fn(std::integral_constant<int, 2 * P + 1>{}, fin + ((2 * P + 1) * N + sp));
-    fn(std::integral_constant<int, 2 * P + 2>{}, fin + ((2 * P + 2) * N + sm));
+    fn(std::integral_constant<int, 2 * P + 1>{}, fin + ((2 * P + 1) * N + sp), 2 * P + 1,
+       geo_row<K>(d, p.ir - C::x, nb.zcol[C::z + 3]));
+    fn(std::integral_constant<int, 2 * P + 2>{}, fin + ((2 * P + 2) * N + sm), 2 * P + 2,
+       geo_row<K>(d, p.ir + C::x, nb.zcol[-C::z + 3]));
   });
 }
 
-template <class S, class Fn>
+template <int K, class S, class Fn>
 __device__ __forceinline__ void for_each_source_wall(const S* __restrict__ fin, const CellPos& p, const Dims& d,
                                                      Fn&& fn) {
   const uint32_t N = uint32_t(d.ncell);
@@ -286,30 +326,30 @@ __device__ __forceinline__ void for_each_source_wall(const S* __restrict__ fin, 
     constexpr int P = decltype(P_)::value;
     using C = Pair<P>;
     bool fp, fm;
-    const uint32_t sp = uint32_t(src_wall<C::x, C::y, C::z, C::s>(p, d, fp));
-    const uint32_t sm = uint32_t(src_wall<-C::x, -C::y, -C::z, C::s>(p, d, fm));
-    fn(std::integral_constant<int, 2 * P + 1>{}, fin + ((fp ? 2 * P + 2 : 2 * P + 1) * N + sp));
-    fn(std::integral_constant<int, 2 * P + 2>{}, fin + ((fm ? 2 * P + 1 : 2 * P + 2) * N + sm));
+    int rp, zp, rm, zm;
+    const uint32_t sp = uint32_t(src_wall<C::x, C::y, C::z, C::s>(p, d, fp, rp, zp));
+    const uint32_t sm = uint32_t(src_wall<-C::x, -C::y, -C::z, C::s>(p, d, fm, rm, zm));
+    const int lp = fp ? 2 * P + 2 : 2 * P + 1, lm = fm ? 2 * P + 1 : 2 * P + 2;
+    fn(std::integral_constant<int, 2 * P + 1>{}, fin + (lp * N + sp), lp, geo_row<K>(d, rp, zp));
+    fn(std::integral_constant<int, 2 * P + 2>{}, fin + (lm * N + sm), lm, geo_row<K>(d, rm, zm));
   });
 }
 
-// Offsets are 32-bit: an instance block holds fewer than 2^32 bytes
-// (checked when the context is created). WALLS selects the code paths
-// compiled in: 0 far from every wall only, 1 near a wall only, 2 both (the
-// node decides).
-template <class S, int WALLS = 2, class Fn>
+// WALLS selects the code paths compiled in: 0 far from every wall only, 1
+// near a wall only, 2 both (the node decides).
+template <int K, class S, int WALLS = 2, class Fn>
 __device__ __forceinline__ void for_each_source(const S* __restrict__ fin, const CellPos& p, const Dims& d,
                                                 Fn&& fn) {
-  fn(std::integral_constant<int, 0>{}, fin + uint32_t(p.cell));
+  fn(std::integral_constant<int, 0>{}, fin + uint32_t(p.cell), 0, geo_row<K>(d, p.ir, p.i3));
   if constexpr (WALLS == 0) {
-    for_each_source_far(fin, p, d, fn);
+    for_each_source_far<K>(fin, p, d, fn);
   } else if constexpr (WALLS == 1) {
-    for_each_source_wall(fin, p, d, fn);
+    for_each_source_wall<K>(fin, p, d, fn);
   } else {
     if (!near_wall(p, d))
-      for_each_source_far(fin, p, d, fn);
+      for_each_source_far<K>(fin, p, d, fn);
     else
-      for_each_source_wall(fin, p, d, fn);
+      for_each_source_wall<K>(fin, p, d, fn);
   }
 }
 
@@ -328,7 +368,7 @@ struct LayerFold {
   static constexpr int dx = q * sx, dy = q * sy, dz = q * sz;  // source - node
 };
 
-template <int SIDE, int J, class S, class Fn>
+template <int K, int SIDE, int J, class S, class Fn>
 __device__ __forceinline__ void for_each_source_layer(const S* __restrict__ fin, const CellPos& p,
                                                       const Dims& d, Fn&& fn) {
   const uint32_t N = uint32_t(d.ncell);
@@ -341,53 +381,72 @@ __device__ __forceinline__ void for_each_source_layer(const S* __restrict__ fin,
     using Fm = LayerFold<SIDE, J, -C::x, -C::y, -C::z, C::s>;
     const uint32_t sp = uint32_t((nb.rrow[3 - Fp::dx] + nb.tcol[3 - Fp::dy]) * d.n3 + nb.zcol[3 - Fp::dz]);
     const uint32_t sm = uint32_t((nb.rrow[3 - Fm::dx] + nb.tcol[3 - Fm::dy]) * d.n3 + nb.zcol[3 - Fm::dz]);
-    fn(std::integral_constant<int, 2 * P + 1>{}, fin + ((Fp::hit ? 2 * P + 2 : 2 * P + 1) * N + sp));
-    fn(std::integral_constant<int, 2 * P + 2>{}, fin + ((Fm::hit ? 2 * P + 1 : 2 * P + 2) * N + sm));
+    constexpr int lp = Fp::hit ? 2 * P + 2 : 2 * P + 1, lm = Fm::hit ? 2 * P + 1 : 2 * P + 2;
+    fn(std::integral_constant<int, 2 * P + 1>{}, fin + (lp * N + sp), lp,
+       geo_row<K>(d, p.ir + Fp::dx, nb.zcol[3 - Fp::dz]));
+    fn(std::integral_constant<int, 2 * P + 2>{}, fin + (lm * N + sm), lm,
+       geo_row<K>(d, p.ir + Fm::dx, nb.zcol[3 - Fm::dz]));
   });
 }
+
+// Decoding visitor: f[L] from the stored value at src, with the reference
+// row table ref (instance base; NULL for FP32 / FP64 storage).
+template <int K, class S, class R>
+struct DecodeInto {
+  R (&f)[Q];
+  const float* ref;
+  const Dims& d;
+  template <class LC>
+  __device__ __forceinline__ void operator()(LC, const S* src, int sl, int row) const {
+    constexpr int L = LC::value;
+    if constexpr (Codec<S, R>::uses_ref)
+      f[L] = Codec<S, R>::template dec<L>(__ldg(src), ref + ref_index<K>(d, sl, row));
+    else
+      f[L] = Codec<S, R>::template dec<L>(__ldg(src), nullptr);
+  }
+};
 
 // Streamed populations of a node within 3 layers of an r-wall of a channel
 // periodic in x3 (nr >= 7), through the per-layer constant folds.
-template <class S, class R>
-__device__ __forceinline__ void gather_edge(const S* __restrict__ fin, const CellPos& p, const Dims& d,
-                                            R (&f)[Q]) {
-  using Cd = Codec<S, R>;
-  auto put = [&](auto L_, const S* src) {
-    constexpr int L = decltype(L_)::value;
-    f[L] = Cd::template dec<L>(__ldg(src));
-  };
-  put(std::integral_constant<int, 0>{}, fin + uint32_t(p.cell));
+template <int K, class S, class R>
+__device__ __forceinline__ void gather_edge(const S* __restrict__ fin, const float* ref, const CellPos& p,
+                                            const Dims& d, R (&f)[Q]) {
+  DecodeInto<K, S, R> put{f, ref, d};
+  put(std::integral_constant<int, 0>{}, fin + uint32_t(p.cell), 0, geo_row<K>(d, p.ir, p.i3));
   const int side = p.ir < 3 ? 0 : 1;
   const int j = side == 0 ? p.ir : d.nr - 1 - p.ir;
   switch (side * 3 + j) {
-    case 0: for_each_source_layer<0, 0>(fin, p, d, put); break;
-    case 1: for_each_source_layer<0, 1>(fin, p, d, put); break;
-    case 2: for_each_source_layer<0, 2>(fin, p, d, put); break;
-    case 3: for_each_source_layer<1, 0>(fin, p, d, put); break;
-    case 4: for_each_source_layer<1, 1>(fin, p, d, put); break;
-    default: for_each_source_layer<1, 2>(fin, p, d, put); break;
+    case 0: for_each_source_layer<K, 0, 0>(fin, p, d, put); break;
+    case 1: for_each_source_layer<K, 0, 1>(fin, p, d, put); break;
+    case 2: for_each_source_layer<K, 0, 2>(fin, p, d, put); break;
+    case 3: for_each_source_layer<K, 1, 0>(fin, p, d, put); break;
+    case 4: for_each_source_layer<K, 1, 1>(fin, p, d, put); break;
+    default: for_each_source_layer<K, 1, 2>(fin, p, d, put); break;
   }
 }
 
-// Load the 41 streamed populations of node p from the post-collision state.
-template <class S, class R, int WALLS = 2>
-__device__ __forceinline__ void gather(const S* __restrict__ fin, const CellPos& p,
+// Load the 41 streamed populations of node p from the post-collision state
+// (instance block fin, reference table ref).
+template <int K, class S, class R, int WALLS = 2>
+__device__ __forceinline__ void gather(const S* __restrict__ fin, const float* ref, const CellPos& p,
                                        const Dims& d, R (&f)[Q]) {
-  using Cd = Codec<S, R>;
-  for_each_source<S, WALLS>(fin, p, d, [&](auto L_, const S* src) {
-    constexpr int L = decltype(L_)::value;
-    f[L] = Cd::template dec<L>(__ldg(src));
-  });
+  for_each_source<K, S, WALLS>(fin, p, d, DecodeInto<K, S, R>{f, ref, d});
 }
 
-// Store the 41 post-collision populations of node `cell` into the instance
-// block `out` (32-bit offsets, as for_each_source).
-template <class S, class R>
-__device__ __forceinline__ void store_node(S* __restrict__ out, uint32_t cell, uint32_t N, const R (&f)[Q]) {
+// Store the 41 post-collision populations of node p into the instance block
+// `out` (32-bit offsets, as for_each_source).
+template <int K, class S, class R>
+__device__ __forceinline__ void store_node(S* __restrict__ out, const float* ref, const CellPos& p, const Dims& d,
+                                           const R (&f)[Q]) {
   using Cd = Codec<S, R>;
+  const uint32_t N = uint32_t(d.ncell), cell = uint32_t(p.cell);
+  const int row = geo_row<K>(d, p.ir, p.i3);
   static_for<0, Q>([&](auto L_) {
     constexpr int L = decltype(L_)::value;
-    out[uint32_t(L) * N + cell] = Cd::template enc<L>(f[L]);
+    if constexpr (Cd::uses_ref)
+      out[uint32_t(L) * N + cell] = Cd::template enc<L>(f[L], ref + ref_index<K>(d, L, row));
+    else
+      out[uint32_t(L) * N + cell] = Cd::template enc<L>(f[L], nullptr);
   });
 }
 

@@ -10,7 +10,10 @@ namespace {
 template <class S, class R, int K>
 cudaError_t launch_k(const S* fin, S* fout, const GeoDev<R>& geo, const InstParams<R>* inst, const Dims& d,
                      int* flag, int threads, int npt, cudaStream_t s) {
-  const size_t smem = 2 * size_t(Q) * threads * sizeof(typename AsyncUnit<S>::T);
+  // two buffers of Q units per thread, and for 2-byte storage as many
+  // reference values (k_step_async's `sref`)
+  const size_t smem = 2 * size_t(Q) * threads * sizeof(typename AsyncUnit<S>::T) *
+                      (Codec<S, R>::uses_ref ? 2 : 1);
   static size_t opted[64] = {};  // per device: largest dynamic shared memory enabled so far
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);

@@ -170,7 +170,7 @@ __global__ void __launch_bounds__(NX, 512 / NX) k_step_tma(const __grid_constant
         f[2 * P + 2] = st[(2 * P + 2) * NX + xs[-C::z + 3]];
       });
     } else {
-      gather(fin + size_t(p.b) * Q * d.ncell, p, d, f);
+      gather<K>(fin + size_t(p.b) * Q * d.ncell, static_cast<const float*>(nullptr), p, d, f);
     }
     __syncwarp();
     if (lane == 0) mbar_arrive(&empty[s]);

@@ -26,7 +26,7 @@ STATUS_NAMES = {0: "LB_OK", 1: "LB_ERR_ARG", 2: "LB_ERR_CUDA", 3: "LB_ERR_NONFIN
 METRICS = {"flat": 0, "cylindrical": 1, "ellipsoidal": 2}
 PRECISIONS = {"fp64": 0, "fp32": 1, "fp16_shifted": 2, "bf16_shifted": 3}
 LB_OPT_CHECK_EVERY, LB_OPT_BLOCK_THREADS, LB_OPT_USE_GRAPH, LB_OPT_STEP_KERNEL = 0, 1, 2, 3
-LB_OPT_SCHEDULE, LB_OPT_NODES_PER_THREAD = 4, 5
+LB_OPT_SCHEDULE, LB_OPT_NODES_PER_THREAD, LB_OPT_STORAGE_REFERENCE = 4, 5, 6
 
 
 class lb_geometry_desc(ctypes.Structure):

@@ -418,12 +418,15 @@ def test_tma_kernel_option_validation():
                                 Channel("ellipsoidal", 1.0, 1.1, 12, 4, 40, b=0.9, periodic3=False)],
                          ids=["cyl", "ell"])
 def test_reduced_precision_storage_against_fp64_oracle(ch, prec, tol):
-    """Populations stored as FP16/BF16 deviations (f - w)/w, FP32 arithmetic:
-    u within tol * u_max of the FP64 oracle after 1, 10 and 100 steps for a
-    flow of realistic magnitude (u_max ~ 0.05). FP16 meets the 1e-3 target;
-    BF16's 8-bit mantissa gives about 1e-2."""
+    """Populations stored as FP16/BF16 deviations (f - w)/w from the rest
+    state (reference mode 0), FP32 arithmetic: u within tol * u_max of the
+    FP64 oracle after 1, 10 and 100 steps for a flow of realistic magnitude
+    (u_max ~ 0.05). FP16 meets the 1e-3 target; BF16's 8-bit mantissa gives
+    about 1e-2."""
+    L = lib()
     params = [dict(tau=0.8, G=G_LAMINAR)]
     tw = Twin(ch, params, prec)
+    tw.ctx.lb_set_option(L.LB_OPT_STORAGE_REFERENCE, 0)
     rho = np.stack([1.0 / tw.sims[0].sqrtg])
     u = (_smooth_flow(ch) + noise_field(31, tw.N, 1e-3))[None]
     tw.init_fields(rho, u)
@@ -435,10 +438,54 @@ def test_reduced_precision_storage_against_fp64_oracle(ch, prec, tol):
     tw.close()
 
 
+@pytest.mark.parametrize("prec,tol", [("fp16_shifted", 1e-4), ("bf16_shifted", 1e-3)])
+@pytest.mark.parametrize("ch", [Channel("cylindrical", 1.0, 1 / ETA, 16, 4, 64),
+                                Channel("ellipsoidal", 1.0, 1.1, 12, 4, 40, b=0.9, periodic3=False)],
+                         ids=["cyl", "ell"])
+def test_reduced_precision_with_row_reference(ch, prec, tol):
+    """The default reference (mode 1): deviations from the equilibrium of the
+    rows' mean initial state. The flow's row profile is then stored exactly
+    in FP32 and only the departures from it in 2 bytes: an order of magnitude
+    closer to the FP64 oracle than mode 0 for the same flow."""
+    params = [dict(tau=0.8, G=G_LAMINAR)]
+    tw = Twin(ch, params, prec)
+    rho = np.stack([1.0 / tw.sims[0].sqrtg])
+    u = (_smooth_flow(ch) + noise_field(31, tw.N, 1e-3))[None]
+    tw.init_fields(rho, u)
+    done = 0
+    for n in (1, 10, 100):
+        tw.step(n - done)
+        done = n
+        er, eu = _compare_macros(tw, tol, tol)
+        print(ch.metric, prec, n, er, eu)
+    tw.close()
+
+
+def test_storage_reference_option():
+    L = lib()
+    tw = Twin(CYL1, [dict(tau=0.8, G=1e-4, seed=2, amp=1e-3)], "fp32")
+    with pytest.raises(L.LBError) as e:
+        tw.ctx.lb_set_option(L.LB_OPT_STORAGE_REFERENCE, 0)    # FP32 has no reference
+    assert e.value.status == L.LB_ERR_ARG
+    tw.close()
+    tw = Twin(CYL1, [dict(tau=0.8, G=1e-4, seed=2, amp=1e-3)], "fp16_shifted")
+    tw.ctx.lb_init(tw.lparams)
+    tw.ctx.lb_set_option(L.LB_OPT_STORAGE_REFERENCE, 0)        # changes meaning: re-init needed
+    with pytest.raises(L.LBError) as e:
+        tw.ctx.lb_step(1)
+    assert e.value.status == L.LB_ERR_STATE
+    with pytest.raises(L.LBError) as e:
+        tw.ctx.lb_set_option(L.LB_OPT_STORAGE_REFERENCE, 2)
+    assert e.value.status == L.LB_ERR_ARG
+    tw.ctx.lb_init(tw.lparams)
+    tw.ctx.lb_step(2)
+    tw.close()
+
+
 @pytest.mark.parametrize("prec", ["fp16_shifted", "bf16_shifted"])
 def test_reduced_precision_state_round_trips(prec):
     L = lib()
-    tw = Twin(CYL1, [dict(tau=0.8, G=1e-4, seed=2, amp=1e-3)], prec)
+    tw = Twin(CYL1, [dict(tau=0.8, G=1e-4, seed=2, amp=1e-3, base=True)], prec)
     tw.ctx.lb_init(tw.lparams)
     tw.ctx.lb_step(5)
     assert tw.ctx.lb_state_bytes() == 41 * tw.N * 2
