@@ -18,9 +18,13 @@ formula above, with exact first and second derivatives by hyper-dual
 used here; the tests compare against them.
 
 Readings (where the paper is silent or ambiguous):
-  * Node positions: r = r_i + (i_r + 1/2) h, i_r = 0..N_r-1, so that walls sit
-    halfway between nodes exactly at r_i and r_o and d = r_o - r_i = N_r h.
-    The third axis is centred: x3 = (i_3 + 1/2 - N_3/2) h in scaled units.
+  * Node positions, bounce-back walls: r = r_i + (i_r + 1/2) h, i_r =
+    0..N_r-1, so that walls sit halfway between nodes exactly at r_i and r_o
+    and d = r_o - r_i = N_r h. The third axis is centred: x3 = (i_3 + 1/2 -
+    N_3/2) h in scaled units.
+  * Node positions, equilibrium (Dirichlet) walls as in Sec. III: the first
+    and last node of a walled axis lie on the walls, r = r_i + i_r h with
+    d = (N_r - 1) h; a walled third axis likewise x3 = (i_3 - (N_3 - 1)/2) h.
   * Rescaled spacings: scaled coordinates y^i with x^i = s_i y^i, s = (1,
     dtheta_scale, d3_scale), so that every lattice spacing is h. The chain
     rule through the embedding gives the scaled metric and symbols.
@@ -165,6 +169,9 @@ class Channel:
     periodic3     True: periodic third axis (z or phi); False: walls there too
     dtheta_scale  Delta theta / h   (1 except in Sec. IV.B's rescaling)
     d3_scale      Delta x3 / h
+    wall          'bounceback' (walls halfway outside the end nodes) or
+                  'equilibrium' (the end nodes are wall nodes held at
+                  f^eq(rho', u = 0), Sec. III)
     """
     metric: str
     r_inner: float
@@ -176,9 +183,12 @@ class Channel:
     periodic3: bool = True
     dtheta_scale: float = 1.0
     d3_scale: float = 1.0
+    wall: str = "bounceback"
 
     @property
     def h(self) -> float:
+        if self.wall == "equilibrium":
+            return (self.r_outer - self.r_inner) / (self.nr - 1)
         return (self.r_outer - self.r_inner) / self.nr
 
     @property
@@ -210,8 +220,12 @@ def node_coordinates(ch: Channel):
     h = ch.h
     ir = np.arange(ch.nr)
     i3 = np.arange(ch.n3)
-    yr = ch.r_inner + (ir + 0.5) * h
-    y3 = (i3 + 0.5 - ch.n3 / 2.0) * h
+    if ch.wall == "equilibrium":
+        yr = ch.r_inner + ir * h
+        y3 = (i3 + 0.5 - ch.n3 / 2.0) * h if ch.periodic3 else (i3 - (ch.n3 - 1) / 2.0) * h
+    else:
+        yr = ch.r_inner + (ir + 0.5) * h
+        y3 = (i3 + 0.5 - ch.n3 / 2.0) * h
     R, Y3 = np.meshgrid(yr, y3, indexing="ij")
     pts = np.stack([R, np.zeros_like(R), Y3], axis=-1).reshape(-1, 3)
     return pts

@@ -29,6 +29,13 @@ Readings:
     folded path ends after one time unit. ``_trace_source`` follows the path
     backwards from the destination with exact rational arithmetic.
   * "Old" forcing (the paper's comparison method): a2 = a2^eq.
+  * Equilibrium walls (the paper's own Dirichlet condition, Sec. III: f^eq
+    evaluated with u = 0 at r_i and r_o every step): the end nodes of a
+    walled axis lie on the walls; after streaming, a wall node's populations
+    are replaced by f^eq(rho', 0) of its own density and metric (no BGK
+    relaxation, no forcing). A population whose source x - c lies beyond a
+    wall is taken from the wall node of the same line (the source clamped
+    onto the wall layer), i.e. nodes outside hold the wall's equilibrium.
 
 Oracle module: test infrastructure only (see ``oracle/__init__.py``).
 """
@@ -96,6 +103,9 @@ class StreamMap:
         nr, nt, n3 = dims
         cells = np.arange(ch.ncells)
         x = np.stack(np.unravel_index(cells, dims), axis=1)       # (n, 3)
+        if ch.wall == "equilibrium":
+            self._init_clamped(x, dims, walled)
+            return
         # The traced path depends only on the coordinates along walled axes,
         # and not even on those when the node is at least 3 nodes away from
         # both walls (|c| <= 3 cannot reach a wall 3.5 away). Trace one
@@ -124,6 +134,22 @@ class StreamMap:
                     y[:, a] %= dims[a]
             self.src_cell[l] = (y[:, 0] * nt + y[:, 1]) * n3 + y[:, 2]
             self.src_pop[l] = np.where(odd[inverse], L.OPPOSITE[l], l)
+
+    def _init_clamped(self, x, dims, walled):
+        """Equilibrium walls: source x - c, periodic axes wrapped, walled axes
+        clamped onto the wall layer; the population index is kept."""
+        nr, nt, n3 = dims
+        self.src_cell = np.empty((L.Q, len(x)), dtype=np.int64)
+        self.src_pop = np.empty((L.Q, len(x)), dtype=np.int64)
+        for l in range(L.Q):
+            y = x - L.C[l][None, :]
+            for a in range(3):
+                if walled[a]:
+                    y[:, a] = np.clip(y[:, a], 0, dims[a] - 1)
+                else:
+                    y[:, a] %= dims[a]
+            self.src_cell[l] = (y[:, 0] * nt + y[:, 1]) * n3 + y[:, 2]
+            self.src_pop[l] = l
 
     def apply(self, f):
         """f: (Q, ncells) -> streamed populations (Q, ncells)."""
@@ -249,6 +275,13 @@ class Simulation:
         self.Gamma_hat = cells(self.geo["Gamma_hat"])
         self.fext = params.G * cells(self.geo["fdir"])
         self.sqrtg = cells(self.geo["sqrtg"])
+        # wall nodes of the equilibrium-wall channel (end nodes of walled axes)
+        self.wall_nodes = np.zeros(ch.ncells, dtype=bool)
+        if ch.wall == "equilibrium":
+            x = np.stack(np.unravel_index(np.arange(ch.ncells), ch.shape), axis=1)
+            for a, w in enumerate(ch.walled):
+                if w:
+                    self.wall_nodes |= (x[:, a] == 0) | (x[:, a] == ch.shape[a] - 1)
         self.f = None
         self.t = 0
 
@@ -268,11 +301,19 @@ class Simulation:
     def streamed(self):
         return self.smap.apply(self.f)
 
+    def _collide(self, fs, cells=slice(None)):
+        out = collide(fs, self.Delta[cells], self.Gamma_hat[cells], self.fext[cells],
+                      self.p.tau, self.p.old_forcing)
+        wall = self.wall_nodes[cells]
+        if wall.any():  # Dirichlet walls: f^eq(rho', u = 0) of the wall node
+            rho, _ = moments(fs[:, wall])
+            out[:, wall] = equilibrium(rho, np.zeros((len(rho), 3)), self.Delta[cells][wall])
+        return out
+
     def step(self, n=1):
         for _ in range(n):
             fs = self.smap.apply(self.f)
-            self.f = collide(fs, self.Delta, self.Gamma_hat, self.fext,
-                             self.p.tau, self.p.old_forcing)
+            self.f = self._collide(fs)
             self.t += 1
 
     def step_cells(self, cells):
@@ -280,8 +321,7 @@ class Simulation:
         (Q, len(cells)); the state is not changed."""
         cells = np.asarray(cells)
         fs = self.f[self.smap.src_pop[:, cells], self.smap.src_cell[:, cells]]
-        return collide(fs, self.Delta[cells], self.Gamma_hat[cells], self.fext[cells],
-                       self.p.tau, self.p.old_forcing)
+        return self._collide(fs, cells)
 
     def macros(self):
         """(rho', u) of the streamed populations: shapes (n,), (n,3)."""
