@@ -72,11 +72,31 @@ typedef enum {
   LB_BF16_SHIFTED = 3   /* the same deviation stored in BF16; FP32 arithmetic */
 } lb_precision;
 
+/* Wall condition of the walled axes (r, and x3 when periodic3 == 0). */
+typedef enum {
+  LB_WALL_BOUNCEBACK = 0,  /* walls halfway outside the first and last node;
+                              populations reflected along their one-step
+                              path (full bounce-back) */
+  LB_WALL_EQUILIBRIUM = 1  /* the paper's Dirichlet walls (Sec. III: zero
+                              wall velocity imposed through the
+                              equilibrium on both walls at every step):
+                              the first and last node lie on the
+                              walls and leave every step as f^eq(rho', 0)
+                              of their own density; a population whose
+                              source lies beyond a wall is read from the
+                              wall node of the same line. First-order
+                              accurate; mass is not conserved exactly. */
+} lb_wall;
+
 /* Channel geometry (Sec. III lattice map; Sec. IV lattice map and the
  * rescaled spacings of Sec. IV.B).
- *   Nodes sit at r = r_inner + (i_r + 1/2) h, i_r = 0..nr-1, so that the walls
- *   are halfway outside the first and last node, exactly at r_inner and
- *   r_outer. The third axis is centred: x3 = (i_3 + 1/2 - n3/2) h * d3_scale.
+ *   LB_WALL_BOUNCEBACK: nodes at r = r_inner + (i_r + 1/2) h, i_r = 0..nr-1,
+ *   h = (r_outer - r_inner)/nr, so that the walls are halfway outside the
+ *   first and last node, exactly at r_inner and r_outer. The third axis is
+ *   centred: x3 = (i_3 + 1/2 - n3/2) h * d3_scale.
+ *   LB_WALL_EQUILIBRIUM: nodes at r = r_inner + i_r h, h = (r_outer -
+ *   r_inner)/(nr - 1) (wall nodes at both ends); a walled third axis
+ *   x3 = (i_3 - (n3 - 1)/2) h * d3_scale, a periodic one as above.
  *   The metric is evaluated at theta = 0 for every theta node (quasi-2-D
  *   channel, periodic in theta); the Christoffel symbols of both coordinate
  *   systems do not depend on theta. */
@@ -85,10 +105,13 @@ typedef struct {
                                (any r_inner < r_outer for FLAT) */
   double b;                 /* ellipsoid semi-axis b > 0; ignored otherwise */
   int nr, ntheta, n3;       /* nodes per axis: nr >= 7, ntheta >= 1, n3 >= 1
-                               (n3 >= 7 when periodic3 == 0) */
+                               (n3 >= 7 when periodic3 == 0) with
+                               bounce-back walls */
   int periodic3;            /* 1: periodic third axis; 0: walls there too */
   double dtheta_scale;      /* Delta theta / h (> 0; 1 unless rescaled) */
   double d3_scale;          /* Delta x3 / h (> 0; 1 unless rescaled) */
+  int wall;                 /* lb_wall (nr >= 3 and walled n3 >= 3 suffice
+                               for LB_WALL_EQUILIBRIUM) */
 } lb_geometry_desc;
 
 /* Per-instance run parameters (Sec. II; Sec. III for the driving force). */
@@ -143,12 +166,14 @@ typedef enum {
                                periodic and the arithmetic FP32, else 1;
                                1: the one-node-per-thread kernel, gathering
                                from global memory; 2: the TMA-pipelined
-                               kernel (FP32 and n3 in {128, 256} only);
+                               kernel (FP32, bounce-back walls and n3 in
+                               {128, 256} only);
                                3: the prefetching kernel: each thread updates
                                LB_OPT_NODES_PER_THREAD nodes and copies the
                                next node's sources into shared memory
                                (cp.async) while it computes the current one;
-                               4: the region split (periodic x3 only): one
+                               4: the region split (periodic x3 and
+                               bounce-back walls only): one
                                kernel for the 3 node layers next to each
                                r-wall, one for the interior without any
                                wall code.

@@ -20,6 +20,11 @@ Readings:
   * Derivatives are lattice-unit finite differences: central inside,
     second-order one-sided at the first and last node of a walled axis using
     u = 0 on the wall half a node away; periodic axes wrap.
+  * Equilibrium (Dirichlet) walls: the wall nodes' velocity is the wall
+    value 0 in every observable (their streamed moments are replaced in the
+    collision); derivatives at a wall node are the second-order one-sided
+    differences of the node values; the channel width in lattice units is
+    N_r - 1 (wall nodes at both ends) in the Dean number.
   * vortex amplitude = rms of u^r over all nodes; vortex_amp_x3 = rms of
     u^r minus its mean along x3 (the x3-periodic part that Dean vortices
     carry); max_speed = largest Euclidean norm of the coordinate velocity.
@@ -38,12 +43,17 @@ from . import lattice as L
 from .geometry import Channel
 
 
-def _d_axis(u, axis, walled):
-    """Derivative of u (nr, nt, n3) along an axis, lattice units."""
+def _d_axis(u, axis, walled, on_nodes=False):
+    """Derivative of u (nr, nt, n3) along an axis, lattice units; on_nodes:
+    the walls are the first and last node (equilibrium walls)."""
     n = u.shape[axis]
     u = np.moveaxis(u, axis, 0)
     d = np.empty_like(u)
-    if walled:
+    if walled and on_nodes:
+        d[1:-1] = 0.5 * (u[2:] - u[:-2])
+        d[0] = 0.5 * (-3.0 * u[0] + 4.0 * u[1] - u[2])
+        d[-1] = 0.5 * (3.0 * u[-1] - 4.0 * u[-2] + u[-3])
+    elif walled:
         if n == 1:
             d[0] = 0.0
         else:
@@ -68,6 +78,12 @@ def diagnostics(ch: Channel, geo: dict, tau: float, rho, u) -> dict:
     sqrtg, speed = cells(geo["sqrtg"]), cells(geo["speed"])
     wA, wOm = cells(geo["wA"]), cells(geo["wOmega"])
 
+    eqw = ch.wall == "equilibrium"
+    if eqw:  # wall nodes carry the Dirichlet velocity 0
+        u = u.copy()
+        u[0], u[-1] = 0.0, 0.0
+        if not ch.periodic3:
+            u[:, :, 0], u[:, :, -1] = 0.0, 0.0
     finite = np.isfinite(rho) & np.isfinite(u).all(axis=-1)
     out = {"nonfinite": int((~finite).sum())}
     out["mass_rho_prime"] = float(rho.sum())
@@ -77,9 +93,10 @@ def diagnostics(ch: Channel, geo: dict, tau: float, rho, u) -> dict:
     nu = (tau - 0.5) * L.CS2
     d = ch.r_outer - ch.r_inner
     R = ch.curvature_radius
-    out["dean"] = 0.0 if math.isinf(R) else vmean * ch.nr / nu * math.sqrt(d / R)
+    width = d / ch.h                                   # N_r, or N_r - 1 with wall nodes
+    out["dean"] = 0.0 if math.isinf(R) else vmean * width / nu * math.sqrt(d / R)
     walled = ch.walled
-    w = _d_axis(u[..., 0], 2, walled[2]) - _d_axis(u[..., 2], 0, walled[0])
+    w = _d_axis(u[..., 0], 2, walled[2], eqw) - _d_axis(u[..., 2], 0, walled[0], eqw)
     out["mean_vorticity"] = float((np.abs(w) * wOm).sum() / wA.sum())
     out["vortex_amp"] = float(np.sqrt((u[..., 0] ** 2).mean()))
     ur_fluct = u[..., 0] - u[..., 0].mean(axis=2, keepdims=True)

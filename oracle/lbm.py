@@ -29,8 +29,9 @@ Readings:
     folded path ends after one time unit. ``_trace_source`` follows the path
     backwards from the destination with exact rational arithmetic.
   * "Old" forcing (the paper's comparison method): a2 = a2^eq.
-  * Equilibrium walls (the paper's own Dirichlet condition, Sec. III: f^eq
-    evaluated with u = 0 at r_i and r_o every step): the end nodes of a
+  * Equilibrium walls (the paper's own Dirichlet condition, Sec. III: the
+    wall velocity 0 enters through the equilibrium on both walls at every
+    step): the end nodes of a
     walled axis lie on the walls; after streaming, a wall node's populations
     are replaced by f^eq(rho', 0) of its own density and metric (no BGK
     relaxation, no forcing). A population whose source x - c lies beyond a

@@ -237,7 +237,7 @@ cudaError_t launch_split(lb_ctx* c, int src, int dst) {
 // arithmetic is FP32 (measured fastest there), the one-kernel step otherwise.
 int resolved_kernel(const lb_ctx* c) {
   if (c->step_kernel != 0) return c->step_kernel;
-  return (c->geom.periodic3 && c->prec != LB_FP64) ? 4 : 1;
+  return (c->geom.periodic3 && c->geom.wall == LB_WALL_BOUNCEBACK && c->prec != LB_FP64) ? 4 : 1;
 }
 
 lb_status launch_step_once(lb_ctx* c) {
@@ -352,16 +352,15 @@ lb_status lb_force_for_dean(lb_metric metric, const lb_geometry_desc* geom, doub
   // De per unit force: mean over the nodes of v(r) for G = 1
   double A, B, C;
   curved_poiseuille(*geom, tau, 1.0, &A, &B, &C);
-  const double h = (geom->r_outer - geom->r_inner) / geom->nr;
   double vsum = 0.0;
   for (int i = 0; i < geom->nr; ++i) {
-    const double r = geom->r_inner + (i + 0.5) * h;
+    const double r = node_r(*geom, i);
     vsum += A * r * std::log(r) + B * r + C / r;
   }
   const double vmean = vsum / geom->nr;
   const double nu = (tau - 0.5) * CS2;
   const double d = geom->r_outer - geom->r_inner;
-  const double de_per_G = vmean * geom->nr / nu * std::sqrt(d / geom->r_inner);
+  const double de_per_G = vmean * (d / lattice_h(*geom)) / nu * std::sqrt(d / geom->r_inner);
   *G_out = De / de_per_G;
   return LB_OK;
 }
@@ -428,6 +427,7 @@ lb_status lb_create_geometry(lb_metric metric, const lb_geometry_desc* geom, int
   d.n3 = geom->n3;
   d.ncell = geom->nr * geom->ntheta * geom->n3;
   d.periodic3 = geom->periodic3 ? 1 : 0;
+  d.wall_eq = geom->wall == LB_WALL_EQUILIBRIUM ? 1 : 0;
   d.batch = batch;
   d.geo_rows3 = c->K == KELL ? geom->n3 : 1;
   d.div_ncell = FastDiv::make(uint32_t(d.ncell));
@@ -493,7 +493,8 @@ lb_status lb_create_geometry(lb_metric metric, const lb_geometry_desc* geom, int
   if (e == cudaSuccess) e = cudaMemsetAsync(c->flag, 0, sizeof(int), c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return bail(LB_ERR_CUDA, std::string("geometry upload: ") + cudaGetErrorString(e));
-  if (prec == LB_FP32 && tma_step_supported(d) && tensor_map_bytes() <= sizeof(c->tmap[0]))
+  if (prec == LB_FP32 && geom->wall == LB_WALL_BOUNCEBACK && tma_step_supported(d) &&
+      tensor_map_bytes() <= sizeof(c->tmap[0]))
     c->tma_ok = make_state_tensor_map(c->tmap[0], static_cast<const float*>(c->f[0]), d) == cudaSuccess &&
                 make_state_tensor_map(c->tmap[1], static_cast<const float*>(c->f[1]), d) == cudaSuccess;
   *out = c;
@@ -507,7 +508,7 @@ lb_status lb_init(lb_ctx* c, const lb_params* p) {
   const lb_geometry_desc& g = c->geom;
   std::vector<double> base(size_t(c->batch) * g.nr, 0.0);
   bool any_base = false;
-  const double h = (g.r_outer - g.r_inner) / g.nr;
+  const bool eqw = g.wall == LB_WALL_EQUILIBRIUM;
   for (int b = 0; b < c->batch; ++b) {
     if (!p[b].init_base_flow) continue;
     any_base = true;
@@ -516,12 +517,14 @@ lb_status lb_init(lb_ctx* c, const lb_params* p) {
     const double nu = (p[b].tau - 0.5) * CS2;
     for (int i = 0; i < g.nr; ++i) {
       if (c->metric == LB_METRIC_FLAT) {
-        // plane Poiseuille between walls at -1/2 and nr - 1/2 (lattice units)
-        base[size_t(b) * g.nr + i] = p[b].force_G / (2.0 * nu) * (i + 0.5) * (g.nr - 0.5 - i);
+        // plane Poiseuille between walls at -1/2 and nr - 1/2, or on the
+        // wall nodes 0 and nr - 1 (lattice units)
+        base[size_t(b) * g.nr + i] = eqw ? p[b].force_G / (2.0 * nu) * i * (g.nr - 1 - i)
+                                         : p[b].force_G / (2.0 * nu) * (i + 0.5) * (g.nr - 0.5 - i);
       } else {
         double A, B, C;
         curved_poiseuille(g, p[b].tau, p[b].force_G, &A, &B, &C);
-        const double r = g.r_inner + (i + 0.5) * h;
+        const double r = node_r(g, i);
         base[size_t(b) * g.nr + i] = (A * r * std::log(r) + B * r + C / r) / r;
       }
     }
@@ -642,6 +645,7 @@ lb_status lb_diagnostics(lb_ctx* c, lb_diag* out) {
   const lb_geometry_desc& g = c->geom;
   const double R = curvature_radius(c->metric, g);
   const double d = g.r_outer - g.r_inner;
+  const double width = d / lattice_h(g);  // channel width in lattice units
   const double N = double(c->ncell);
   for (int b = 0; b < c->batch; ++b) {
     const double* q = &h[size_t(b) * DIAG_NQ];
@@ -650,7 +654,7 @@ lb_status lb_diagnostics(lb_ctx* c, lb_diag* out) {
     o.mass_physical = q[1];
     o.mean_v_theta = q[2] / q[3];
     const double nu = (c->tau[b] - 0.5) * CS2;
-    o.dean = R > 0.0 ? o.mean_v_theta * g.nr / nu * std::sqrt(d / R) : 0.0;
+    o.dean = R > 0.0 ? o.mean_v_theta * width / nu * std::sqrt(d / R) : 0.0;
     o.mean_vorticity = q[4] / q[3];
     o.vortex_amp = std::sqrt(q[5] / N);
     o.vortex_amp_x3 = std::sqrt(q[6] / N);
@@ -750,8 +754,8 @@ lb_status lb_set_option(lb_ctx* c, int option, long long value) {
     case LB_OPT_STEP_KERNEL:
       if (value < 0 || value > 4)
         return fail(c, LB_ERR_ARG, "need 0 (auto), 1 (plain), 2 (TMA), 3 (prefetching) or 4 (region split)");
-      if (value == 4 && !c->geom.periodic3)
-        return fail(c, LB_ERR_ARG, "the region-split step kernel needs a periodic x3 axis");
+      if (value == 4 && (!c->geom.periodic3 || c->geom.wall != LB_WALL_BOUNCEBACK))
+        return fail(c, LB_ERR_ARG, "the region-split step kernel needs a periodic x3 axis and bounce-back walls");
       if (value == 2 && !c->tma_ok)
         return fail(c, LB_ERR_ARG, "the TMA step kernel needs FP32 and n3 in {128, 256}");
       c->step_kernel = int(value);
@@ -784,7 +788,7 @@ lb_status lb_autotune(lb_ctx* c, int steps_per_trial, lb_tune* best, lb_tune* tr
     for (int t : {64, 128, 192, 256}) cand.push_back({t, 1, 0, 0.0});
   else
     for (int t : {64, 96, 128}) cand.push_back({t, 1, 0, 0.0});
-  if (c->geom.periodic3)
+  if (c->geom.periodic3 && c->geom.wall == LB_WALL_BOUNCEBACK)
     for (int t : {64, 96, 128}) cand.push_back({t, 4, 0, 0.0});
   if (c->tma_ok) cand.push_back({0, 2, 0, 0.0});  // the TMA kernel fixes its own block shape
   for (int t : {128, 256})

@@ -80,6 +80,12 @@ __global__ void k_convert(S* state, double* dbl, size_t n, Dims d, int to_double
   }
 }
 
+// Equilibrium walls: the wall nodes' velocity is the Dirichlet value 0 in
+// every observable (their streamed moments are replaced in the collision).
+__device__ __forceinline__ bool eq_wall_node(const Dims& d, int ir, int i3) {
+  return d.wall_eq && (ir == 0 || ir == d.nr - 1 || (!d.periodic3 && (i3 == 0 || i3 == d.n3 - 1)));
+}
+
 // mean of u^r along x3 for every (instance, i_r, i_theta) row
 __global__ void k_rowmean(const double* __restrict__ u, double* __restrict__ rowmean, Dims d) {
   const int rows_per = d.nr * d.nt;
@@ -87,17 +93,26 @@ __global__ void k_rowmean(const double* __restrict__ u, double* __restrict__ row
   if (row >= d.batch * rows_per) return;
   const int b = row / rows_per;
   const int rr = row - b * rows_per;
+  const int ir = rr / d.nt;
   const double* ur = u + size_t(b) * 3 * d.ncell + size_t(rr) * d.n3;
   double s = 0.0;
-  for (int i = 0; i < d.n3; ++i) s += ur[i];
+  for (int i = 0; i < d.n3; ++i) s += eq_wall_node(d, ir, i) ? 0.0 : ur[i];
   rowmean[row] = s / d.n3;
 }
 
-// derivative along an axis from the values at offsets -1, 0, +1; the wall
-// version uses u = 0 half a node outside the first and last node.
-__device__ __forceinline__ double d_axis(double um, double u0, double up, int i, int n, bool walled) {
+// derivative along an axis from the values at offsets -2 .. +2 (u2m, um, u0,
+// up, u2p); the bounce-back wall version uses u = 0 half a node outside the
+// first and last node, the equilibrium-wall version second-order one-sided
+// differences at the wall nodes (whose value is 0).
+__device__ __forceinline__ double d_axis(double u2m, double um, double u0, double up, double u2p, int i, int n,
+                                         bool walled, bool eqw) {
   if (!walled) return 0.5 * (up - um);
   if (n == 1) return 0.0;
+  if (eqw) {
+    if (i == 0) return 0.5 * (-3.0 * u0 + 4.0 * up - u2p);
+    if (i == n - 1) return 0.5 * (3.0 * u0 - 4.0 * um + u2m);
+    return 0.5 * (up - um);
+  }
   if (i == 0) return u0 + up / 3.0;
   if (i == n - 1) return -(u0 + um / 3.0);
   return 0.5 * (up - um);
@@ -153,21 +168,26 @@ __global__ void __launch_bounds__(DIAG_THREADS)
     const double* gr = geo64 + size_t(ir * d.n3 + i3) * 4;
     const double sg = gr[0], sp = gr[1], wA = gr[2], wOm = gr[3];
     const double r = rb[c];
-    const double u0 = ur[c], u1 = ut[c], u2 = uz[c];
+    const bool eqw = d.wall_eq != 0;
+    // velocity component at node (jr, j3) of this theta plane: 0 on an
+    // equilibrium wall node and outside the node range
+    auto U = [&](const double* a, int jr, int j3) -> double {
+      if (jr < 0 || jr >= d.nr || j3 < 0 || j3 >= d.n3 || eq_wall_node(d, jr, j3)) return 0.0;
+      return a[(size_t(jr) * d.nt + it) * d.n3 + j3];
+    };
+    const double u0 = U(ur, ir, i3), u1 = U(ut, ir, i3), u2 = U(uz, ir, i3);
     // d_3 u^r
-    double um, up;
+    double d3ur;
     if (d.periodic3) {
-      um = ur[c - i3 + (i3 == 0 ? d.n3 - 1 : i3 - 1)];
-      up = ur[c - i3 + (i3 == d.n3 - 1 ? 0 : i3 + 1)];
+      const int jm = i3 == 0 ? d.n3 - 1 : i3 - 1, jp = i3 == d.n3 - 1 ? 0 : i3 + 1;
+      d3ur = d_axis(0.0, U(ur, ir, jm), u0, U(ur, ir, jp), 0.0, i3, d.n3, false, eqw);
     } else {
-      um = i3 > 0 ? ur[c - 1] : 0.0;
-      up = i3 < d.n3 - 1 ? ur[c + 1] : 0.0;
+      d3ur = d_axis(U(ur, ir, i3 - 2), U(ur, ir, i3 - 1), u0, U(ur, ir, i3 + 1), U(ur, ir, i3 + 2), i3, d.n3,
+                    true, eqw);
     }
-    const double d3ur = d_axis(um, u0, up, i3, d.n3, !d.periodic3);
     // d_r u^3 (walls on r)
-    const double zm = ir > 0 ? uz[c - plane] : 0.0;
-    const double zp = ir < d.nr - 1 ? uz[c + plane] : 0.0;
-    const double drz = d_axis(zm, u2, zp, ir, d.nr, true);
+    const double drz = d_axis(U(uz, ir - 2, i3), U(uz, ir - 1, i3), u2, U(uz, ir + 1, i3), U(uz, ir + 2, i3), ir,
+                              d.nr, true, eqw);
     const double fl = u0 - rowmean[(size_t(b) * d.nr + ir) * d.nt + it];
     a[0] += r;
     a[1] += sg * sg * r;

@@ -30,14 +30,21 @@ std::string validate_geometry(lb_metric metric, const lb_geometry_desc& g) {
     return "unknown metric";
   if (!(g.r_outer > g.r_inner)) return "need r_outer > r_inner";
   if (metric != LB_METRIC_FLAT && !(g.r_inner > 0.0)) return "need r_inner > 0";
-  if (g.nr < 7) return "need nr >= 7 (walls with |c| = 3 populations)";
+  if (g.wall != LB_WALL_BOUNCEBACK && g.wall != LB_WALL_EQUILIBRIUM) return "unknown wall condition";
+  const bool eq = g.wall == LB_WALL_EQUILIBRIUM;
+  if (eq) {
+    if (g.nr < 3) return "need nr >= 3 (two wall nodes and a fluid node)";
+  } else if (g.nr < 7) {
+    return "need nr >= 7 (walls with |c| = 3 populations)";
+  }
   if (g.ntheta < 1 || g.n3 < 1) return "need ntheta >= 1 and n3 >= 1";
-  if (!g.periodic3 && g.n3 < 7) return "need n3 >= 7 when the third axis has walls";
+  if (!g.periodic3 && g.n3 < (eq ? 3 : 7))
+    return eq ? "need n3 >= 3 when the third axis has walls" : "need n3 >= 7 when the third axis has walls";
   if (!(g.dtheta_scale > 0.0) || !(g.d3_scale > 0.0)) return "need positive dtheta_scale, d3_scale";
   if (metric == LB_METRIC_ELLIPSOIDAL) {
     if (!(g.b > 0.0)) return "need b > 0";
-    double h = (g.r_outer - g.r_inner) / g.nr;
-    double phmax = 0.5 * g.n3 * h * g.d3_scale;
+    const double h = lattice_h(g);
+    const double phmax = (eq && !g.periodic3 ? 0.5 * (g.n3 - 1) : 0.5 * g.n3) * h * g.d3_scale;
     if (!(phmax < 0.5 * M_PI)) {
       std::snprintf(buf, sizeof buf, "phi range +-%.4g reaches the pole (|phi| must stay < pi/2)",
                     phmax);
@@ -49,6 +56,19 @@ std::string validate_geometry(lb_metric metric, const lb_geometry_desc& g) {
   return "";
 }
 
+double lattice_h(const lb_geometry_desc& g) {
+  return (g.r_outer - g.r_inner) / (g.wall == LB_WALL_EQUILIBRIUM ? g.nr - 1 : g.nr);
+}
+
+double node_r(const lb_geometry_desc& g, int ir) {
+  return g.r_inner + (g.wall == LB_WALL_EQUILIBRIUM ? ir : ir + 0.5) * lattice_h(g);
+}
+
+double node_x3(const lb_geometry_desc& g, int i3) {
+  const bool on_walls = g.wall == LB_WALL_EQUILIBRIUM && !g.periodic3;
+  return (on_walls ? i3 - 0.5 * (g.n3 - 1) : i3 + 0.5 - 0.5 * g.n3) * lattice_h(g) * g.d3_scale;
+}
+
 double curvature_radius(lb_metric metric, const lb_geometry_desc& g) {
   if (metric == LB_METRIC_CYLINDRICAL) return g.r_inner;
   if (metric == LB_METRIC_ELLIPSOIDAL) return g.r_inner * g.b * g.b;
@@ -57,13 +77,13 @@ double curvature_radius(lb_metric metric, const lb_geometry_desc& g) {
 
 std::vector<double> evaluate_geometry(lb_metric metric, const lb_geometry_desc& gd) {
   const int nr = gd.nr, n3 = gd.n3;
-  const double h = (gd.r_outer - gd.r_inner) / nr;
+  const double h = lattice_h(gd);
   const double s[3] = {1.0, gd.dtheta_scale, gd.d3_scale};
   std::vector<double> out(size_t(nr) * n3 * LB_GEO_STRIDE, 0.0);
   for (int ir = 0; ir < nr; ++ir) {
-    const double r = gd.r_inner + (ir + 0.5) * h;
+    const double r = node_r(gd, ir);
     for (int i3 = 0; i3 < n3; ++i3) {
-      const double x3 = (i3 + 0.5 - 0.5 * n3) * h * gd.d3_scale;  // z or phi
+      const double x3 = node_x3(gd, i3);  // z or phi
       double g[3] = {1.0, 1.0, 1.0};                               // physical, diagonal at theta = 0
       double G[3][3][3] = {};                                      // physical Gamma^i_jk
       double wA = 1.0, wOm = 1.0;
@@ -111,7 +131,7 @@ void curved_poiseuille(const lb_geometry_desc& gd, double tau, double G, double*
   // solution is A r ln r with A = -G / (2 nu h^2).
   const double cs2 = 1.0 - std::sqrt(0.4);
   const double nu = (tau - 0.5) * cs2;
-  const double h = (gd.r_outer - gd.r_inner) / gd.nr;
+  const double h = lattice_h(gd);
   const double a = -G / (2.0 * nu * h * h);
   const double ri = gd.r_inner, ro = gd.r_outer;
   // B r + C / r = -a r ln r at r_i and r_o

@@ -27,6 +27,12 @@ std::string validate_geometry(lb_metric metric, const lb_geometry_desc& g);
 // nr * n3 rows of LB_GEO_STRIDE doubles (row = i_r * n3 + i_3).
 std::vector<double> evaluate_geometry(lb_metric metric, const lb_geometry_desc& g);
 
+// Lattice spacing h: d / nr (bounce-back walls) or d / (nr - 1) (wall nodes).
+double lattice_h(const lb_geometry_desc& g);
+// Physical radius of node i_r and the x3 coordinate of node i_3 (z or phi).
+double node_r(const lb_geometry_desc& g, int ir);
+double node_x3(const lb_geometry_desc& g, int i3);
+
 // Streamwise curvature radius of the inner wall (r_i, r_i b^2; 0 for FLAT).
 double curvature_radius(lb_metric metric, const lb_geometry_desc& g);
 

@@ -11,6 +11,8 @@ namespace lbgm {
 // populations are in f: moments, equilibrium, non-equilibrium stress,
 // forcing, BGK, store into the instance block fout. flag is set to 1 when
 // the node's density is not finite.
+// Nodes on an equilibrium wall (the end nodes of the walled axes) leave the
+// step as f^eq(rho', 0) of their own density and metric (Sec. III).
 template <typename S, typename Real, int K>
 __device__ __forceinline__ void collide_store(Real (&f)[Q], S* __restrict__ fout, const float* ref,
                                               const GeoDev<Real>& geo, const InstParams<Real>& ip, const Dims& d,
@@ -21,6 +23,11 @@ __device__ __forceinline__ void collide_store(Real (&f)[Q], S* __restrict__ fout
   }
   const int row = K == KELL ? p.ir * d.geo_rows3 + p.i3 : p.ir;
   const NodeGeo<Real, K> g = load_geo<Real, K>(geo, row);
+  if (d.wall_eq && (p.ir == 0 || p.ir == d.nr - 1 || (!d.periodic3 && (p.i3 == 0 || p.i3 == d.n3 - 1)))) {
+    equilibrium<Real, K>(m.rho, Real(0.0), Real(0.0), Real(0.0), g, f);
+    store_node<K>(fout, ref, p, d, f);
+    return;
+  }
   const Coef<Real> k = coefficients<Real, K>(m, g, ip.kappa, ip.G);
   collide<Real, K>(f, k, g, ip.omega);
   store_node<K>(fout, ref, p, d, f);

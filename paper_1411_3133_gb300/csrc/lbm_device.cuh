@@ -51,6 +51,7 @@ struct Dims {
   // 2-byte storage: reference populations over the nr * geo_rows3 geometry
   // rows, per instance (ref_index; NULL for FP32 / FP64 storage)
   const float* ref;
+  int wall_eq;     // 1: equilibrium (Dirichlet) walls on the end nodes
 };
 
 // Index of reference population l of geometry row r in an instance's table:
@@ -318,9 +319,37 @@ __device__ __forceinline__ void for_each_source_far(const S* __restrict__ fin, c
   });
 }
 
+// Equilibrium walls: the source x - c with walled axes clamped onto the
+// wall layer (periodic axes wrapped); no flip.
+template <int K, class S, class Fn>
+__device__ __forceinline__ void for_each_source_clamped(const S* __restrict__ fin, const CellPos& p,
+                                                        const Dims& d, Fn&& fn) {
+  const uint32_t N = uint32_t(d.ncell);
+  auto src = [&](int cx, int cy, int cz, int& yr, int& yz) {
+    yr = min(max(p.ir - cx, 0), d.nr - 1);
+    const int yt = wrap_small(p.it - cy, d.nt);
+    yz = p.i3 - cz;
+    yz = d.periodic3 ? wrap_small(yz, d.n3) : min(max(yz, 0), d.n3 - 1);
+    return uint32_t((yr * d.nt + yt) * d.n3 + yz);
+  };
+  static_for<0, NPAIR>([&](auto P_) {
+    constexpr int P = decltype(P_)::value;
+    using C = Pair<P>;
+    int rp, zp, rm, zm;
+    const uint32_t sp = src(C::x, C::y, C::z, rp, zp);
+    const uint32_t sm = src(-C::x, -C::y, -C::z, rm, zm);
+    fn(std::integral_constant<int, 2 * P + 1>{}, fin + ((2 * P + 1) * N + sp), 2 * P + 1, geo_row<K>(d, rp, zp));
+    fn(std::integral_constant<int, 2 * P + 2>{}, fin + ((2 * P + 2) * N + sm), 2 * P + 2, geo_row<K>(d, rm, zm));
+  });
+}
+
 template <int K, class S, class Fn>
 __device__ __forceinline__ void for_each_source_wall(const S* __restrict__ fin, const CellPos& p, const Dims& d,
                                                      Fn&& fn) {
+  if (d.wall_eq) {
+    for_each_source_clamped<K>(fin, p, d, fn);
+    return;
+  }
   const uint32_t N = uint32_t(d.ncell);
   static_for<0, NPAIR>([&](auto P_) {
     constexpr int P = decltype(P_)::value;

@@ -48,9 +48,10 @@ __global__ void k_noalloc_weights(int metric, lb_geometry_desc g, double* w) {
   const int row = blockIdx.x * blockDim.x + threadIdx.x;
   if (row >= g.nr * g.n3) return;
   const int ir = row / g.n3, i3 = row - ir * g.n3;
-  const double h = (g.r_outer - g.r_inner) / g.nr;
-  const double r = g.r_inner + (ir + 0.5) * h;
-  const double x3 = (i3 + 0.5 - 0.5 * g.n3) * h * g.d3_scale;
+  const bool eqw = g.wall == LB_WALL_EQUILIBRIUM;  // node positions as evaluate_geometry
+  const double h = (g.r_outer - g.r_inner) / (eqw ? g.nr - 1 : g.nr);
+  const double r = g.r_inner + (eqw ? ir : ir + 0.5) * h;
+  const double x3 = (eqw && !g.periodic3 ? i3 - 0.5 * (g.n3 - 1) : i3 + 0.5 - 0.5 * g.n3) * h * g.d3_scale;
   double g1 = 1.0, g2 = 1.0, wA = 1.0, wOm = 1.0;
   if (metric == LB_METRIC_CYLINDRICAL) {
     g1 = r * r;
@@ -93,6 +94,7 @@ extern "C" lb_status lb_diagnostics_noalloc(lb_metric metric, const lb_geometry_
   d.n3 = geom->n3;
   d.ncell = geom->nr * geom->ntheta * geom->n3;
   d.periodic3 = geom->periodic3 ? 1 : 0;
+  d.wall_eq = geom->wall == LB_WALL_EQUILIBRIUM ? 1 : 0;
   d.batch = batch;
   const size_t N = size_t(d.ncell);
   const int nblk = int(std::min<size_t>(1024, (N + 255) / 256));
@@ -147,7 +149,7 @@ extern "C" lb_status lb_diagnostics_noalloc(lb_metric metric, const lb_geometry_
     o.mass_physical = q[1];
     o.mean_v_theta = q[2] / q[3];
     const double nu = (tau[b] - 0.5) * cs2;
-    o.dean = R > 0.0 ? o.mean_v_theta * geom->nr / nu * std::sqrt(dd / R) : 0.0;
+    o.dean = R > 0.0 ? o.mean_v_theta * (dd / lattice_h(*geom)) / nu * std::sqrt(dd / R) : 0.0;
     o.mean_vorticity = q[4] / q[3];
     o.vortex_amp = std::sqrt(q[5] / double(N));
     o.vortex_amp_x3 = std::sqrt(q[6] / double(N));

@@ -33,7 +33,8 @@ class lb_geometry_desc(ctypes.Structure):
     _fields_ = [("r_inner", ctypes.c_double), ("r_outer", ctypes.c_double),
                 ("b", ctypes.c_double), ("nr", ctypes.c_int), ("ntheta", ctypes.c_int),
                 ("n3", ctypes.c_int), ("periodic3", ctypes.c_int),
-                ("dtheta_scale", ctypes.c_double), ("d3_scale", ctypes.c_double)]
+                ("dtheta_scale", ctypes.c_double), ("d3_scale", ctypes.c_double),
+                ("wall", ctypes.c_int)]
 
 
 class lb_params(ctypes.Structure):
@@ -178,10 +179,14 @@ def lb_velocity_set():
     return c.reshape(LB_Q, 3).astype(np.int64), w
 
 
+WALLS = {"bounceback": 0, "equilibrium": 1}
+
+
 def make_desc(r_inner, r_outer, nr, ntheta, n3, b=1.0, periodic3=True, dtheta_scale=1.0,
-              d3_scale=1.0) -> lb_geometry_desc:
+              d3_scale=1.0, wall="bounceback") -> lb_geometry_desc:
     return lb_geometry_desc(float(r_inner), float(r_outer), float(b), int(nr), int(ntheta),
-                            int(n3), int(bool(periodic3)), float(dtheta_scale), float(d3_scale))
+                            int(n3), int(bool(periodic3)), float(dtheta_scale), float(d3_scale),
+                            WALLS[wall])
 
 
 def lb_geometry_eval(metric: str, desc: lb_geometry_desc) -> np.ndarray:
@@ -259,10 +264,11 @@ class ChannelSpec:
     periodic3: bool = True
     dtheta_scale: float = 1.0
     d3_scale: float = 1.0
+    wall: str = "bounceback"
 
     def desc(self) -> lb_geometry_desc:
         return make_desc(self.r_inner, self.r_outer, self.nr, self.ntheta, self.n3, self.b,
-                         self.periodic3, self.dtheta_scale, self.d3_scale)
+                         self.periodic3, self.dtheta_scale, self.d3_scale, self.wall)
 
     @property
     def ncells(self):

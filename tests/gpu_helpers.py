@@ -23,7 +23,7 @@ def perm_lib_to_oracle():
 
 def spec_of(ch: Channel):
     return lib().ChannelSpec(ch.metric, ch.r_inner, ch.r_outer, ch.nr, ch.ntheta, ch.n3, ch.b,
-                             ch.periodic3, ch.dtheta_scale, ch.d3_scale)
+                             ch.periodic3, ch.dtheta_scale, ch.d3_scale, ch.wall)
 
 
 class Twin:

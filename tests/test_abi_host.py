@@ -58,13 +58,16 @@ CHANNELS = [
     Channel("ellipsoidal", 1.0, 1.1, 8, 4, 12, b=0.9, periodic3=False),
     Channel("ellipsoidal", 0.25, 0.275, 16, 4, 32, b=2.0, periodic3=False,
             dtheta_scale=2.0, d3_scale=4.0),
+    Channel("cylindrical", 1.0, 1 / 0.975, 17, 4, 32, wall="equilibrium"),
+    Channel("ellipsoidal", 1.0, 1.1, 9, 4, 13, b=0.9, periodic3=False, wall="equilibrium"),
+    Channel("ellipsoidal", 1.0, 1.1, 9, 4, 13, b=0.9, wall="equilibrium"),
 ]
 
 
-@pytest.mark.parametrize("ch", CHANNELS, ids=lambda c: f"{c.metric}{c.shape}")
+@pytest.mark.parametrize("ch", CHANNELS, ids=lambda c: f"{c.metric}{c.shape}{c.wall[:2]}{int(c.periodic3)}")
 def test_geometry_matches_oracle(L, ch):
     desc = L.make_desc(ch.r_inner, ch.r_outer, ch.nr, ch.ntheta, ch.n3, ch.b, ch.periodic3,
-                       ch.dtheta_scale, ch.d3_scale)
+                       ch.dtheta_scale, ch.d3_scale, ch.wall)
     rows = L.lb_geometry_eval(ch.metric, desc)
     geo = channel_geometry(ch)
     assert np.allclose(rows[..., 0:9].reshape(geo["Delta"].shape), geo["Delta"], rtol=0, atol=1e-13)
@@ -85,9 +88,27 @@ def test_force_for_dean_matches_closed_form(L, nr, tau, De):
     assert v.mean() * nr / nu * math.sqrt((ro - ri) / ri) == pytest.approx(De, rel=1e-12)
 
 
+def test_force_for_dean_with_wall_nodes(L):
+    """Wall nodes: d = (N_r - 1) h, nodes r_i + i h, the laminar profile
+    vanishing on the end nodes; De = <v> (N_r - 1) / nu sqrt(d / r_i)."""
+    from analytic import curved_poiseuille_coeffs
+    ri, ro, nr, tau, De = 1.0, 1 / 0.975, 33, 0.6, 40.0
+    desc = L.make_desc(ri, ro, nr, 4, 32, wall="equilibrium")
+    G = L.lb_force_for_dean("cylindrical", desc, tau, De)
+    h = (ro - ri) / (nr - 1)
+    r = ri + np.arange(nr) * h
+    A, B, C = curved_poiseuille_coeffs(ri, ro, h, G, tau)
+    v = A * r * np.log(r) + B * r + C / r
+    assert abs(v[0]) < 1e-12 * abs(v).max() and abs(v[-1]) < 1e-12 * abs(v).max()
+    nu = (tau - 0.5) * CS2
+    assert v.mean() * (nr - 1) / nu * math.sqrt((ro - ri) / ri) == pytest.approx(De, rel=1e-12)
+
+
 @pytest.mark.parametrize("kw,msg", [
     (dict(r_inner=1.0, r_outer=0.9), "r_outer"),
     (dict(nr=6), "nr >= 7"),
+    (dict(nr=2, wall="equilibrium"), "nr >= 3"),
+    (dict(periodic3=False, n3=2, wall="equilibrium"), "n3 >= 3"),
     (dict(ntheta=0), "ntheta"),
     (dict(periodic3=False, n3=5), "n3 >= 7"),
     (dict(dtheta_scale=0.0), "dtheta_scale"),

@@ -31,6 +31,8 @@ MEMBERS = [
       dict(tau=1.1, G=0.0, seed=3, amp=5e-3, old=True)]),
     (Channel("ellipsoidal", 1.0, 1.1, 8, 3, 35, b=1.2), [dict(tau=0.8, G=2e-4, seed=13, amp=1e-2)]),
     (Channel("cylindrical", 1.0, 1 / ETA, 16, 4, 200), [dict(tau=0.55, G=3e-5, seed=14, amp=1e-3)]),
+    (Channel("ellipsoidal", 1.0, 1.1, 9, 3, 11, b=0.9, periodic3=False, wall="equilibrium"),
+     [dict(tau=0.7, G=3e-4, seed=15, amp=1e-2)]),
 ]
 
 
@@ -91,7 +93,7 @@ def test_batch_members_interleaved_with_single_steps():
     batch.lb_batch_step(2)
     for i, c in enumerate(alone):
         c.lb_step(2 if i == 0 else 9 + (i == 2))
-    for i in (1, 2, 3, 4, 5):
+    for i in range(1, len(MEMBERS)):
         assert np.array_equal(_state(batched[i]), _state(alone[i])), i
     assert np.array_equal(_state(batched[0]), _state(alone[0]))
     batch.close()
@@ -102,7 +104,7 @@ def test_batch_members_against_oracle():
     import torch
     L = lib()
     stream = torch.cuda.Stream()
-    twins = [Twin(ch, params, "fp64", stream=stream) for ch, params in MEMBERS[:5]]
+    twins = [Twin(ch, params, "fp64", stream=stream) for ch, params in MEMBERS[:5] + MEMBERS[6:]]
     for tw in twins:
         tw.ctx.lb_init(tw.lparams)
         for b, s in enumerate(tw.sims):

@@ -81,6 +81,16 @@ CASES = {
                      [dict(tau=0.55, G=5e-4, seed=12, amp=1e-2)]),
     "ell_periodic_phi": (Channel("ellipsoidal", 1.0, 1.1, 8, 3, 35, b=1.2),
                          [dict(tau=0.8, G=2e-4, seed=13, amp=1e-2)]),
+    "cyl_eqwall": (Channel("cylindrical", 1.0, 1 / ETA, 17, 4, 32, wall="equilibrium"),
+                   [dict(tau=0.8, G=2e-4, seed=21, amp=1e-2)]),
+    "flat_eqwall_4": (Channel("flat", 0.0, 1.0, 9, 2, 9, periodic3=False, wall="equilibrium"),
+                      [dict(tau=0.6, G=1e-3, seed=22, amp=1e-2)]),
+    "ell_eqwall_4": (Channel("ellipsoidal", 1.0, 1.1, 10, 4, 14, b=0.9, periodic3=False,
+                             wall="equilibrium"), [dict(tau=0.7, G=3e-4, seed=23, amp=1e-2)]),
+    "ell_eqwall_periodic": (Channel("ellipsoidal", 1.0, 1.1, 8, 3, 35, b=1.2, wall="equilibrium"),
+                            [dict(tau=0.8, G=2e-4, seed=24, amp=1e-2)]),
+    "cyl_eqwall_nr3": (Channel("cylindrical", 1.0, 1.02, 3, 2, 8, wall="equilibrium"),
+                       [dict(tau=0.9, G=1e-4, seed=25, amp=1e-2)]),
     "batch3": (Channel("cylindrical", 1.0, 1 / ETA, 8, 4, 33),
                [dict(tau=0.8, G=1e-4, seed=1, amp=1e-3), dict(tau=0.6, G=3e-4, seed=2, amp=2e-3),
                 dict(tau=1.1, G=0.0, seed=3, amp=5e-3, old=True)]),
@@ -135,7 +145,9 @@ def _smooth_flow(ch, amp=0.05):
 
 
 @pytest.mark.parametrize("ch", [CYL1, Channel("ellipsoidal", 1.0, 1.1, 10, 4, 40, b=0.9,
-                                              periodic3=False)], ids=["cyl", "ell"])
+                                              periodic3=False),
+                                Channel("ellipsoidal", 1.0, 1.1, 10, 4, 40, b=0.9, periodic3=False,
+                                        wall="equilibrium")], ids=["cyl", "ell", "ell_eqwall"])
 def test_fp32_step_parity(ch):
     """FP32 against the FP64 oracle, 1e-5 of u_max for a flow of realistic
     magnitude (u_max ~ 0.05), after 1, 10 and 100 steps."""
@@ -167,8 +179,9 @@ def test_init_fields_matches_oracle():
     tw.close()
 
 
-def test_diagnostics_match_oracle():
-    ch = Channel("ellipsoidal", 1.0, 1.1, 10, 3, 16, b=0.9, periodic3=False)
+@pytest.mark.parametrize("wall", ["bounceback", "equilibrium"])
+def test_diagnostics_match_oracle(wall):
+    ch = Channel("ellipsoidal", 1.0, 1.1, 10, 3, 16, b=0.9, periodic3=False, wall=wall)
     params = [dict(tau=0.7, G=3e-4, seed=4, amp=1e-2), dict(tau=0.6, G=1e-4, seed=5, amp=1e-2)]
     tw = Twin(ch, params, "fp64")
     tw.ctx.lb_init(tw.lparams)
@@ -183,6 +196,28 @@ def test_diagnostics_match_oracle():
                   "vortex_amp", "vortex_amp_x3", "max_speed"):
             assert dl[b][k] == pytest.approx(do[k], rel=1e-11, abs=1e-18), k
         assert dl[b]["nonfinite"] == 0 and dl[b]["step"] == 20
+    tw.close()
+
+
+def test_equilibrium_wall_base_flow_vanishes_on_wall_nodes():
+    """lb_init's laminar profile with wall nodes: zero velocity on the end
+    nodes, the closed form in between, and it stays near it (first-order
+    wall condition) over 200 steps."""
+    from analytic import curved_poiseuille_coeffs
+    ch = Channel("cylindrical", 1.0, 1 / ETA, 17, 2, 8, wall="equilibrium")
+    tau, G = 0.8, 2e-4
+    tw = Twin(ch, [dict(tau=tau, G=G, base=True)], "fp64")
+    tw.ctx.lb_init(tw.lparams)
+    r = 1.0 + np.arange(ch.nr) * ch.h
+    A, B, C = curved_poiseuille_coeffs(1.0, 1 / ETA, ch.h, G, tau)
+    uth = (A * r * np.log(r) + B * r + C / r) / r
+    rho, u = tw.lib_macros()
+    ut = u[0, :, 1].reshape(ch.nr, -1)
+    assert abs(uth[0]) < 1e-12 * abs(uth).max() and abs(uth[-1]) < 1e-12 * abs(uth).max()
+    tw.ctx.lb_step(200)
+    rho, u = tw.lib_macros()
+    ut = u[0, :, 1].reshape(ch.nr, -1).mean(axis=1)
+    assert np.abs(ut[1:-1] - uth[1:-1]).max() < 0.15 * np.abs(uth).max()
     tw.close()
 
 

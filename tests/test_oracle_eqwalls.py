@@ -1,5 +1,6 @@
 """Pins of the oracle's equilibrium (Dirichlet) walls, the paper's own wall
-condition (Sec. III: f^eq evaluated with u = 0 at r_i and r_o every step),
+condition (Sec. III: zero wall velocity imposed through the equilibrium on
+both walls at every step),
 against what the mathematics fixes:
 
 * the flat rest state is a fixed point with walls on two axes;
@@ -111,3 +112,48 @@ def test_curved_poiseuille_first_order():
         errs.append(np.abs(u[:, 1] - uth).max() / uth.max())
     assert errs[0] < 0.1
     assert errs[0] / errs[1] > 1.7 and errs[1] / errs[2] > 1.7, errs
+
+
+def test_observables_use_the_wall_value_and_one_sided_differences():
+    """u^3 = i (N_r - 1 - i) vanishes on both wall nodes; its r-derivative
+    N_r - 1 - 2 i is exact for the second-order differences everywhere, so
+    the mean |vorticity| of the flat channel is the node mean of |N_r - 1 -
+    2 i|. Garbage velocities on the wall nodes must not change anything."""
+    from oracle.diagnostics import diagnostics
+    ch = Channel("flat", 0.0, 1.0, 9, 2, 8, periodic3=False, wall="equilibrium")
+    geo = channel_geometry(ch)
+    nr, nt, n3 = ch.shape
+    i = np.arange(nr)[:, None, None] * np.ones((1, nt, n3))
+    u = np.zeros(ch.shape + (3,))
+    u[..., 2] = i * (nr - 1 - i)
+    u[:, :, 0, 2] = 0.0
+    u[:, :, -1, 2] = 0.0                      # x3 wall nodes hold the wall value too
+    rho = np.ones(ch.ncells)
+    d = diagnostics(ch, geo, 0.8, rho, u.reshape(-1, 3))
+    expect = np.abs(nr - 1 - 2 * i)            # d_r u^3; d_3 u^r = 0 everywhere
+    expect[:, :, 0] = 0.0                       # u^3 = 0 on the x3 wall columns
+    expect[:, :, -1] = 0.0
+    assert d["mean_vorticity"] == pytest.approx(expect.mean(), rel=1e-14)
+    noisy = u.copy()
+    noisy[0] = 7.0
+    noisy[-1] = -3.0
+    noisy[:, :, 0] = 5.0
+    noisy[:, :, -1] = 2.0
+    d2 = diagnostics(ch, geo, 0.8, rho, noisy.reshape(-1, 3))
+    for k in ("mean_vorticity", "mean_v_theta", "vortex_amp", "vortex_amp_x3", "max_speed"):
+        assert d2[k] == pytest.approx(d[k], rel=1e-14, abs=1e-300), k
+
+
+def test_dean_number_uses_the_wall_node_width():
+    from oracle.diagnostics import diagnostics
+    ch = Channel("cylindrical", 1.0, 1.1, 11, 1, 4, wall="equilibrium")
+    geo = channel_geometry(ch)
+    u = np.zeros((ch.ncells, 3))
+    u[:, 1] = 0.01
+    d = diagnostics(ch, geo, 0.8, np.ones(ch.ncells), u)
+    # <v_theta> = mean of r u^theta over the 9 fluid nodes and 2 wall nodes (value 0)
+    r = 1.0 + 0.01 * np.arange(11)
+    vmean = (r * 0.01)[1:-1].sum() / 11
+    assert d["mean_v_theta"] == pytest.approx(vmean, rel=1e-13)
+    nu_l = (0.8 - 0.5) * OL.CS2
+    assert d["dean"] == pytest.approx(vmean * 10 / nu_l * math.sqrt(0.1 / 1.0), rel=1e-13)
