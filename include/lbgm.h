@@ -201,7 +201,7 @@ typedef enum {
                                requires lb_init again (LB_ERR_STATE until
                                then); state bytes (lb_get_state) are
                                deviations from the reference of the last
-                               initialisation. */
+                               initialisation or lb_capture_reference. */
 } lb_option;
 
 /* One configuration measured by lb_autotune / lb_batch_autotune. */
@@ -286,6 +286,17 @@ lb_status lb_diagnostics(lb_ctx* ctx, lb_diag* out);
  * precision formats a state read out and written back is unchanged (the
  * stored deviations round-trip). */
 lb_status lb_get_populations(lb_ctx* ctx, double* f, int on_device);
+
+/* FP16/BF16 storage only: make the current state the reference of the stored
+ * deviations. The reference population of every geometry row becomes the
+ * mean of that population over the row's nodes (all theta and x3 of a layer
+ * for the cylinder and flat channel; all theta of an (r, x3) row for the
+ * ellipsoid), and the state is re-encoded against it. Called once a laminar
+ * state has developed, its non-equilibrium part moves into the FP32 table
+ * and only departures from it -- the perturbations of an instability -- are
+ * rounded to 2 bytes. The populations do not change beyond one rounding of
+ * the new encoding. Synchronises the stream; LB_ERR_ARG for other precisions. */
+lb_status lb_capture_reference(lb_ctx* ctx);
 lb_status lb_set_populations(lb_ctx* ctx, const double* f, int on_device);
 
 /* Raw state for checkpointing (private layout, native precision) plus the

@@ -688,6 +688,21 @@ lb_status lb_get_populations(lb_ctx* c, double* f, int on_device) {
   return LB_OK;
 }
 
+lb_status lb_capture_reference(lb_ctx* c) {
+  lb_status s;
+  if (!usable(c, &s)) return s;
+  if (!c->ref_tab) return fail(c, LB_ERR_ARG, "only the 2-byte storage formats have a reference");
+  const size_t n = c->state_elems;
+  if (!c->dbl_stage) c->dbl_stage = static_cast<double*>(dalloc(c, n * sizeof(double)));
+  if (!c->dbl_stage) return fail(c, LB_ERR_CUDA, "staging allocation failed");
+  // decode with the old table, average, re-encode with the new one
+  LB_CUDA(c, launch_convert(int(c->prec), 1, c->f[c->cur], c->dbl_stage, n, c->dims, c->stream));
+  LB_CUDA(c, launch_ref_from_state(c->dbl_stage, c->ref_tab, c->dims, c->stream));
+  LB_CUDA(c, launch_convert(int(c->prec), 0, c->f[c->cur], c->dbl_stage, n, c->dims, c->stream));
+  LB_CUDA(c, cudaStreamSynchronize(c->stream));
+  return LB_OK;
+}
+
 lb_status lb_set_populations(lb_ctx* c, const double* f, int on_device) {
   if (!c || !f) return fail(c, LB_ERR_ARG, "null argument");
   if (c->tau.empty()) return fail(c, LB_ERR_STATE, "call lb_init once first (parameters)");

@@ -277,6 +277,31 @@ cudaError_t launch_convert(int prec, int to_double, void* state, double* dbl, si
   return cudaGetLastError();
 }
 
+// Row means of FP64 populations into the reference table (ref_index
+// layout): one thread per (instance, row, population).
+__global__ void k_ref_from_state(const double* __restrict__ dbl, float* __restrict__ ref, Dims d) {
+  const size_t nrows = size_t(d.nr) * size_t(d.geo_rows3);
+  const size_t t = blockIdx.x * size_t(blockDim.x) + threadIdx.x;
+  if (t >= size_t(d.batch) * nrows * Q) return;
+  const size_t l = t % Q, br = t / Q, b = br / nrows, row = br - b * nrows;
+  const int ir = int(row / size_t(d.geo_rows3)), i3 = int(row - size_t(ir) * d.geo_rows3);
+  const bool ell = d.geo_rows3 > 1;
+  const int n3s = ell ? 1 : d.n3;
+  const double* f = dbl + (b * Q + l) * size_t(d.ncell);
+  double s = 0.0;
+  for (int it = 0; it < d.nt; ++it)
+    for (int k3 = 0; k3 < n3s; ++k3) s += f[(size_t(ir) * d.nt + it) * d.n3 + (ell ? i3 : k3)];
+  const double mean = s / double(d.nt * n3s);
+  float* rb = ref + b * Q * nrows;
+  rb[ell ? l * nrows + row : row * Q + l] = float(mean);
+}
+
+cudaError_t launch_ref_from_state(const double* dbl, float* ref, const Dims& d, cudaStream_t s) {
+  const size_t n = size_t(d.batch) * size_t(d.nr) * size_t(d.geo_rows3) * Q;
+  k_ref_from_state<<<unsigned((n + 255) / 256), 256, 0, s>>>(dbl, ref, d);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_ref_table(int K, float* ref, const GeoDev<float>& geo, const double* sqrtg,
                              const double* base_uth, const double* rho_in, const double* u_in, const Dims& d,
                              int mode, cudaStream_t s) {

@@ -88,6 +88,7 @@ SIGNATURES = {
     "lb_macros": (ctypes.c_int, [_P, _P, _P, ctypes.c_int]),
     "lb_diagnostics": (ctypes.c_int, [_P, ctypes.POINTER(lb_diag)]),
     "lb_get_populations": (ctypes.c_int, [_P, _P, ctypes.c_int]),
+    "lb_capture_reference": (ctypes.c_int, [_P]),
     "lb_set_populations": (ctypes.c_int, [_P, _P, ctypes.c_int]),
     "lb_state_bytes": (ctypes.c_size_t, [_P]),
     "lb_get_state": (ctypes.c_int, [_P, _P, ctypes.c_size_t, ctypes.c_int]),
@@ -357,6 +358,9 @@ class LBContext:
             return out.reshape(self.batch, LB_Q, N)
         _check(load_library().lb_get_populations(self.ctx, _ptr(out), int(on_device)), self.ctx)
         return out
+
+    def lb_capture_reference(self):
+        _check(load_library().lb_capture_reference(self.ctx), self.ctx)
 
     def lb_set_populations(self, f, on_device=False):
         if isinstance(f, np.ndarray):

@@ -83,8 +83,11 @@ def critical_dean(deans, sigmas):
 
 def run_sweep(spec: L.ChannelSpec, taus, deans, steps: int, sample_every: int = 1000,
               precision: str = "fp32", seed: int = 20241111, noise_amp: float = 1e-4,
-              use_graph: bool = True) -> SweepResult:
-    """One batched run: instance b has tau = taus[b] and target De = deans[b]."""
+              use_graph: bool = True, capture_at: int = 20_000) -> SweepResult:
+    """One batched run: instance b has tau = taus[b] and target De = deans[b].
+    With 2-byte storage the developed laminar state becomes the storage
+    reference at step `capture_at` (lb_capture_reference), before the
+    vortices have grown out of the noise floor."""
     import time
 
     import torch
@@ -102,9 +105,15 @@ def run_sweep(spec: L.ChannelSpec, taus, deans, steps: int, sample_every: int = 
     ts, amps, des, vort = [], [], [], []
     t0 = time.perf_counter()
     done = 0
+    two_byte = precision in ("fp16_shifted", "bf16_shifted")
     while done < steps:
         n = min(sample_every, steps - done)
-        ctx.lb_step(n)
+        if two_byte and done < capture_at <= done + n:
+            ctx.lb_step(capture_at - done)
+            ctx.lb_capture_reference()
+            ctx.lb_step(done + n - capture_at)
+        else:
+            ctx.lb_step(n)
         done += n
         d = ctx.lb_diagnostics()
         ts.append(done)

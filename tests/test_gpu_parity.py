@@ -517,6 +517,48 @@ def test_storage_reference_option():
     tw.close()
 
 
+@pytest.mark.parametrize("prec,tol", [("fp16_shifted", 1e-4), ("bf16_shifted", 1e-3)])
+def test_capture_reference_keeps_the_state_and_the_parity(prec, tol):
+    """lb_capture_reference moves the developed state's row means into the
+    reference: the populations change by at most one rounding of the new
+    encoding, the stored deviations shrink, and the run stays on the FP64
+    oracle."""
+    import torch
+    L = lib()
+    ch = Channel("cylindrical", 1.0, 1 / ETA, 16, 4, 64)
+    tw = Twin(ch, [dict(tau=0.8, G=G_LAMINAR)], prec)
+    rho = np.stack([1.0 / tw.sims[0].sqrtg])
+    u = (_smooth_flow(ch) + noise_field(33, tw.N, 1e-3))[None]
+    tw.init_fields(rho, u)
+    tw.step(40)
+    before = tw.ctx.lb_get_populations()
+    raw0 = torch.empty(tw.ctx.lb_state_bytes(), dtype=torch.uint8)
+    tw.ctx.lb_get_state(raw0)
+    tw.ctx.lb_capture_reference()
+    after = tw.ctx.lb_get_populations()
+    w = L.lb_velocity_set()[1]
+    ulp = 2.0 ** (-11 if prec == "fp16_shifted" else -8)
+    # one rounding of the new deviation, whose size is below the old one's
+    old_dev = np.abs(before / w[None, :, None] - 1.0).max()
+    assert (np.abs(after - before) / w[None, :, None]).max() <= ulp * old_dev
+    raw1 = torch.empty_like(raw0)
+    tw.ctx.lb_get_state(raw1)
+    dt = torch.float16 if prec == "fp16_shifted" else torch.bfloat16
+    assert raw1.view(dt).float().abs().max() < 0.5 * raw0.view(dt).float().abs().max()
+    f_lib = tw.lib_f()[0]
+    for s in tw.sims:
+        s.f = f_lib.copy()                      # continue the oracle from the captured state
+    tw.step(60)
+    _compare_macros(tw, tol, tol)
+    tw.close()
+    tw2 = Twin(CYL1, [dict(tau=0.8)], "fp32")   # FP32 has no reference
+    tw2.ctx.lb_init(tw2.lparams)
+    with pytest.raises(L.LBError) as e:
+        tw2.ctx.lb_capture_reference()
+    assert e.value.status == L.LB_ERR_ARG
+    tw2.close()
+
+
 @pytest.mark.parametrize("prec", ["fp16_shifted", "bf16_shifted"])
 def test_reduced_precision_state_round_trips(prec):
     L = lib()
