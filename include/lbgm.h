@@ -407,6 +407,43 @@ void lb_batch_destroy(lb_batch* batch);
 /* Message of the last failure on the batch (NULL: as lb_last_error(NULL)). */
 const char* lb_batch_last_error(const lb_batch* batch);
 
+/* --------------------------------------------------------------------- */
+/* Surrogate of developed channel flow, for warm starts (no counterpart in
+ * the paper). A multilayer perceptron maps x = (De, r, z) -- a Dean number
+ * and a node's position, each scaled by the caller (typically De / 100,
+ * (r - r_i)/d and x3 / L_3 in [0, 1)) -- to the node's fields y = (rho',
+ * u^r, u^theta, u^3) of a converged LB run. Features (De, r, sin(2 pi k z),
+ * cos(2 pi k z), k = 1..n_fourier) feed depth - 1 hidden layers of `width`
+ * SiLU units and a linear layer of 4 outputs, which predicts (y - mean)/std
+ * per field (lb_mlp_set_output_scale). Weights: FP32 master copy and Adam
+ * moments, BF16 in every product, FP32 accumulation; He-uniform initial
+ * weights from a SplitMix64 stream seeded with `seed`, zero biases.
+ * Parameters are laid out layer by layer as W (fan_out x fan_in, row-major)
+ * then b. All x, y arrays are device FP32, row-major ([n][3], [n][4]);
+ * calls are ordered on `cuda_stream` (NULL: legacy default stream). */
+typedef struct lb_mlp lb_mlp;
+lb_status lb_mlp_create(int n_fourier, int width, int depth, int max_batch, unsigned long long seed,
+                        void* cuda_stream, lb_mlp** out);
+size_t lb_mlp_param_count(const lb_mlp* net);
+/* host arrays mean[4], std[4] (std > 0) */
+lb_status lb_mlp_set_output_scale(lb_mlp* net, const float* mean, const float* std);
+/* One Adam step (beta 0.9 / 0.999, eps 1e-8, learning rate lr) on the mean
+ * squared error of the normalised outputs over n <= max_batch samples;
+ * *loss (host, may be NULL: then no synchronisation) receives that error
+ * before the step. */
+lb_status lb_mlp_train_step(lb_mlp* net, const float* x, const float* y, int n, float lr, float* loss);
+/* y = the network's fields at n <= max_batch inputs (asynchronous). */
+lb_status lb_mlp_predict(lb_mlp* net, const float* x, int n, float* y);
+/* FP32 master parameters / gradients of the last train step, host arrays of
+ * lb_mlp_param_count floats; set_params also resets the Adam state. */
+lb_status lb_mlp_get_params(lb_mlp* net, float* host, size_t count);
+lb_status lb_mlp_set_params(lb_mlp* net, const float* host, size_t count);
+lb_status lb_mlp_get_grads(lb_mlp* net, float* host, size_t count);
+void lb_mlp_destroy(lb_mlp* net);
+/* Message of the last failure (NULL: of the calling thread's last
+ * lb_mlp_create). */
+const char* lb_mlp_last_error(const lb_mlp* net);
+
 #ifdef __cplusplus
 }
 #endif

@@ -73,6 +73,7 @@ class lb_allocator(ctypes.Structure):
 # C signatures: name -> (restype, argtypes)
 _P = ctypes.c_void_p
 _D = ctypes.POINTER(ctypes.c_double)
+_F = ctypes.POINTER(ctypes.c_float)
 SIGNATURES = {
     "lb_velocity_set": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int), _D]),
     "lb_geometry_eval": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(lb_geometry_desc), _D,
@@ -112,6 +113,17 @@ SIGNATURES = {
     "lb_batch_step_count": (ctypes.c_longlong, [_P]),
     "lb_batch_destroy": (None, [_P]),
     "lb_batch_last_error": (ctypes.c_char_p, [_P]),
+    "lb_mlp_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                     ctypes.c_ulonglong, _P, ctypes.POINTER(_P)]),
+    "lb_mlp_param_count": (ctypes.c_size_t, [_P]),
+    "lb_mlp_set_output_scale": (ctypes.c_int, [_P, _F, _F]),
+    "lb_mlp_train_step": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.c_float, _F]),
+    "lb_mlp_predict": (ctypes.c_int, [_P, _P, ctypes.c_int, _P]),
+    "lb_mlp_get_params": (ctypes.c_int, [_P, _F, ctypes.c_size_t]),
+    "lb_mlp_set_params": (ctypes.c_int, [_P, _F, ctypes.c_size_t]),
+    "lb_mlp_get_grads": (ctypes.c_int, [_P, _F, ctypes.c_size_t]),
+    "lb_mlp_destroy": (None, [_P]),
+    "lb_mlp_last_error": (ctypes.c_char_p, [_P]),
 }
 
 _lib = None
@@ -436,3 +448,73 @@ class LBBatch:
 
     def lb_batch_step_count(self):
         return int(load_library().lb_batch_step_count(self.handle))
+
+
+def _check_mlp(status, net):
+    if status != LB_OK:
+        raise LBError(status, load_library().lb_mlp_last_error(net).decode())
+
+
+class LBMlp:
+    """One lb_mlp (see include/lbgm.h): inputs x (n, 3) and fields y (n, 4)
+    are torch CUDA float32 tensors."""
+
+    def __init__(self, n_fourier=4, width=256, depth=5, max_batch=16384, seed=20241111, stream=None):
+        import torch
+        lib = load_library()
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = ctypes.c_void_p()
+        _check_mlp(lib.lb_mlp_create(int(n_fourier), int(width), int(depth), int(max_batch), int(seed),
+                                     ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h)), None)
+        self.handle = h
+        self.n_fourier, self.width, self.depth, self.max_batch = n_fourier, width, depth, max_batch
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load_library().lb_mlp_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def param_count(self):
+        return int(load_library().lb_mlp_param_count(self.handle))
+
+    def set_output_scale(self, mean, std):
+        m = np.ascontiguousarray(mean, dtype=np.float32)
+        s = np.ascontiguousarray(std, dtype=np.float32)
+        _check_mlp(load_library().lb_mlp_set_output_scale(self.handle, m.ctypes.data_as(_F),
+                                                          s.ctypes.data_as(_F)), self.handle)
+
+    def train_step(self, x, y, lr, want_loss=True):
+        loss = ctypes.c_float()
+        _check_mlp(load_library().lb_mlp_train_step(self.handle, _ptr(x), _ptr(y), int(x.shape[0]),
+                                                    float(lr), ctypes.byref(loss) if want_loss else None),
+                   self.handle)
+        return loss.value if want_loss else None
+
+    def predict(self, x, out=None):
+        import torch
+        if out is None:
+            out = torch.empty((x.shape[0], 4), dtype=torch.float32, device=x.device)
+        _check_mlp(load_library().lb_mlp_predict(self.handle, _ptr(x), int(x.shape[0]), _ptr(out)),
+                   self.handle)
+        return out
+
+    def _host_call(self, fn, arr=None):
+        n = self.param_count()
+        a = np.zeros(n, dtype=np.float32) if arr is None else np.ascontiguousarray(arr, dtype=np.float32)
+        _check_mlp(fn(self.handle, a.ctypes.data_as(_F), n), self.handle)
+        return a
+
+    def get_params(self):
+        return self._host_call(load_library().lb_mlp_get_params)
+
+    def set_params(self, p):
+        self._host_call(load_library().lb_mlp_set_params, p)
+
+    def get_grads(self):
+        return self._host_call(load_library().lb_mlp_get_grads)

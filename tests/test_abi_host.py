@@ -166,3 +166,14 @@ def test_batch_entry_points_reject_bad_arguments_without_a_gpu(L):
     assert lib.lb_batch_nodes(None) == -1 and lib.lb_batch_step_count(None) == -1
     lib.lb_batch_destroy(None)
     assert lib.lb_autotune(None, 1, None, None, 0, None) == L.LB_ERR_ARG
+
+
+def test_mlp_create_rejects_bad_arguments_without_a_gpu(L):
+    lib = L.load_library()
+    out = ctypes.c_void_p(5)
+    assert lib.lb_mlp_create(2, 2, 5, 16, 1, None, ctypes.byref(out)) == L.LB_ERR_ARG
+    assert out.value is None
+    assert lib.lb_mlp_create(2, 64, 1, 16, 1, None, ctypes.byref(out)) == L.LB_ERR_ARG
+    assert b"width" in lib.lb_mlp_last_error(None)
+    assert lib.lb_mlp_param_count(None) == 0
+    lib.lb_mlp_destroy(None)
