@@ -287,6 +287,15 @@ lb_status lb_diagnostics(lb_ctx* ctx, lb_diag* out);
  * stored deviations round-trip). */
 lb_status lb_get_populations(lb_ctx* ctx, double* f, int on_device);
 
+/* Convergence monitor: per instance b, change[b] = max over nodes and
+ * components of |u - u_prev| and umax[b] (may be NULL) = max |u|, with u
+ * the velocity of lb_macros; then u_prev = u. u_prev is a caller-owned
+ * DEVICE array [batch * 3 * N] in the field layout (start it from
+ * lb_macros(..., on_device = 1)); change, umax are host arrays [batch]. A run
+ * stepped K times between two calls has converged to a per-step residual r
+ * when change[b] <= r * K * umax[b]. Synchronises the stream. */
+lb_status lb_velocity_change(lb_ctx* ctx, double* u_prev, double* change, double* umax);
+
 /* FP16/BF16 storage only: make the current state the reference of the stored
  * deviations. The reference population of every geometry row becomes the
  * mean of that population over the row's nodes (all theta and x3 of a layer

@@ -665,6 +665,24 @@ lb_status lb_diagnostics(lb_ctx* c, lb_diag* out) {
   return LB_OK;
 }
 
+lb_status lb_velocity_change(lb_ctx* c, double* u_prev, double* change, double* umax) {
+  lb_status s;
+  if (!usable(c, &s)) return s;
+  if (!u_prev || !change) return fail(c, LB_ERR_ARG, "null argument");
+  // partial maxima reuse the observables' partial buffer (batch * nblk * DIAG_NQ >= batch * nblk * 2)
+  LB_CUDA(c, launch_macros(int(c->prec), c->K, c->f[c->cur], nullptr, c->u_s, c->dims, c->stream));
+  LB_CUDA(c, launch_residual(c->u_s, u_prev, c->dims, c->partial, c->nblk, c->diag_out, c->stream));
+  std::vector<double> h(2 * size_t(c->batch));
+  LB_CUDA(c, cudaMemcpyAsync(h.data(), c->diag_out, h.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                             c->stream));
+  LB_CUDA(c, cudaStreamSynchronize(c->stream));
+  for (int b = 0; b < c->batch; ++b) {
+    change[b] = h[2 * b];
+    if (umax) umax[b] = h[2 * b + 1];
+  }
+  return LB_OK;
+}
+
 lb_status lb_get_populations(lb_ctx* c, double* f, int on_device) {
   lb_status s;
   if (!usable(c, &s)) return s;

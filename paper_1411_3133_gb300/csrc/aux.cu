@@ -277,6 +277,56 @@ cudaError_t launch_convert(int prec, int to_double, void* state, double* dbl, si
   return cudaGetLastError();
 }
 
+// Per instance (blockIdx.y): max |u - u_prev| and max |u| over the nodes,
+// then u_prev = u. Partial maxima per block, reduced by k_residual_final.
+__global__ void __launch_bounds__(256) k_residual(const double* __restrict__ u, double* __restrict__ u_prev,
+                                                  size_t per_inst, double* __restrict__ partial, int nblk) {
+  __shared__ double sd[256], su[256];
+  const size_t b = blockIdx.y;
+  double md = 0.0, mu = 0.0;
+  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < per_inst; i += size_t(nblk) * blockDim.x) {
+    const size_t k = b * per_inst + i;
+    const double v = u[k];
+    md = fmax(md, fabs(v - u_prev[k]));
+    mu = fmax(mu, fabs(v));
+    u_prev[k] = v;
+  }
+  sd[threadIdx.x] = md;
+  su[threadIdx.x] = mu;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) {
+      sd[threadIdx.x] = fmax(sd[threadIdx.x], sd[threadIdx.x + s]);
+      su[threadIdx.x] = fmax(su[threadIdx.x], su[threadIdx.x + s]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    partial[(b * nblk + blockIdx.x) * 2] = sd[0];
+    partial[(b * nblk + blockIdx.x) * 2 + 1] = su[0];
+  }
+}
+
+__global__ void k_residual_final(const double* __restrict__ partial, int nblk, int batch, double* __restrict__ out) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= batch) return;
+  double md = 0.0, mu = 0.0;
+  for (int i = 0; i < nblk; ++i) {
+    md = fmax(md, partial[(size_t(b) * nblk + i) * 2]);
+    mu = fmax(mu, partial[(size_t(b) * nblk + i) * 2 + 1]);
+  }
+  out[2 * b] = md;
+  out[2 * b + 1] = mu;
+}
+
+cudaError_t launch_residual(const double* u, double* u_prev, const Dims& d, double* partial, int nblk,
+                            double* out, cudaStream_t s) {
+  const size_t per = size_t(3) * d.ncell;
+  k_residual<<<dim3(nblk, d.batch), 256, 0, s>>>(u, u_prev, per, partial, nblk);
+  k_residual_final<<<(d.batch + 255) / 256, 256, 0, s>>>(partial, nblk, d.batch, out);
+  return cudaGetLastError();
+}
+
 // Row means of FP64 populations into the reference table (ref_index
 // layout): one thread per (instance, row, population).
 __global__ void k_ref_from_state(const double* __restrict__ dbl, float* __restrict__ ref, Dims d) {

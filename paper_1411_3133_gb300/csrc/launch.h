@@ -88,6 +88,10 @@ cudaError_t launch_init(int prec, int K, void* f, const void* geo, const double*
                         const double* u_in, const Dims& d, cudaStream_t s);
 cudaError_t launch_convert(int prec, int to_double, void* state, double* dbl, size_t n, const Dims& d,
                            cudaStream_t s);
+// Per instance max |u - u_prev| and max |u| into out[2 b], out[2 b + 1];
+// u_prev = u afterwards (partial: batch * nblk * 2 doubles).
+cudaError_t launch_residual(const double* u, double* u_prev, const Dims& d, double* partial, int nblk,
+                            double* out, cudaStream_t s);
 // Reference table from the row means of FP64 populations (k_ref_from_state).
 cudaError_t launch_ref_from_state(const double* dbl, float* ref, const Dims& d, cudaStream_t s);
 // Reference populations of 2-byte storage (k_ref_table): mode 0 weights,

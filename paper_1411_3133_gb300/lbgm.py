@@ -90,6 +90,7 @@ SIGNATURES = {
     "lb_diagnostics": (ctypes.c_int, [_P, ctypes.POINTER(lb_diag)]),
     "lb_get_populations": (ctypes.c_int, [_P, _P, ctypes.c_int]),
     "lb_capture_reference": (ctypes.c_int, [_P]),
+    "lb_velocity_change": (ctypes.c_int, [_P, _P, _D, _D]),
     "lb_set_populations": (ctypes.c_int, [_P, _P, ctypes.c_int]),
     "lb_state_bytes": (ctypes.c_size_t, [_P]),
     "lb_get_state": (ctypes.c_int, [_P, _P, ctypes.c_size_t, ctypes.c_int]),
@@ -370,6 +371,15 @@ class LBContext:
             return out.reshape(self.batch, LB_Q, N)
         _check(load_library().lb_get_populations(self.ctx, _ptr(out), int(on_device)), self.ctx)
         return out
+
+    def lb_velocity_change(self, u_prev):
+        """(change, umax) per instance against the device array u_prev, which
+        is updated to the current velocity."""
+        ch = np.zeros(self.batch)
+        um = np.zeros(self.batch)
+        _check(load_library().lb_velocity_change(self.ctx, _ptr(u_prev), ch.ctypes.data_as(_D),
+                                                 um.ctypes.data_as(_D)), self.ctx)
+        return ch, um
 
     def lb_capture_reference(self):
         _check(load_library().lb_capture_reference(self.ctx), self.ctx)

@@ -244,3 +244,23 @@ def test_mixed_sweep_full_size_sampled_members_bitwise():
         batch.close()
         for c in ctxs:
             c.close()
+
+
+def test_velocity_change_monitor():
+    import torch
+    L = lib()
+    ctxs = _contexts("fp32")
+    c = ctxs[3]                                   # three instances
+    N = c.spec.ncells
+    u_prev = torch.empty(3 * 3 * N, dtype=torch.float64, device="cuda")
+    c.lb_macros(None, u_prev, on_device=True)
+    ch, um = c.lb_velocity_change(u_prev)
+    assert np.all(ch == 0)
+    _, u = c.lb_macros()
+    assert np.allclose(um, np.abs(u).reshape(3, -1).max(axis=1), rtol=0, atol=0)
+    before = u_prev.cpu().numpy().reshape(3, -1)
+    c.lb_step(5)
+    ch, um = c.lb_velocity_change(u_prev)
+    _, u = c.lb_macros()
+    assert np.allclose(ch, np.abs(u.reshape(3, -1) - before).max(axis=1), rtol=0, atol=0)
+    assert np.array_equal(u_prev.cpu().numpy().reshape(3, -1), u.reshape(3, -1))
