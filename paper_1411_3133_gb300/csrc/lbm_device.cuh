@@ -456,9 +456,18 @@ __device__ __forceinline__ void gather_edge(const S* __restrict__ fin, const flo
 
 // Load the 41 streamed populations of node p from the post-collision state
 // (instance block fin, reference table ref).
+// WALLS = 2 (either path): near an r-wall of a channel periodic in x3 with
+// bounce-back walls, the compile-time folds of gather_edge replace the
+// general wall rule (the same sources, fewer instructions).
 template <int K, class S, class R, int WALLS = 2>
 __device__ __forceinline__ void gather(const S* __restrict__ fin, const float* ref, const CellPos& p,
                                        const Dims& d, R (&f)[Q]) {
+  if constexpr (WALLS == 2) {
+    if (d.periodic3 && !d.wall_eq && d.nr >= 7 && near_wall(p, d)) {
+      gather_edge<K>(fin, ref, p, d, f);
+      return;
+    }
+  }
   for_each_source<K, S, WALLS>(fin, p, d, DecodeInto<K, S, R>{f, ref, d});
 }
 

@@ -42,3 +42,14 @@ def test_inputs_and_targets_layout():
     y = S.targets(rho, u)
     assert y.shape == (2 * spec.nr * spec.n3, 4)
     assert np.allclose(y[7], [7, 8, 9, 10])
+
+
+def test_steps_to_developed():
+    t = np.arange(1, 11) * 2000
+    grow = np.array([1e-6, 1e-5, 1e-4, 6e-4, 1.1e-3, 1.19e-3, 1.2e-3, 1.2e-3, 1.21e-3, 1.2e-3])
+    warm = np.full(10, 1.2e-3)
+    late = grow.copy()
+    late[-1] = 2e-3                                   # leaves the band at the end: never developed
+    a = np.stack([grow, warm, late], axis=1)
+    s = S.steps_to_developed(t, a, np.array([1.2e-3, 1.2e-3, 1.2e-3]))
+    assert s[0] == 10000 and s[1] == 2000 and np.isinf(s[2])
