@@ -52,4 +52,4 @@ def test_steps_to_developed():
     late[-1] = 2e-3                                   # leaves the band at the end: never developed
     a = np.stack([grow, warm, late], axis=1)
     s = S.steps_to_developed(t, a, np.array([1.2e-3, 1.2e-3, 1.2e-3]))
-    assert s[0] == 10000 and s[1] == 2000 and np.isinf(s[2])
+    assert s[0] == 12000 and s[1] == 2000 and np.isinf(s[2])      # 1.19e-3 is within 2 %
