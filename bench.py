@@ -190,6 +190,30 @@ def time_oracle(mode: str, steps: int = 1, reps: int = 1, budget: float = 120.0)
 
 
 # ---------------------------------------------------------------------------
+# multi-rank aggregation (weak scaling: every rank runs the whole workload)
+# ---------------------------------------------------------------------------
+def max_over_ranks(x: float, dist, device) -> float:
+    """The slowest rank's time (every rank gets it); x itself without a
+    process group."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_mlups(world: int, units_per_rank: int, steps: int, seconds: float) -> float:
+    """Node updates of all ranks per second, in millions."""
+    return world * units_per_rank * steps / seconds / 1e6
+
+
+def rank_seed(base: int, rank: int) -> int:
+    """Seed of rank `rank`'s copy of the workload (independent noise)."""
+    return base + 1000 * rank
+
+
+# ---------------------------------------------------------------------------
 # workloads
 # ---------------------------------------------------------------------------
 class SweepRunner:
@@ -206,7 +230,7 @@ class SweepRunner:
         params = []
         for b in range(wl.batch):
             G = L.lb_force_for_dean("cylindrical", desc, wl.taus[b], wl.deans[b])
-            params.append(L.make_params(wl.taus[b], G, False, wl.seeds[b] + 1000 * rank,
+            params.append(L.make_params(wl.taus[b], G, False, rank_seed(wl.seeds[b], rank),
                                         wl.noise_amp, True))
         self.ctx = L.LBContext(spec, batch=wl.batch, precision=wl.precision)
         self.ctx.lb_set_option(L.LB_OPT_USE_GRAPH, 1)
@@ -278,7 +302,7 @@ class MixedRunner:
         from paper_1411_3133_gb300.sweep import mixed_contexts
         from paper_1411_3133_gb300.workloads import mixed_batch
         self.args, self.L = args, L
-        self.insts = mixed_batch(seed=20241111 + 1000 * rank)
+        self.insts = mixed_batch(seed=rank_seed(20241111, rank))
         self.ctxs, self.batch = mixed_contexts(self.insts, args.precision)
         self.batch.lb_batch_set_option(L.LB_OPT_USE_GRAPH, 1)
         self.cells = self.batch.lb_batch_nodes()
@@ -402,12 +426,9 @@ def main():
     clocks = sampler.stop() if sampler else None
     d = runner.diagnostics()
     finite = all(x["nonfinite"] == 0 for x in d)
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist, "cuda")
     sec = ms / 1e3
-    value = world * cells * args.steps / sec / 1e6
+    value = whole_job_mlups(world, cells, args.steps, sec)
     per_launch = sec / args.steps
     bpu = BYTES_PER_UPDATE[args.precision]
     achieved = bpu * cells / per_launch / 1e9
@@ -419,11 +440,8 @@ def main():
     if dist:
         dist.barrier()
     e2e_sec, h2d, d2h = runner.e2e(args.e2e_steps)
-    if dist:
-        t = torch.tensor([e2e_sec], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_sec = float(t.item())
-    e2e_value = world * cells * args.e2e_steps / e2e_sec / 1e6
+    e2e_sec = max_over_ranks(e2e_sec, dist, "cuda")
+    e2e_value = whole_job_mlups(world, cells, args.e2e_steps, e2e_sec)
     runner.close()
 
     if rank == 0:
