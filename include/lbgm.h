@@ -399,8 +399,10 @@ lb_status lb_batch_create(lb_ctx* const* members, int count, lb_batch** out);
 lb_status lb_batch_step(lb_batch* batch, long long n);
 lb_status lb_batch_set_option(lb_batch* batch, int option, long long value);
 
-/* As lb_autotune over block_threads in {64, 128, 192, 256} x LB_OPT_SCHEDULE
- * in {0, 1}; the trial steps are real batch steps. */
+/* As lb_autotune over block_threads in {64, 96, 128} (FP64: {64, 96, 128,
+ * 192, 256}) x LB_OPT_SCHEDULE in {0, 1}; the trial steps are real batch
+ * steps. With FP32 arithmetic the work-list kernel runs at most 128 threads
+ * per block (LB_OPT_BLOCK_THREADS above that runs as 128). */
 lb_status lb_batch_autotune(lb_batch* batch, int steps_per_trial, lb_tune* best, lb_tune* trials,
                             int max_trials, int* n_trials);
 

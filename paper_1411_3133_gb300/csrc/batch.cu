@@ -119,6 +119,15 @@ void append_records(const lb_batch* b, int K, std::vector<unsigned char>& bytes,
   }
 }
 
+int max_threads(lb_precision p) {
+  switch (p) {
+    case LB_FP64: return step_list_max_threads_f64();
+    case LB_FP32: return step_list_max_threads_f32();
+    case LB_FP16_SHIFTED: return step_list_max_threads_h16();
+    default: return step_list_max_threads_b16();
+  }
+}
+
 cudaError_t occupancy(lb_precision p, int K, int threads, int* out) {
   switch (p) {
     case LB_FP64: return step_list_occupancy_f64(K, threads, out);
@@ -366,7 +375,9 @@ lb_status lb_batch_set_option(lb_batch* b, int option, long long value) {
       return LB_OK;
     case LB_OPT_BLOCK_THREADS:
       if (value < 64 || value > 256 || value % 32) return bfail(b, LB_ERR_ARG, "need 64..256, multiple of 32");
-      b->threads = int(value);
+      // tiles are block-sized: the work-list kernel's bound (128 with FP32
+      // arithmetic) caps the block
+      b->threads = std::min(int(value), max_threads(b->prec));
       return LB_OK;
     case LB_OPT_USE_GRAPH:
       b->use_graph = value ? 1 : 0;
@@ -387,8 +398,9 @@ lb_status lb_batch_autotune(lb_batch* b, int steps_per_trial, lb_tune* best, lb_
   if (steps_per_trial < 1) return bfail(b, LB_ERR_ARG, "need steps_per_trial >= 1");
   if (max_trials < 0 || (max_trials > 0 && !trials)) return bfail(b, LB_ERR_ARG, "bad trials buffer");
   std::vector<lb_tune> cand;
-  for (int t : {64, 128, 192, 256})
-    for (int sc : {0, 1}) cand.push_back({t, sc, 0, 0.0});
+  for (int t : {64, 96, 128, 192, 256})
+    if (t <= max_threads(b->prec))
+      for (int sc : {0, 1}) cand.push_back({t, sc, 0, 0.0});
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   LB_BCUDA(b, cudaEventCreate(&e0));
   cudaError_t e = cudaEventCreate(&e1);

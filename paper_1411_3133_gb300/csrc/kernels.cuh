@@ -71,11 +71,19 @@ template <>
 struct StepBounds<double, double> {
   static constexpr int maxt = 256, minb = 1;
 };
+// Per metric kind: one block fewer per SM for the ellipsoid, whose (i_r,
+// i_3) geometry rows and extra Christoffel terms need more registers.
+template <class S, class Real, int K>
+struct KBounds {
+  static constexpr int maxt = StepBounds<S, Real>::maxt;
+  static constexpr int minb = K == KELL && StepBounds<S, Real>::minb > 1 ? StepBounds<S, Real>::minb - 1
+                                                                          : StepBounds<S, Real>::minb;
+};
 // Uniform batch: fin/fout are whole states (batch blocks of Q * ncell);
 // block (x, y) updates nodes [x blockDim, (x + 1) blockDim) of instance y, so
 // the instance's block base is uniform across the thread block.
 template <typename S, typename Real, int K>
-__global__ void __launch_bounds__(StepBounds<S, Real>::maxt, StepBounds<S, Real>::minb)
+__global__ void __launch_bounds__(KBounds<S, Real, K>::maxt, KBounds<S, Real, K>::minb)
     k_step(const S* __restrict__ fin, S* __restrict__ fout, GeoDev<Real> geo,
            const InstParams<Real>* __restrict__ inst, Dims d, int* __restrict__ flag) {
   const uint32_t cell = blockIdx.x * blockDim.x + threadIdx.x;
@@ -92,7 +100,7 @@ __global__ void __launch_bounds__(StepBounds<S, Real>::maxt, StepBounds<S, Real>
 // gather alone, k_step_edge the 6 wall layers with the per-layer constant
 // folds (gather_edge), so neither kernel carries the other's code.
 template <typename S, typename Real, int K>
-__global__ void __launch_bounds__(StepBounds<S, Real>::maxt, StepBounds<S, Real>::minb)
+__global__ void __launch_bounds__(KBounds<S, Real, K>::maxt, KBounds<S, Real, K>::minb)
     k_step_bulk(const S* __restrict__ fin, S* __restrict__ fout, GeoDev<Real> geo,
                 const InstParams<Real>* __restrict__ inst, Dims d, int* __restrict__ flag) {
   const uint32_t layer = uint32_t(d.nt) * uint32_t(d.n3);
@@ -105,7 +113,7 @@ __global__ void __launch_bounds__(StepBounds<S, Real>::maxt, StepBounds<S, Real>
 }
 
 template <typename S, typename Real, int K>
-__global__ void __launch_bounds__(StepBounds<S, Real>::maxt, StepBounds<S, Real>::minb)
+__global__ void __launch_bounds__(KBounds<S, Real, K>::maxt, KBounds<S, Real, K>::minb)
     k_step_edge(const S* __restrict__ fin, S* __restrict__ fout, GeoDev<Real> geo,
                 const InstParams<Real>* __restrict__ inst, Dims d, int* __restrict__ flag) {
   const uint32_t layer = uint32_t(d.nt) * uint32_t(d.n3);
@@ -140,11 +148,13 @@ struct ListInst {
 // when gridDim.x < nwork). `parity` 0 reads f0 and writes f1, 1 the reverse.
 // The instance record is staged once per item in shared memory.
 template <typename S, typename Real, int K>
-__global__ void __launch_bounds__(256) k_step_list(const ListInst<S, Real>* __restrict__ insts,
+__global__ void __launch_bounds__(KBounds<S, Real, K>::maxt, KBounds<S, Real, K>::minb)
+    k_step_list(const ListInst<S, Real>* __restrict__ insts,
                                                    const int2* __restrict__ work, int nwork, int parity) {
   constexpr int kWords = sizeof(ListInst<S, Real>) / 4;
   static_assert(sizeof(ListInst<S, Real>) % 4 == 0, "record must be whole words");
   static_assert(kWords <= 64, "the smallest block (64 threads) copies the record");
+  static_assert(KBounds<S, Real, K>::maxt >= 64, "blocks of 64 threads must be allowed");
   __shared__ union {
     ListInst<S, Real> rec;
     uint32_t w[kWords];

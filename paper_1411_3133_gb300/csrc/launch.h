@@ -45,15 +45,19 @@ cudaError_t launch_step_split_b16(int K, const __nv_bfloat16* fin, __nv_bfloat16
 cudaError_t launch_step_list_f64(int K, const void* insts, const int2* work, int nwork, int threads,
                                  int grid, int parity, cudaStream_t s);
 cudaError_t step_list_occupancy_f64(int K, int threads, int* blocks_per_sm);
+int step_list_max_threads_f64();
 cudaError_t launch_step_list_f32(int K, const void* insts, const int2* work, int nwork, int threads,
                                  int grid, int parity, cudaStream_t s);
 cudaError_t step_list_occupancy_f32(int K, int threads, int* blocks_per_sm);
+int step_list_max_threads_f32();
 cudaError_t launch_step_list_h16(int K, const void* insts, const int2* work, int nwork, int threads,
                                  int grid, int parity, cudaStream_t s);
 cudaError_t step_list_occupancy_h16(int K, int threads, int* blocks_per_sm);
+int step_list_max_threads_h16();
 cudaError_t launch_step_list_b16(int K, const void* insts, const int2* work, int nwork, int threads,
                                  int grid, int parity, cudaStream_t s);
 cudaError_t step_list_occupancy_b16(int K, int threads, int* blocks_per_sm);
+int step_list_max_threads_b16();
 
 // Prefetching step kernel (cp.async into shared memory); each thread updates
 // npt nodes.

@@ -456,14 +456,16 @@ __device__ __forceinline__ void gather_edge(const S* __restrict__ fin, const flo
 
 // Load the 41 streamed populations of node p from the post-collision state
 // (instance block fin, reference table ref).
-// WALLS = 2 (either path): near an r-wall of a channel periodic in x3 with
-// bounce-back walls, the compile-time folds of gather_edge replace the
-// general wall rule (the same sources, fewer instructions).
+// WALLS = 2 (either path): near an r-wall with bounce-back walls, at least 3
+// nodes away from any x3 wall, only the r-wall can lie on a population's
+// path, and the compile-time folds of gather_edge replace the general wall
+// rule (the same sources, fewer instructions).
 template <int K, class S, class R, int WALLS = 2>
 __device__ __forceinline__ void gather(const S* __restrict__ fin, const float* ref, const CellPos& p,
                                        const Dims& d, R (&f)[Q]) {
   if constexpr (WALLS == 2) {
-    if (d.periodic3 && !d.wall_eq && d.nr >= 7 && near_wall(p, d)) {
+    const bool x3_clear = d.periodic3 || (p.i3 >= 3 && p.i3 <= d.n3 - 4);
+    if (!d.wall_eq && d.nr >= 7 && x3_clear && (p.ir < 3 || p.ir > d.nr - 4)) {
       gather_edge<K>(fin, ref, p, d, f);
       return;
     }

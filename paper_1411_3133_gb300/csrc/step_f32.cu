@@ -15,6 +15,8 @@ cudaError_t launch_step_list_f32(int K, const void* insts, const int2* work, int
   return launch_step_list_t<float, float>(K, insts, work, nwork, threads, grid, parity, s);
 }
 
+int step_list_max_threads_f32() { return step_list_max_threads_t<float, float>(); }
+
 cudaError_t step_list_occupancy_f32(int K, int threads, int* blocks_per_sm) {
   return step_list_occupancy_t<float, float>(K, threads, blocks_per_sm);
 }

@@ -15,6 +15,8 @@ cudaError_t launch_step_list_f64(int K, const void* insts, const int2* work, int
   return launch_step_list_t<double, double>(K, insts, work, nwork, threads, grid, parity, s);
 }
 
+int step_list_max_threads_f64() { return step_list_max_threads_t<double, double>(); }
+
 cudaError_t step_list_occupancy_f64(int K, int threads, int* blocks_per_sm) {
   return step_list_occupancy_t<double, double>(K, threads, blocks_per_sm);
 }

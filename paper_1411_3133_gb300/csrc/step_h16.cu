@@ -15,6 +15,8 @@ cudaError_t launch_step_list_h16(int K, const void* insts, const int2* work, int
   return launch_step_list_t<__half, float>(K, insts, work, nwork, threads, grid, parity, s);
 }
 
+int step_list_max_threads_h16() { return step_list_max_threads_t<__half, float>(); }
+
 cudaError_t step_list_occupancy_h16(int K, int threads, int* blocks_per_sm) {
   return step_list_occupancy_t<__half, float>(K, threads, blocks_per_sm);
 }

@@ -68,6 +68,12 @@ cudaError_t launch_step_list_t(int K, const void* insts, const int2* work, int n
   return cudaGetLastError();
 }
 
+// Largest block of the work-list kernel (its launch bounds).
+template <class S, class R>
+int step_list_max_threads_t() {
+  return StepBounds<S, R>::maxt;
+}
+
 // Resident blocks per SM of the work-list kernel at `threads` per block.
 template <class S, class R>
 cudaError_t step_list_occupancy_t(int K, int threads, int* blocks_per_sm) {

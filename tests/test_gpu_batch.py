@@ -130,12 +130,12 @@ def test_batch_autotune_steps_are_real_steps():
     batched, alone = _contexts("fp32"), _contexts("fp32")
     batch = L.LBBatch(batched)
     best, trials = batch.lb_batch_autotune(steps_per_trial=3)
-    assert len(trials) == 8
+    assert len(trials) == 6                               # FP32: blocks up to 128
     assert {(t["block_threads"], t["schedule"]) for t in trials} == \
-        {(t, s) for t in (64, 128, 192, 256) for s in (0, 1)}
+        {(t, s) for t in (64, 96, 128) for s in (0, 1)}
     assert all(t["ms_per_step"] > 0 for t in trials)
     assert best["ms_per_step"] == min(t["ms_per_step"] for t in trials)
-    steps = 8 * (3 + 1)
+    steps = 6 * (3 + 1)
     assert batch.lb_batch_step_count() == steps
     batch.lb_batch_step(5)          # with the chosen configuration
     for c in alone:
