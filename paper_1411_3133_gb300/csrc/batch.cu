@@ -1,8 +1,10 @@
 // Batches of contexts of different geometry (lb_batch_* of include/lbgm.h).
 //
 // Every instance of every member becomes one ListInst record; instances are
-// grouped by metric kind and each group gets a work list of (instance, first
-// node) tiles. One batch step is one k_step_list launch per group; groups
+// grouped by metric kind and each group gets two work lists: tiles of
+// interior nodes (instance, first node, count) and tiles of wall nodes
+// (instance, first index into a list of wall-node indices, count). One batch
+// step is two k_step_list launches per group (interior, then walls); groups
 // after the first run on forked streams so that small groups overlap.
 #include <cuda_runtime.h>
 
@@ -23,11 +25,42 @@ constexpr int kMaxGroups = 3;  // flat, cylinder, ellipsoid
 struct Group {
   int K = 0;
   int ninst = 0;
-  int nwork = 0;
-  size_t inst_off = 0;   // byte offset of the ListInst records in dmem
-  size_t work_off = 0;   // byte offset of the int2 tiles in dmem
-  int blocks_per_sm = 0; // occupancy of k_step_list<K> at the built block size
+  int nwork[2] = {0, 0};        // interior tiles, wall-node tiles
+  size_t inst_off = 0;          // byte offset of the ListInst records in dmem
+  size_t work_off[2] = {0, 0};  // byte offsets of the int4 tiles in dmem
+  size_t cells_off = 0;         // byte offset of the wall-node indices in dmem
+  int blocks_per_sm = 0;        // occupancy of the interior kernel at the built block size
 };
+
+// Tiles of one instance (group-local index li): runs of interior nodes (no
+// wall within 3 nodes) as (li, first node, count), and the wall nodes' indices
+// appended to `cells` as (li, first index, count); counts <= threads.
+void instance_tiles(const Dims& d, int li, int threads, std::vector<int4>& interior, std::vector<int4>& wall,
+                    std::vector<int>& cells) {
+  const int nr = d.nr, nt = d.nt, n3 = d.n3;
+  auto inner_r = [&](int ir) { return ir >= 3 && ir <= nr - 4; };
+  auto inner_3 = [&](int i3) { return d.periodic3 || (i3 >= 3 && i3 <= n3 - 4); };
+  int run_start = -1;
+  auto close_run = [&](int end) {
+    for (int a = run_start; a < end; a += threads) interior.push_back(make_int4(li, a, std::min(threads, end - a), 0));
+    run_start = -1;
+  };
+  const size_t w0 = cells.size();
+  for (int ir = 0; ir < nr; ++ir)
+    for (int it = 0; it < nt; ++it)
+      for (int i3 = 0; i3 < n3; ++i3) {
+        const int cell = (ir * nt + it) * n3 + i3;
+        if (inner_r(ir) && inner_3(i3)) {
+          if (run_start < 0) run_start = cell;
+        } else {
+          if (run_start >= 0) close_run(cell);
+          cells.push_back(cell);
+        }
+      }
+  if (run_start >= 0) close_run(nr * nt * n3);
+  for (size_t a = w0; a < cells.size(); a += size_t(threads))
+    wall.push_back(make_int4(li, int(a), int(std::min(size_t(threads), cells.size() - a)), 0));
+}
 
 }  // namespace
 
@@ -143,9 +176,9 @@ lb_status build(lb_batch* b) {
   drop_graph(b);
   b->built = false;
   std::vector<unsigned char> recs;
-  std::vector<int2> work;
+  std::vector<int4> tiles[kMaxGroups][2];
+  std::vector<int> cells[kMaxGroups];
   b->ngroups = 0;
-  size_t rec_total = 0;
   for (int K : {int(KCYL), int(KELL), int(KFLAT)}) {
     Group gr;
     gr.K = K;
@@ -159,23 +192,31 @@ lb_status build(lb_batch* b) {
     if (gr.ninst == 0) continue;
     gr.inst_off = before;
     // tiles, instance-major; instance ids are local to the group
-    const size_t w0 = work.size();
+    const int gi = b->ngroups;
     int local = 0;
     for (const lb_ctx* c : b->m) {
       if (c->K != K) continue;
       for (int bi = 0; bi < c->batch; ++bi, ++local)
-        for (size_t t = 0; t < c->ncell; t += size_t(b->threads)) work.push_back(make_int2(local, int(t)));
+        instance_tiles(c->dims, local, b->threads, tiles[gi][0], tiles[gi][1], cells[gi]);
     }
-    gr.nwork = int(work.size() - w0);
-    gr.work_off = w0;  // in tiles for now
+    gr.nwork[0] = int(tiles[gi][0].size());
+    gr.nwork[1] = int(tiles[gi][1].size());
     cudaError_t e = occupancy(b->prec, K, b->threads, &gr.blocks_per_sm);
     if (e != cudaSuccess) return bcuda(b, e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
     b->g[b->ngroups++] = gr;
-    rec_total = recs.size();
   }
-  const size_t work_base = (rec_total + 255) / 256 * 256;
-  for (int i = 0; i < b->ngroups; ++i) b->g[i].work_off = work_base + b->g[i].work_off * sizeof(int2);
-  const size_t need = work_base + work.size() * sizeof(int2);
+  // layout: records | per group: interior tiles, wall tiles, wall-node indices
+  auto al = [](size_t x) { return (x + 255) / 256 * 256; };
+  size_t off = al(recs.size());
+  for (int i = 0; i < b->ngroups; ++i) {
+    for (int m = 0; m < 2; ++m) {
+      b->g[i].work_off[m] = off;
+      off = al(off + tiles[i][m].size() * sizeof(int4));
+    }
+    b->g[i].cells_off = off;
+    off = al(off + cells[i].size() * sizeof(int));
+  }
+  const size_t need = off;
   if (need > b->dmem_bytes) {
     if (b->dmem) cudaFree(b->dmem);
     b->dmem = nullptr;
@@ -185,8 +226,15 @@ lb_status build(lb_batch* b) {
   }
   unsigned char* base = static_cast<unsigned char*>(b->dmem);
   LB_BCUDA(b, cudaMemcpyAsync(base, recs.data(), recs.size(), cudaMemcpyHostToDevice, b->stream));
-  LB_BCUDA(b, cudaMemcpyAsync(base + work_base, work.data(), work.size() * sizeof(int2), cudaMemcpyHostToDevice,
-                              b->stream));
+  for (int i = 0; i < b->ngroups; ++i) {
+    for (int m = 0; m < 2; ++m)
+      if (!tiles[i][m].empty())
+        LB_BCUDA(b, cudaMemcpyAsync(base + b->g[i].work_off[m], tiles[i][m].data(),
+                                    tiles[i][m].size() * sizeof(int4), cudaMemcpyHostToDevice, b->stream));
+    if (!cells[i].empty())
+      LB_BCUDA(b, cudaMemcpyAsync(base + b->g[i].cells_off, cells[i].data(), cells[i].size() * sizeof(int),
+                                  cudaMemcpyHostToDevice, b->stream));
+  }
   LB_BCUDA(b, cudaStreamSynchronize(b->stream));  // the host vectors go out of scope
   b->base_cur.resize(b->m.size());
   for (size_t i = 0; i < b->m.size(); ++i) b->base_cur[i] = b->m[i]->cur;
@@ -205,18 +253,32 @@ bool records_current(const lb_batch* b) {
   return true;
 }
 
+// The interior tiles, then the wall-node tiles of one group, on stream s.
 cudaError_t launch_group(const lb_batch* b, const Group& gr, cudaStream_t s) {
   const unsigned char* base = static_cast<const unsigned char*>(b->dmem);
   const void* insts = base + gr.inst_off;
-  const int2* work = reinterpret_cast<const int2*>(base + gr.work_off);
+  const int* cells = reinterpret_cast<const int*>(base + gr.cells_off);
   const int grid = b->schedule == 1 ? std::max(1, gr.blocks_per_sm) * b->nsm : 0;
-  switch (b->prec) {
-    case LB_FP64: return launch_step_list_f64(gr.K, insts, work, gr.nwork, b->threads, grid, b->parity, s);
-    case LB_FP32: return launch_step_list_f32(gr.K, insts, work, gr.nwork, b->threads, grid, b->parity, s);
-    case LB_FP16_SHIFTED:
-      return launch_step_list_h16(gr.K, insts, work, gr.nwork, b->threads, grid, b->parity, s);
-    default: return launch_step_list_b16(gr.K, insts, work, gr.nwork, b->threads, grid, b->parity, s);
+  for (int m = 0; m < 2; ++m) {
+    const int4* work = reinterpret_cast<const int4*>(base + gr.work_off[m]);
+    cudaError_t e;
+    switch (b->prec) {
+      case LB_FP64:
+        e = launch_step_list_f64(gr.K, m, insts, work, gr.nwork[m], cells, b->threads, grid, b->parity, s);
+        break;
+      case LB_FP32:
+        e = launch_step_list_f32(gr.K, m, insts, work, gr.nwork[m], cells, b->threads, grid, b->parity, s);
+        break;
+      case LB_FP16_SHIFTED:
+        e = launch_step_list_h16(gr.K, m, insts, work, gr.nwork[m], cells, b->threads, grid, b->parity, s);
+        break;
+      default:
+        e = launch_step_list_b16(gr.K, m, insts, work, gr.nwork[m], cells, b->threads, grid, b->parity, s);
+        break;
+    }
+    if (e != cudaSuccess) return e;
   }
+  return cudaSuccess;
 }
 
 // One batch step: group 0 on the batch stream, the others forked.

@@ -142,15 +142,21 @@ struct ListInst {
   int* flag;
 };
 
-// Work-list step over instances of one metric kind. Work item j updates the
-// nodes [work[j].y, work[j].y + blockDim.x) of instance work[j].x; blocks
-// take items j = blockIdx.x, blockIdx.x + gridDim.x, ... (a persistent grid
-// when gridDim.x < nwork). `parity` 0 reads f0 and writes f1, 1 the reverse.
-// The instance record is staged once per item in shared memory.
-template <typename S, typename Real, int K>
+// Work-list step over instances of one metric kind. Work item j = (instance,
+// first, count) covers `count` <= blockDim.x nodes of one instance: with
+// WALLS = 0 the interior nodes first .. first + count - 1 (no wall within 3
+// nodes: the far-from-wall gather alone), with WALLS = 2 the nodes
+// cells[first .. first + count - 1] (the wall nodes: folds, or clamps for
+// equilibrium walls). Splitting the two keeps the interior kernel's code small
+// (instruction fetch is what binds a kernel carrying every wall variant).
+// Blocks take items j = blockIdx.x, blockIdx.x + gridDim.x, ... (a
+// persistent grid when gridDim.x < nwork). `parity` 0 reads f0 and writes f1,
+// 1 the reverse. The instance record is staged once per item in shared
+// memory.
+template <typename S, typename Real, int K, int WALLS>
 __global__ void __launch_bounds__(KBounds<S, Real, K>::maxt, KBounds<S, Real, K>::minb)
-    k_step_list(const ListInst<S, Real>* __restrict__ insts,
-                                                   const int2* __restrict__ work, int nwork, int parity) {
+    k_step_list(const ListInst<S, Real>* __restrict__ insts, const int4* __restrict__ work, int nwork,
+                const int* __restrict__ cells, int parity) {
   constexpr int kWords = sizeof(ListInst<S, Real>) / 4;
   static_assert(sizeof(ListInst<S, Real>) % 4 == 0, "record must be whole words");
   static_assert(kWords <= 64, "the smallest block (64 threads) copies the record");
@@ -160,19 +166,19 @@ __global__ void __launch_bounds__(KBounds<S, Real, K>::maxt, KBounds<S, Real, K>
     uint32_t w[kWords];
   } sh;
   for (int j = blockIdx.x; j < nwork; j += gridDim.x) {
-    const int2 w = work[j];
+    const int4 w = work[j];
     __syncthreads();  // the previous item's readers are done
     if (threadIdx.x < kWords)
       sh.w[threadIdx.x] = reinterpret_cast<const uint32_t*>(insts + w.x)[threadIdx.x];
     __syncthreads();
     const ListInst<S, Real>& I = sh.rec;
-    const uint32_t t = uint32_t(w.y) + threadIdx.x;
-    if (t < uint32_t(I.d.ncell)) {
+    if (int(threadIdx.x) < w.z) {
+      const uint32_t t = WALLS == 0 ? uint32_t(w.y) + threadIdx.x : uint32_t(cells[w.y + threadIdx.x]);
       const Dims d = I.d;
       const CellPos p = locate(d, t);
       const S* fin = parity ? I.f1 : I.f0;
       S* fout = const_cast<S*>(parity ? I.f0 : I.f1);
-      step_node<S, Real, K>(fin, fout, d.ref, I.geo, *I.ip, d, p, I.flag);
+      step_node<S, Real, K, WALLS>(fin, fout, d.ref, I.geo, *I.ip, d, p, I.flag);
     }
   }
 }

@@ -10,9 +10,9 @@ cudaError_t launch_step_b16(int K, const __nv_bfloat16* fin, __nv_bfloat16* fout
   return launch_step_t<__nv_bfloat16, float>(K, fin, fout, geo, inst, d, flag, threads, s);
 }
 
-cudaError_t launch_step_list_b16(int K, const void* insts, const int2* work, int nwork, int threads,
-                                 int grid, int parity, cudaStream_t s) {
-  return launch_step_list_t<__nv_bfloat16, float>(K, insts, work, nwork, threads, grid, parity, s);
+cudaError_t launch_step_list_b16(int K, int walls, const void* insts, const int4* work, int nwork,
+                                 const int* cells, int threads, int grid, int parity, cudaStream_t s) {
+  return launch_step_list_t<__nv_bfloat16, float>(K, walls, insts, work, nwork, cells, threads, grid, parity, s);
 }
 
 int step_list_max_threads_b16() { return step_list_max_threads_t<__nv_bfloat16, float>(); }

@@ -53,18 +53,23 @@ cudaError_t launch_step_split_t(int K, const S* fin, S* fout, const GeoDev<R>& g
 }
 
 // grid 0: one block per work item; otherwise `grid` persistent blocks.
+// walls 0: interior tiles (cells NULL); 1: wall-node tiles over `cells`.
 template <class S, class R>
-cudaError_t launch_step_list_t(int K, const void* insts, const int2* work, int nwork, int threads, int grid,
-                               int parity, cudaStream_t s) {
+cudaError_t launch_step_list_t(int K, int walls, const void* insts, const int4* work, int nwork, const int* cells,
+                               int threads, int grid, int parity, cudaStream_t s) {
   if (nwork == 0) return cudaSuccess;
   const auto* I = static_cast<const ListInst<S, R>*>(insts);
   const int g = grid > 0 && grid < nwork ? grid : nwork;
+#define LB_LIST(KK)                                                                          \
+  (walls ? (k_step_list<S, R, KK, 2><<<g, threads, 0, s>>>(I, work, nwork, cells, parity), 0) \
+         : (k_step_list<S, R, KK, 0><<<g, threads, 0, s>>>(I, work, nwork, cells, parity), 0))
   switch (K) {
-    case KFLAT: k_step_list<S, R, KFLAT><<<g, threads, 0, s>>>(I, work, nwork, parity); break;
-    case KCYL: k_step_list<S, R, KCYL><<<g, threads, 0, s>>>(I, work, nwork, parity); break;
-    case KELL: k_step_list<S, R, KELL><<<g, threads, 0, s>>>(I, work, nwork, parity); break;
+    case KFLAT: LB_LIST(KFLAT); break;
+    case KCYL: LB_LIST(KCYL); break;
+    case KELL: LB_LIST(KELL); break;
     default: return cudaErrorInvalidValue;
   }
+#undef LB_LIST
   return cudaGetLastError();
 }
 
@@ -79,11 +84,11 @@ template <class S, class R>
 cudaError_t step_list_occupancy_t(int K, int threads, int* blocks_per_sm) {
   switch (K) {
     case KFLAT:
-      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_step_list<S, R, KFLAT>, threads, 0);
+      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_step_list<S, R, KFLAT, 0>, threads, 0);
     case KCYL:
-      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_step_list<S, R, KCYL>, threads, 0);
+      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_step_list<S, R, KCYL, 0>, threads, 0);
     case KELL:
-      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_step_list<S, R, KELL>, threads, 0);
+      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_step_list<S, R, KELL, 0>, threads, 0);
     default:
       return cudaErrorInvalidValue;
   }
