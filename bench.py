@@ -235,7 +235,7 @@ class SweepRunner:
         self.ctx = L.LBContext(spec, batch=wl.batch, precision=wl.precision)
         self.ctx.lb_set_option(L.LB_OPT_USE_GRAPH, 1)
         self.ctx.lb_set_option(L.LB_OPT_STEP_KERNEL,
-                               {"auto": 0, "plain": 1, "tma": 2, "async": 3, "split": 4}[args.step_kernel])
+                               {"auto": 0, "plain": 1, "tma": 2, "async": 3, "split": 4, "tiled": 5}[args.step_kernel])
         self.ctx.lb_set_option(L.LB_OPT_BLOCK_THREADS, args.threads)
         self.ctx.lb_set_option(L.LB_OPT_NODES_PER_THREAD, args.npt)
         self.ctx.lb_init(params)
@@ -289,6 +289,47 @@ class SweepRunner:
 
     def close(self):
         self.ctx.close()
+
+
+class EllipsoidRunner(SweepRunner):
+    """24 instances of the double-curved channel of Sec. IV.B (R2/R1 = 1,
+    64 x 4 x 256, walls on r and phi), De linspace(20, 150, 24) through the
+    force of the cylinder of the same streamwise radius and width, tau 0.55,
+    from rest plus noise."""
+
+    def __init__(self, args, L, rank):
+        from paper_1411_3133_gb300.workloads import ellipsoid_cross_section
+        self.args, self.L = args, L
+        wl = ellipsoid_cross_section(1.0, precision=args.precision)
+        self.wl = wl
+        spec = L.ChannelSpec(**wl.geometry_kwargs())
+        ref = L.make_desc(1.0, 1.0 + (wl.r_outer - wl.r_inner), wl.nr, wl.ntheta, wl.n3)
+        params = [L.make_params(0.55, L.lb_force_for_dean("cylindrical", ref, 0.55, float(de)), False,
+                                rank_seed(wl.seeds[0] + b, rank), 1e-4, False)
+                  for b, de in enumerate(__import__("numpy").linspace(20, 150, 24))]
+        self.batch = 24
+        self.ctx = L.LBContext(spec, batch=24, precision=args.precision)
+        self.ctx.lb_set_option(L.LB_OPT_USE_GRAPH, 1)
+        self.ctx.lb_set_option(L.LB_OPT_STEP_KERNEL,
+                               {"auto": 0, "plain": 1, "tma": 2, "async": 3, "split": 4, "tiled": 5}[args.step_kernel])
+        self.ctx.lb_set_option(L.LB_OPT_BLOCK_THREADS, args.threads)
+        self.ctx.lb_init(params)
+        self.cells = 24 * wl.ncells
+        self.stream = self.ctx.stream
+        if args.step_kernel == "auto":
+            args.step_kernel = "plain" if args.precision == "fp64" else "tiled"
+        self.kernel = {"tiled": f"k_step_list<{args.precision},KELL> interior + wall tiles ({args.threads} threads)"
+                       }.get(args.step_kernel, f"k_step<{args.precision},KELL> ({args.threads} threads)")
+        self.profiled = False
+        self.launches_per_step = 2 if args.step_kernel == "tiled" else 1
+
+    def config(self):
+        wl = self.wl
+        return {"workload": f"double-curved channel (ellipsoidal coordinates, R2/R1 = 1, d = R1/40) "
+                            f"{wl.nr}x{wl.ntheta}x{wl.n3}, walls on r and phi, 24 instances (De 20..150), "
+                            f"D3Q41, {self.args.precision}",
+                "cells_per_instance": wl.ncells, "instances": 24, "precision": self.args.precision,
+                "l2": f"inputs larger than L2: state {2 * self.state_bytes / 1e6:.0f} MB, no flush"}
 
 
 class MixedRunner:
@@ -368,13 +409,14 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--cpu-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--step-kernel", default="auto", choices=["auto", "plain", "tma", "async", "split"])
+    ap.add_argument("--step-kernel", default="auto", choices=["auto", "plain", "tma", "async", "split", "tiled"])
     ap.add_argument("--npt", type=int, default=4, help="nodes per thread of the prefetching kernel")
     ap.add_argument("--threads", type=int, default=128, help="threads per block of the step kernel")
     ap.add_argument("--precision", default="fp32", choices=sorted(BYTES_PER_UPDATE))
-    ap.add_argument("--workload", default="sweep", choices=["sweep", "mixed"],
+    ap.add_argument("--workload", default="sweep", choices=["sweep", "mixed", "ellipsoid"],
                     help="sweep: 24-instance 64x4x256 cylinder Dean sweep; mixed: 128 channels "
-                         "of mixed metric and size in one lb_batch")
+                         "of mixed metric and size in one lb_batch; ellipsoid: 24 instances of the "
+                         "64x4x256 double-curved channel with four walls")
     ap.add_argument("--tune-steps", type=int, default=20,
                     help="mixed: steps per autotuner trial (taken inside the warm-up)")
     args = ap.parse_args()
@@ -400,7 +442,7 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
 
-    runner = (MixedRunner if args.workload == "mixed" else SweepRunner)(args, L, rank)
+    runner = {"mixed": MixedRunner, "ellipsoid": EllipsoidRunner}.get(args.workload, SweepRunner)(args, L, rank)
     cells = runner.cells
     stream = runner.stream
 

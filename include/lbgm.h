@@ -162,8 +162,9 @@ typedef enum {
                                register cap); larger values run as 128 */
   LB_OPT_USE_GRAPH = 2,     /* 1: lb_step replays a captured CUDA graph of
                                pairs of steps (default 0) */
-  LB_OPT_STEP_KERNEL = 3,   /* 0: automatic (default): 4 where x3 is
-                               periodic and the arithmetic FP32, else 1;
+  LB_OPT_STEP_KERNEL = 3,   /* 0: automatic (default): FP64 arithmetic 1,
+                               else 4 where x3 is periodic with bounce-back
+                               walls, else 5;
                                1: the one-node-per-thread kernel, gathering
                                from global memory; 2: the TMA-pipelined
                                kernel (FP32, bounce-back walls and n3 in
@@ -176,7 +177,10 @@ typedef enum {
                                bounce-back walls only): one
                                kernel for the 3 node layers next to each
                                r-wall, one for the interior without any
-                               wall code.
+                               wall code; 5: tiled: runs of interior nodes
+                               and the wall nodes in two kernels (the
+                               lb_batch work-list kernels over this context
+                               alone), for any geometry.
                                Unsupported choices return LB_ERR_ARG. All
                                give bitwise identical states. */
   LB_OPT_SCHEDULE = 4,      /* batches only (lb_batch_set_option): 0: one
@@ -348,7 +352,8 @@ lb_status lb_diagnostics_noalloc(lb_metric metric, const lb_geometry_desc* geom,
 /* Autotuner of the step launch. Runs steps_per_trial (>= 1) time steps in
  * each configuration -- block_threads in {64, 96, 128} (FP64: {64, 128, 192,
  * 256}) with the plain step kernel, {64, 96, 128} with the region split
- * where x3 is periodic, the TMA kernel where the context supports it, and the
+ * where x3 is periodic and with the tiled step, the TMA kernel where the
+ * context supports it, and the
  * prefetching kernel with block_threads in {128, 256} x
  * nodes_per_thread in {2, 4, 8} -- timed with
  * CUDA events on the context's stream, then keeps the fastest. Every

@@ -237,7 +237,8 @@ cudaError_t launch_split(lb_ctx* c, int src, int dst) {
 // arithmetic is FP32 (measured fastest there), the one-kernel step otherwise.
 int resolved_kernel(const lb_ctx* c) {
   if (c->step_kernel != 0) return c->step_kernel;
-  return (c->geom.periodic3 && c->geom.wall == LB_WALL_BOUNCEBACK && c->prec != LB_FP64) ? 4 : 1;
+  if (c->prec == LB_FP64) return 1;
+  return (c->geom.periodic3 && c->geom.wall == LB_WALL_BOUNCEBACK) ? 4 : 5;
 }
 
 lb_status launch_step_once(lb_ctx* c) {
@@ -263,6 +264,12 @@ lb_status launch_step_once(lb_ctx* c) {
                               c->block_threads, c->nodes_per_thread, c->stream);
   else if (kern == 4)
     e = launch_split(c, src, dst);
+  else if (kern == 5) {
+    lb_status st = ctx_tiled_prepare(c);  // a no-op once the tiles are current
+    if (st == LB_OK) st = ctx_tiled_launch(c);
+    if (st != LB_OK) return st;
+    e = cudaSuccess;
+  }
   else if (use_tma(c))
     e = launch_step_tma_f32(c->K, c->tmap[src], static_cast<const float*>(c->f[src]),
                             static_cast<float*>(c->f[dst]), c->geo_f,
@@ -580,6 +587,10 @@ lb_status lb_step(lb_ctx* c, long long n) {
       ++c->step;
       --n;
     }
+    if (resolved_kernel(c) == 5) {  // tiles are uploaded outside the capture
+      s = ctx_tiled_prepare(c);
+      if (s != LB_OK) return s;
+    }
     if (!c->graph || c->graph_threads != c->block_threads || c->graph_kernel != c->step_kernel ||
         c->graph_npt != c->nodes_per_thread) {
       if (c->graph) cudaGraphExecDestroy(c->graph);
@@ -785,8 +796,9 @@ lb_status lb_set_option(lb_ctx* c, int option, long long value) {
       c->use_graph = value ? 1 : 0;
       return LB_OK;
     case LB_OPT_STEP_KERNEL:
-      if (value < 0 || value > 4)
-        return fail(c, LB_ERR_ARG, "need 0 (auto), 1 (plain), 2 (TMA), 3 (prefetching) or 4 (region split)");
+      if (value < 0 || value > 5)
+        return fail(c, LB_ERR_ARG,
+                    "need 0 (auto), 1 (plain), 2 (TMA), 3 (prefetching), 4 (region split) or 5 (tiled)");
       if (value == 4 && (!c->geom.periodic3 || c->geom.wall != LB_WALL_BOUNCEBACK))
         return fail(c, LB_ERR_ARG, "the region-split step kernel needs a periodic x3 axis and bounce-back walls");
       if (value == 2 && !c->tma_ok)
@@ -823,6 +835,7 @@ lb_status lb_autotune(lb_ctx* c, int steps_per_trial, lb_tune* best, lb_tune* tr
     for (int t : {64, 96, 128}) cand.push_back({t, 1, 0, 0.0});
   if (c->geom.periodic3 && c->geom.wall == LB_WALL_BOUNCEBACK)
     for (int t : {64, 96, 128}) cand.push_back({t, 4, 0, 0.0});
+  for (int t : {64, 96, 128}) cand.push_back({t, 5, 0, 0.0});
   if (c->tma_ok) cand.push_back({0, 2, 0, 0.0});  // the TMA kernel fixes its own block shape
   for (int t : {128, 256})
     for (int npt : {2, 4, 8}) cand.push_back({t, 3, npt, 0.0});
@@ -877,6 +890,7 @@ lb_status lb_autotune(lb_ctx* c, int steps_per_trial, lb_tune* best, lb_tune* tr
 void lb_destroy(lb_ctx* c) {
   if (!c) return;
   cudaStreamSynchronize(c->stream);
+  lb_batch_destroy(c->tiles);
   if (c->aux) {
     cudaStreamSynchronize(c->aux);
     cudaStreamDestroy(c->aux);

@@ -379,6 +379,35 @@ lb_status run(lb_batch* b, long long n, bool graph) {
 
 }  // namespace
 
+// A context stepped through its own single-member batch (interior and
+// wall-node tiles in separate kernels): build the tiles for the context's
+// current buffer and block size, outside any stream capture.
+lb_status lbgm::ctx_tiled_prepare(lb_ctx* c) {
+  if (!c->tiles) {
+    lb_ctx* one[1] = {c};
+    lb_status s = lb_batch_create(one, 1, &c->tiles);
+    if (s != LB_OK) return ctx_fail(c, s, std::string("tiled step: ") + lb_last_error(nullptr));
+  }
+  lb_batch* b = c->tiles;
+  b->threads = std::min(c->block_threads, max_threads(b->prec));
+  if (!records_current(b)) {
+    lb_status s = build(b);
+    if (s != LB_OK) return ctx_fail(c, s, "tiled step: " + b->err);
+  }
+  return LB_OK;
+}
+
+// One step's launches; the caller flips the context's buffer and counts the
+// step (the batch's parity follows, so its records stay current).
+lb_status lbgm::ctx_tiled_launch(lb_ctx* c) {
+  lb_batch* b = c->tiles;
+  if (!b || !records_current(b) || b->threads != std::min(c->block_threads, max_threads(b->prec)))
+    return ctx_fail(c, LB_ERR_STATE, "tiled step used without preparation");
+  lb_status s = step_once(b);
+  if (s != LB_OK) return ctx_fail(c, s, "tiled step: " + b->err);
+  return LB_OK;
+}
+
 extern "C" {
 
 lb_status lb_batch_create(lb_ctx* const* members, int count, lb_batch** out) {

@@ -66,6 +66,7 @@ struct lb_ctx {
   int step_kernel = 0;               // LB_OPT_STEP_KERNEL
   int nodes_per_thread = 4;          // LB_OPT_NODES_PER_THREAD
   int graph_npt = 0;
+  lb_batch* tiles = nullptr;         // private single-member batch of the tiled step
   cudaStream_t aux = nullptr;        // second stream of the region-split step
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   bool tma_ok = false;               // tensor maps built for both buffers
@@ -79,5 +80,9 @@ namespace lbgm {
 lb_status ctx_fail(lb_ctx* c, lb_status s, const std::string& msg);
 // False (with *s set) unless c is non-NULL, initialised and not poisoned.
 bool ctx_usable(lb_ctx* c, lb_status* s);
+// Tiled step (LB_OPT_STEP_KERNEL 5): prepare the tiles (outside captures),
+// then launch one step of them.
+lb_status ctx_tiled_prepare(lb_ctx* c);
+lb_status ctx_tiled_launch(lb_ctx* c);
 
 }  // namespace lbgm

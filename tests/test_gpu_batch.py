@@ -153,17 +153,17 @@ def test_context_autotune_steps_are_real_steps():
     a.lb_init(params)
     b.lb_init(params)
     best, trials = a.lb_autotune(steps_per_trial=2)
-    # three block sizes for the plain and the region-split kernels, the TMA
-    # kernel (n3 = 128), six prefetching configurations
-    assert len(trials) == 13
-    assert {t["schedule"] for t in trials} == {1, 2, 3, 4}
-    assert {t["block_threads"] for t in trials if t["schedule"] == 1} == {64, 96, 128}
-    assert {t["block_threads"] for t in trials if t["schedule"] == 4} == {64, 96, 128}
+    # three block sizes for the plain, region-split and tiled kernels, the
+    # TMA kernel (n3 = 128), six prefetching configurations
+    assert len(trials) == 16
+    assert {t["schedule"] for t in trials} == {1, 2, 3, 4, 5}
+    for k in (1, 4, 5):
+        assert {t["block_threads"] for t in trials if t["schedule"] == k} == {64, 96, 128}
     assert {(t["block_threads"], t["nodes_per_thread"]) for t in trials if t["schedule"] == 3} == \
         {(t, n) for t in (128, 256) for n in (2, 4, 8)}
     assert best["ms_per_step"] == min(t["ms_per_step"] for t in trials)
-    assert a.lb_step_count() == 13 * 3
-    b.lb_step(39)
+    assert a.lb_step_count() == 16 * 3
+    b.lb_step(48)
     assert np.array_equal(_state(a), _state(b))
     a.close()
     b.close()

@@ -423,11 +423,38 @@ def test_region_split_kernel_is_bitwise_equal_to_plain_kernel(ch, batch, precisi
     tw.close()
 
 
+@pytest.mark.parametrize("precision", ["fp32", "bf16_shifted"])
+@pytest.mark.parametrize("ch,batch", [
+    (Channel("ellipsoidal", 1.0, 1.1, 12, 3, 40, b=0.9, periodic3=False), 2),
+    (Channel("flat", 0.0, 1.0, 8, 2, 9, periodic3=False), 1),
+    (Channel("cylindrical", 1.0, 1 / 0.9, 9, 3, 13), 3),
+    (Channel("cylindrical", 1.0, 1 / ETA, 9, 2, 16, wall="equilibrium"), 2),
+], ids=["ell4wall", "flat4wall", "cyl_ragged", "cyl_eqwall"])
+def test_tiled_step_is_bitwise_equal_to_plain_kernel(ch, batch, precision):
+    """Interior runs and wall nodes in the two work-list kernels (option 5)
+    give the one-kernel states, with graph replay and odd step counts."""
+    L = lib()
+    params = [dict(tau=0.6 + 0.1 * b, G=2e-4, seed=70 + b, amp=1e-2) for b in range(batch)]
+    outs = []
+    for kern, threads in ((1, 128), (5, 128), (5, 64)):
+        tw = Twin(ch, params, precision)
+        tw.ctx.lb_set_option(L.LB_OPT_STEP_KERNEL, kern)
+        tw.ctx.lb_set_option(L.LB_OPT_BLOCK_THREADS, threads)
+        tw.ctx.lb_set_option(L.LB_OPT_USE_GRAPH, 1)
+        tw.ctx.lb_init(tw.lparams)
+        tw.ctx.lb_step(3)
+        tw.ctx.lb_step(14)
+        outs.append(tw.ctx.lb_get_populations())
+        tw.close()
+    for o in outs[1:]:
+        assert np.array_equal(outs[0], o)
+
+
 def test_prefetching_kernel_option_validation():
     L = lib()
     tw = Twin(CYL1, [dict(tau=0.8)], "fp16_shifted")
     with pytest.raises(L.LBError) as e:
-        tw.ctx.lb_set_option(L.LB_OPT_STEP_KERNEL, 5)
+        tw.ctx.lb_set_option(L.LB_OPT_STEP_KERNEL, 6)
     assert e.value.status == L.LB_ERR_ARG
     for bad in (0, 65):
         with pytest.raises(L.LBError):
