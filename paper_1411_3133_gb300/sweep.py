@@ -271,6 +271,208 @@ def compare_time_to_critical_dean(steps=300_000, sample_every=2000, modes=None):
     return out
 
 
+def critical_dean_knee(deans, w):
+    """De_c of an imperfect bifurcation read off the mean-vorticity curve
+    <omega>(De) (Sec. IV: the double-curved channel carries a secondary flow
+    at every De, and the paper takes the Dean number where the vorticity
+    starts to rise steeply): the De of the largest second derivative
+    d^2<omega>/dDe^2 (three-point formula on the sampled, possibly uneven
+    grid), refined by the vertex of the parabola through that value and its
+    two neighbours. NaN when the largest value sits at either end of the
+    range (no knee inside the sweep, e.g. a curve that is still convex at the
+    last De) or fewer than five finite samples."""
+    d = np.asarray(deans, float)
+    w = np.asarray(w, float)
+    ok = np.isfinite(d) & np.isfinite(w)
+    d, w = d[ok], w[ok]
+    order = np.argsort(d)
+    d, w = d[order], w[order]
+    n = len(d)
+    if n < 5:
+        return float("nan")
+    h1 = d[1:-1] - d[:-2]
+    h2 = d[2:] - d[1:-1]
+    w2 = 2.0 * (h1 * w[2:] - (h1 + h2) * w[1:-1] + h2 * w[:-2]) / (h1 * h2 * (h1 + h2))
+    k = int(np.argmax(w2))
+    if k == 0 or k == len(w2) - 1:
+        return float("nan")
+    x = d[k:k + 3]                      # abscissae of w2[k-1], w2[k], w2[k+1]
+    a, b, _ = np.polyfit(x, w2[k - 1:k + 2], 2)
+    if a >= 0:
+        return float(x[1])
+    return float(np.clip(-b / (2.0 * a), x[0], x[2]))
+
+
+def decay_rate(t, A, floor, skip_frac=0.25, above=100.0):
+    """Slope of ln A over the samples after the first skip_frac of the run that
+    lie above `above` x the round-off floor: the decay rate (negative) of a
+    vortex below threshold. NaN with fewer than three such samples."""
+    t = np.asarray(t, float)
+    A = np.asarray(A, float)
+    start = int(len(t) * skip_frac)
+    t, A = t[start:], A[start:]
+    keep = np.isfinite(A) & (A > above * floor)
+    if keep.sum() < 3:
+        return float("nan")
+    return float(np.polyfit(t[keep], np.log(A[keep]), 1)[0])
+
+
+def critical_dean_decay(deans, sigmas, npoints=4):
+    """De_c from decay rates below threshold: the linear stability rate obeys
+    sigma ~ (De - De_c) near threshold, so a least-squares line through the
+    `npoints` negative rates closest to threshold (largest De) crosses zero
+    at De_c. NaN if fewer than two negative rates."""
+    d = np.asarray(deans, float)
+    s = np.asarray(sigmas, float)
+    ok = np.isfinite(d) & np.isfinite(s) & (s < 0)
+    d, s = d[ok], s[ok]
+    if len(d) < 2:
+        return float("nan")
+    order = np.argsort(d)[::-1][:npoints]
+    slope, icpt = np.polyfit(d[order], s[order], 1)
+    return float(-icpt / slope) if slope > 0 else float("nan")
+
+
+def continuation_sweep(spec: L.ChannelSpec, tau, deans, donor_dean, donor_steps=400_000,
+                       steps=400_000, sample_every=2000, precision="fp32", seed=20241111,
+                       noise_amp=1e-4):
+    """De_c of a sharp (supercritical) Dean bifurcation by continuation: one
+    instance at donor_dean (above threshold) develops the 2-cell vortex from
+    the laminar profile plus noise; its populations then start every instance
+    of a batch at the Dean numbers `deans` (each with its own force). Above
+    threshold the vortex settles at its saturated amplitude (A^2 ~ De - De_c);
+    below it decays exponentially at a rate ~ De_c - De, far above the
+    round-off floor. Returns {"dean", "a_final", "saturated", "sigma",
+    "De_c_saturation", "De_c_decay", "donor_amp", "seconds"}."""
+    import time
+
+    import torch
+
+    desc = spec.desc()
+    t0 = time.perf_counter()
+    donor = L.LBContext(spec, batch=1, precision=precision)
+    donor.lb_set_option(L.LB_OPT_USE_GRAPH, 1)
+    donor.lb_set_option(L.LB_OPT_CHECK_EVERY, 0)
+    donor.lb_init([L.make_params(tau, L.lb_force_for_dean(spec.metric, desc, tau, donor_dean), False,
+                                 seed, noise_amp, True)])
+    donor.lb_step(donor_steps)
+    donor_amp = donor.lb_diagnostics()[0]["vortex_amp_x3"]
+    f = donor.lb_get_populations()
+    donor.close()
+    params = [L.make_params(tau, L.lb_force_for_dean(spec.metric, desc, tau, de), False, seed + 1 + i,
+                            0.0, True) for i, de in enumerate(deans)]
+    ctx = L.LBContext(spec, batch=len(deans), precision=precision)
+    ctx.lb_set_option(L.LB_OPT_USE_GRAPH, 1)
+    ctx.lb_set_option(L.LB_OPT_CHECK_EVERY, 0)
+    ctx.lb_init(params)
+    ctx.lb_set_populations(np.ascontiguousarray(np.repeat(f, len(deans), axis=0)))
+    ts, amps, des = [], [], []
+    done = 0
+    while done < steps:
+        n = min(sample_every, steps - done)
+        ctx.lb_step(n)
+        done += n
+        dg = ctx.lb_diagnostics()
+        ts.append(done)
+        amps.append([x["vortex_amp_x3"] for x in dg])
+        des.append([x["dean"] for x in dg])
+    torch.cuda.synchronize()
+    ctx.close()
+    A = np.array(amps)
+    S = len(A)
+    de = np.array(des)[-max(2, S // 4):].mean(axis=0)      # the developed flow's Dean number
+    a_fin = A[-max(2, S // 8):].mean(axis=0)
+    floor = 1e-9 if precision != "fp64" else 1e-14
+    sat = np.array([is_saturated(A[:, i], floor) for i in range(A.shape[1])])
+    sig = np.array([decay_rate(ts, A[:, i], floor) if not sat[i] else float("nan")
+                    for i in range(A.shape[1])])
+    return {"dean": de.tolist(), "a_final": a_fin.tolist(), "saturated": sat.tolist(),
+            "sigma": sig.tolist(), "donor_amp": donor_amp,
+            "De_c_saturation": critical_dean_saturation(de, a_fin, floor, saturated=sat),
+            "De_c_decay": critical_dean_decay(de, sig),
+            "seconds": time.perf_counter() - t0}
+
+
+def double_curved_study(cases, deans=None, steps=300_000, sample_every=2000, tau=1.0, eta=0.9,
+                        nr=65, ntheta=4, n3=128, noise_amp=1e-4, seed=20241111, precision="fp32",
+                        wall="equilibrium", max_speed=0.4):
+    """The double-curved channel of Sec. IV: walls at r_i and r_o = r_i / eta
+    (the paper's Dirichlet walls by default), periodic in phi over n3 nodes,
+    tau = 1, for each case (label, r_i, b): streamwise curvature radius
+    R_theta = r_i b^2, cross-sectional radius R_phi = r_i. One context per
+    case holds the Dean numbers (force from the cylinder of radius R_theta
+    and the same width and N_r, which drops targets whose laminar mean speed
+    would exceed max_speed lattice units); one lb_batch steps all cases.
+    Per case: measured De, final mean vorticity <omega^theta> and vortex
+    amplitude, and De_c read off the vorticity curve (critical_dean_knee)."""
+    import time
+
+    import torch
+
+    deans = list(np.linspace(14.0, 44.0, 16)) if deans is None else list(deans)
+    cs2 = 1.0 - np.sqrt(0.4)
+    nu = (tau - 0.5) * cs2
+    stream = torch.cuda.Stream()
+    ctxs, kept = [], []
+    for k, (label, ri, b) in enumerate(cases):
+        ro = ri / eta
+        spec = L.ChannelSpec("ellipsoidal", ri, ro, nr, ntheta, n3, b=b, periodic3=True, wall=wall)
+        R = ri * b * b
+        d = ro - ri
+        des_k = [de for de in deans if de * nu / ((nr - 1) * np.sqrt(d / R)) <= max_speed]
+        ref = L.make_desc(R, R + d, nr, ntheta, n3, wall=wall)  # cylinder of the same R_theta
+        params = [L.make_params(tau, L.lb_force_for_dean("cylindrical", ref, tau, de), False,
+                                seed + 100 * k + i, noise_amp, False) for i, de in enumerate(des_k)]
+        ctx = L.LBContext(spec, batch=len(des_k), precision=precision, stream=stream)
+        ctx.lb_init(params)
+        ctxs.append(ctx)
+        kept.append(des_k)
+    batch = L.LBBatch(ctxs)
+    batch.lb_batch_set_option(L.LB_OPT_USE_GRAPH, 1)
+    amps = [[] for _ in cases]
+    vort = [[] for _ in cases]
+    des = [[] for _ in cases]
+    t0 = time.perf_counter()
+    for _ in range(steps // sample_every):
+        batch.lb_batch_step(sample_every)
+        for k, ctx in enumerate(ctxs):
+            dg = ctx.lb_diagnostics()
+            amps[k].append([x["vortex_amp_x3"] for x in dg])
+            vort[k].append([x["mean_vorticity"] for x in dg])
+            des[k].append([x["dean"] for x in dg])
+    torch.cuda.synchronize()
+    sec = time.perf_counter() - t0
+    out = {"seconds": sec, "steps": steps, "nodes": batch.lb_batch_nodes(), "cases": []}
+    for k, (label, ri, b) in enumerate(cases):
+        A = np.array(amps[k])
+        W = np.array(vort[k])
+        S = len(A)
+        de = np.array(des[k])[: max(2, S // 4)].mean(axis=0)
+        w_fin = W[-max(2, S // 8):].mean(axis=0)
+        # still moving at the end of the run: last tenth vs the one before
+        k10 = max(2, S // 10)
+        drift = np.abs(W[-1] / W[-k10] - 1.0)
+        out["cases"].append({"label": label, "r_i": ri, "b": b, "R_theta": ri * b * b, "R_phi": ri,
+                             "dean_target": kept[k], "dean": de.tolist(),
+                             "vorticity": w_fin.tolist(), "a_final": A[-max(2, S // 8):].mean(axis=0).tolist(),
+                             "drift": drift.tolist(),
+                             "De_c": critical_dean_knee(de, w_fin)})
+    batch.close()
+    for c in ctxs:
+        c.close()
+    return out
+
+
+def streamwise_curvature_cases(bs=(0.8, 0.85, 0.9, 0.95, 1.0, 1.05, 1.1, 1.2)):
+    """Sec. IV.A: r_i = R_phi = 1 fixed, R_theta = b^2 varied."""
+    return [("b=%g" % b, 1.0, b) for b in bs]
+
+
+def cross_section_curvature_cases(ris=(0.8, 0.9, 1.0, 1.1, 1.2, 1.4, 1.6, 1.8)):
+    """Sec. IV.B: R_theta = r_i b^2 = 1 fixed, R_phi = r_i varied."""
+    return [("r_i=%g" % ri, ri, 1.0 / np.sqrt(ri)) for ri in ris]
+
+
 if __name__ == "__main__":
     import argparse
     import json
@@ -280,8 +482,34 @@ if __name__ == "__main__":
     ap.add_argument("--sample-every", type=int, default=2000)
     ap.add_argument("--modes", default="fp64_sequential,fp64,fp32,fp16_shifted,bf16_shifted")
     ap.add_argument("--out", default=None)
+    ap.add_argument("--double-curved", action="store_true",
+                    help="the Sec. IV studies instead: R_theta = b^2 (r_i = 1) and R_phi = r_i (R_theta = 1)")
+    ap.add_argument("--continuation", default=None, metavar="ETA",
+                    help="De_c of the cylinder of aspect ratio ETA (128 x 1 x 256, tau 0.9, Sec. III) "
+                         "by continuation from a developed vortex")
     a = ap.parse_args()
     L.load_library()
+    if a.double_curved:
+        r = double_curved_study(streamwise_curvature_cases() + cross_section_curvature_cases(),
+                                steps=a.steps, sample_every=a.sample_every)
+        for c in r["cases"]:
+            print("%-10s R_theta %.3f R_phi %.2f De_c %.2f  max drift %.3f" %
+                  (c["label"], c["R_theta"], c["R_phi"], c["De_c"], max(c["drift"])))
+        print("seconds %.1f  nodes %d" % (r["seconds"], r["nodes"]))
+        if a.out:
+            with open(a.out, "w") as f:
+                json.dump(r, f)
+        raise SystemExit(0)
+    if a.continuation:
+        eta = float(a.continuation)
+        spec = L.ChannelSpec("cylindrical", 1.0, 1.0 / eta, 129, 1, 256, wall="equilibrium")
+        r = continuation_sweep(spec, 0.9, list(np.linspace(38.0, 53.0, 16)), donor_dean=54.0,
+                               donor_steps=a.steps, steps=a.steps, sample_every=a.sample_every)
+        print(json.dumps({k: v for k, v in r.items()}, indent=1))
+        if a.out:
+            with open(a.out, "w") as f:
+                json.dump(r, f)
+        raise SystemExit(0)
     r = compare_time_to_critical_dean(a.steps, a.sample_every, a.modes.split(","))
     text = json.dumps(r)
     print(json.dumps({m: {k: v for k, v in x.items() if k not in ("amp", "times")} for m, x in r.items()},

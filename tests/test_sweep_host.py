@@ -86,3 +86,58 @@ def test_mixed_batch_recipe_is_seeded_and_in_range():
     assert 7.0e6 < total < 9.5e6                           # about 7.9 M nodes expected
     ratios = np.log([i.R2_over_R1 for i in a if i.metric == "ellipsoidal"])
     assert ratios.min() < np.log(0.5) and ratios.max() > np.log(2.0)   # spans the range
+
+
+def test_knee_of_imperfect_bifurcation_curve():
+    """A base flow ~ De^2 plus a smooth onset (softplus) at De_c: the largest
+    curvature of <omega>(De) sits at De_c; a pure power law has no knee."""
+    from paper_1411_3133_gb300.sweep import critical_dean_knee
+    for dec, s in ((30.0, 1.5), (24.3, 1.0), (35.7, 2.0)):
+        de = np.linspace(14.0, 44.0, 16)
+        w = 1e-7 * de ** 2 + 1e-4 * s * np.log1p(np.exp((de - dec) / s))
+        got = critical_dean_knee(de, w)
+        assert abs(got - dec) < 0.35 * (de[1] - de[0]), (dec, got)
+        # uneven, unsorted samples
+        rng = np.random.default_rng(3)
+        de2 = np.sort(14.0 + 30.0 * rng.random(24))
+        w2 = 1e-7 * de2 ** 2 + 1e-4 * s * np.log1p(np.exp((de2 - dec) / s))
+        perm = rng.permutation(24)
+        assert abs(critical_dean_knee(de2[perm], w2[perm]) - dec) < 1.0
+    de = np.linspace(14.0, 44.0, 16)
+    assert np.isnan(critical_dean_knee(de, 1e-7 * de ** 3))
+    assert np.isnan(critical_dean_knee(de[:4], de[:4]))
+    # NaN samples (diverged instances) are dropped
+    w = 1e-7 * de ** 2 + 1e-4 * np.log1p(np.exp(de - 30.0))
+    w[-2:] = np.nan
+    assert abs(critical_dean_knee(de, w) - 30.0) < 0.7
+
+
+def test_decay_rate_and_its_zero_crossing():
+    from paper_1411_3133_gb300.sweep import critical_dean_decay, decay_rate
+    t = np.arange(2000, 400001, 2000, dtype=float)
+    dec, slope = 47.3, 4e-7
+    de = np.array([40.0, 42.0, 44.0, 46.0, 48.0, 50.0])
+    sig_true = slope * (de - dec)
+    sig = []
+    for s in sig_true:
+        # mean-flow transient early on, then the slow mode; a floor at 1e-9
+        A = np.maximum(3e-3 * np.exp(s * t) + 1e-3 * np.exp(-1e-4 * t), 1e-9)
+        sig.append(decay_rate(t, A, 1e-9) if s < 0 else float("nan"))
+    sig = np.array(sig)
+    assert np.allclose(sig[:4], sig_true[:4], rtol=0.02)
+    assert critical_dean_decay(de, sig) == pytest.approx(dec, abs=0.05)
+    # a fast decay that hits the floor early keeps only the samples above it
+    A = np.maximum(1e-3 * np.exp(-5e-5 * t), 1e-9)
+    assert decay_rate(t, A, 1e-9) == pytest.approx(-5e-5, rel=1e-6)
+    assert np.isnan(decay_rate(t, np.full_like(t, 1e-9), 1e-9))
+    assert np.isnan(critical_dean_decay(de, [np.nan, -1e-6, np.nan, 1e-6, 1e-6, 1e-6]))
+
+
+def test_double_curved_case_lists_follow_the_paper():
+    """Sec. IV.A varies R_theta = r_i b^2 at r_i = 1; Sec. IV.B varies
+    R_phi = r_i at R_theta = 1."""
+    from paper_1411_3133_gb300.sweep import cross_section_curvature_cases, streamwise_curvature_cases
+    for label, ri, b in streamwise_curvature_cases():
+        assert ri == 1.0 and 0.6 <= b * b * ri <= 1.5
+    for label, ri, b in cross_section_curvature_cases():
+        assert ri * b * b == pytest.approx(1.0)
