@@ -42,26 +42,42 @@ KERNEL_SOURCES = ["paper_1411_3133_gb300/csrc/lbm_device.cuh", "paper_1411_3133_
 METRIC = "MLUPS and % of HBM roofline at 1 GB300"
 
 
-def kernel_source_hash() -> str:
+FP64_PROFILE_FILE = os.path.join(ROOT, "profiles", "k_step_fp64_cyl64x4x256_b24.md")
+FP64_KERNEL_SOURCES = KERNEL_SOURCES[:3] + ["paper_1411_3133_gb300/csrc/step_f64.cu",
+                                            "paper_1411_3133_gb300/csrc/lattice.cuh"]
+
+
+def kernel_source_hash(sources=None) -> str:
     h = hashlib.sha256()
-    for p in KERNEL_SOURCES:
+    for p in (KERNEL_SOURCES if sources is None else sources):
         with open(os.path.join(ROOT, p), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
 
 
-def measured_traffic():
-    """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel source; else None."""
+def profile_value(path, key, sources=None):
+    """A figure from a committed ncu summary, if the summary was taken on the
+    current kernel source; else None."""
     try:
-        text = open(PROFILE_FILE).read()
+        text = open(path).read()
     except OSError:
         return None
     m_hash = re.search(r"kernel_source_sha:\s*([0-9a-f]+)", text)
-    m_tr = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
-    if not m_hash or not m_tr or m_hash.group(1) != kernel_source_hash():
+    m_val = re.search(key + r":\s*([0-9.eE+]+)", text)
+    if not m_hash or not m_val or m_hash.group(1) != kernel_source_hash(sources):
         return None
-    return float(m_tr.group(1))
+    return float(m_val.group(1))
+
+
+def measured_traffic():
+    """DRAM bytes per launch of the FP32 split step (committed ncu summary)."""
+    return profile_value(PROFILE_FILE, "dram_bytes_per_launch")
+
+
+def measured_fp64_flops():
+    """FP64 flops per lattice update executed by k_step<double> (ncu DFMA,
+    DADD and DMUL thread-instruction counts, committed summary)."""
+    return profile_value(FP64_PROFILE_FILE, "fp64_flops_per_update", FP64_KERNEL_SOURCES)
 
 
 def peaks():
@@ -476,6 +492,23 @@ def main():
     achieved = bpu * cells / per_launch / 1e9
     peak, peak_kind = peaks()
     traffic = measured_traffic() if runner.profiled else None
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+                "unit": "GB/s", "frac": round(achieved / peak, 4),
+                "traffic": traffic, "peak_source": peak_kind,
+                "kernel": runner.kernel, "algorithmic_bytes_per_launch": bpu * cells}
+    fpu = measured_fp64_flops() if (args.precision == "fp64" and args.step_kernel == "plain"
+                                    and args.workload == "sweep") else None
+    if fpu is not None:
+        # the FP64 step is bound by the FP64 units: report it against the
+        # FMA peak measured on this GPU, outside the timed region
+        alu_peak = L.lb_fma_peak("fp64", stream) / 1e12
+        alu = fpu * cells / per_launch / 1e12
+        roofline = {"bound": "alu", "achieved": round(alu, 4), "peak": round(alu_peak, 4),
+                    "unit": "TFLOP/s", "frac": round(alu / alu_peak, 4), "traffic": None,
+                    "peak_source": "measured (lb_fma_peak, FP64 FMA chains on this GPU)",
+                    "kernel": runner.kernel, "fp64_flops_per_update": fpu,
+                    "hbm": {"achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                            "frac": round(achieved / peak, 4), "peak_source": peak_kind}}
 
     # end to end through the C ABI with host buffers: each step uploads the
     # state from pinned host memory, advances it one step and reads it back
@@ -500,10 +533,7 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": DTYPE[args.precision], "data": "synthetic",
             "config": dict(runner.config(), bytes_per_update=bpu, parallelism=f"replicas x{world}"),
-            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
-                         "unit": "GB/s", "frac": round(achieved / peak, 4),
-                         "traffic": traffic, "peak_source": peak_kind,
-                         "kernel": runner.kernel, "algorithmic_bytes_per_launch": bpu * cells},
+            "roofline": roofline,
             "e2e": {"value": round(e2e_value, 2), "unit": "MLUPS", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "steps": args.e2e_steps},
             "gpu_launches": args.steps * runner.launches_per_step,

@@ -349,6 +349,19 @@ lb_status lb_diagnostics_noalloc(lb_metric metric, const lb_geometry_desc* geom,
                                  const double* tau, const double* rho, const double* u,
                                  void* cuda_stream, lb_diag* out);
 
+/* Measured fused multiply-add peak of the current CUDA device, in flop/s
+ * (2 flops per FMA): the ALU roof against which the FP64 step, bound by the
+ * FP64 units rather than by HBM, is reported. Not part of the paper's
+ * method; a measurement aid.
+ *   precision    LB_FP64 or LB_FP32 (others: LB_ERR_ARG)
+ *   cuda_stream  cudaStream_t to run on (NULL: the legacy default stream)
+ *   flops_per_s  host output; best of three timed launches of a kernel in
+ *                which every thread runs eight independent FMA chains
+ *                (eight 256-thread blocks per SM), each lasting >= 20 ms
+ * Allocates and frees a few bytes of device memory; synchronises
+ * cuda_stream. Errors are reported through lb_last_error(NULL). */
+lb_status lb_fma_peak(lb_precision precision, void* cuda_stream, double* flops_per_s);
+
 /* Autotuner of the step launch. Runs steps_per_trial (>= 1) time steps in
  * each configuration -- block_threads in {64, 96, 128} (FP64: {64, 128, 192,
  * 256}) with the plain step kernel, {64, 96, 128} with the region split

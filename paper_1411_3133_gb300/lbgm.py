@@ -100,6 +100,7 @@ SIGNATURES = {
     "lb_diagnostics_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(lb_geometry_desc),
                                               ctypes.c_int, _D, _P, _P, _P,
                                               ctypes.POINTER(lb_diag)]),
+    "lb_fma_peak": (ctypes.c_int, [ctypes.c_int, _P, _D]),
     "lb_autotune": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(lb_tune), ctypes.POINTER(lb_tune),
                                    ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     "lb_destroy": (None, [_P]),
@@ -261,6 +262,14 @@ def lb_diagnostics_noalloc(metric: str, desc: lb_geometry_desc, taus, rho, u, st
                                                  taus.ctypes.data_as(_D), _ptr(rho), _ptr(u),
                                                  handle, out))
     return [d.as_dict() for d in out]
+
+
+def lb_fma_peak(precision: str = "fp64", stream=None) -> float:
+    """Measured FMA peak of the current device in flop/s (see include/lbgm.h)."""
+    out = ctypes.c_double()
+    handle = None if stream is None else ctypes.c_void_p(stream.cuda_stream)
+    _check(load_library().lb_fma_peak(PRECISIONS[precision], handle, ctypes.byref(out)))
+    return out.value
 
 
 # ---------------------------------------------------------------------------

@@ -177,3 +177,12 @@ def test_mlp_create_rejects_bad_arguments_without_a_gpu(L):
     assert b"width" in lib.lb_mlp_last_error(None)
     assert lib.lb_mlp_param_count(None) == 0
     lib.lb_mlp_destroy(None)
+
+
+def test_fma_peak_rejects_bad_arguments_without_a_gpu(L):
+    lib = L.load_library()
+    v = ctypes.c_double(-1.0)
+    assert lib.lb_fma_peak(L.PRECISIONS["fp16_shifted"], None, ctypes.byref(v)) == L.LB_ERR_ARG
+    assert b"precision" in lib.lb_last_error(None)
+    assert lib.lb_fma_peak(L.PRECISIONS["fp64"], None, None) == L.LB_ERR_ARG
+    assert v.value == -1.0                        # untouched on failure
