@@ -355,9 +355,10 @@ lb_status lb_diagnostics_noalloc(lb_metric metric, const lb_geometry_desc* geom,
  * method; a measurement aid.
  *   precision    LB_FP64 or LB_FP32 (others: LB_ERR_ARG)
  *   cuda_stream  cudaStream_t to run on (NULL: the legacy default stream)
- *   flops_per_s  host output; best of three timed launches of a kernel in
+ *   flops_per_s  host output; best of five timed launches of a kernel in
  *                which every thread runs eight independent FMA chains
- *                (eight 256-thread blocks per SM), each lasting >= 20 ms
+ *                (eight 256-thread blocks per SM), each lasting >= 50 ms
+ *                after a warm-up launch
  * Allocates and frees a few bytes of device memory; synchronises
  * cuda_stream. Errors are reported through lb_last_error(NULL). */
 lb_status lb_fma_peak(lb_precision precision, void* cuda_stream, double* flops_per_s);

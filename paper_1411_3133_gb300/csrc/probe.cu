@@ -4,7 +4,7 @@
 //
 // Every thread runs eight independent fused multiply-add chains
 // a <- a * m + c (m slightly below 1, so the chains converge instead of
-// overflowing) for `iters` rounds; 2 flops per FMA. The grid holds eight
+// overflowing), four rounds per loop trip; 2 flops per FMA. The grid holds eight
 // 256-thread blocks per SM, enough warps to hide the FMA latency. The
 // result is stored only when it equals an impossible value, which keeps the
 // chains alive without a memory stream.
@@ -25,13 +25,16 @@ __device__ inline float fma_t(float a, float b, float c) { return fmaf(a, b, c);
 __device__ inline double fma_t(double a, double b, double c) { return fma(a, b, c); }
 
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_fma_probe(long long iters, T m, T c, T* sink) {
+__global__ void __launch_bounds__(kThreads) k_fma_probe(int iters, T m, T c, T* sink) {
   T a[kChains];
 #pragma unroll
   for (int k = 0; k < kChains; ++k) a[k] = T(threadIdx.x + k);
-  for (long long i = 0; i < iters; ++i) {
+  for (int i = 0; i < iters; ++i) {  // 4 x kChains FMAs per loop trip
 #pragma unroll
-    for (int k = 0; k < kChains; ++k) a[k] = fma_t(a[k], m, c);
+    for (int u = 0; u < 4; ++u) {
+#pragma unroll
+      for (int k = 0; k < kChains; ++k) a[k] = fma_t(a[k], m, c);
+    }
   }
   T s = 0;
 #pragma unroll
@@ -60,10 +63,14 @@ lb_status run_probe(cudaStream_t st, double* flops_per_s) {
   const T m = T(0.999999), c = T(1e-6);
   double best = 0.0;
   lb_status status = LB_OK;
-  k_fma_probe<T><<<blocks, kThreads, 0, st>>>(1024, m, c, sink);  // warm-up
-  long long iters = 1 << 12;
+  // warm-up; the lengthening runs below warm up further
+  cudaEventRecord(e0, st);
+  k_fma_probe<T><<<blocks, kThreads, 0, st>>>(256, m, c, sink);
+  cudaEventRecord(e1, st);
+  cudaEventSynchronize(e1);
+  int iters = 1 << 10;
   int timed = 0;
-  while (timed < 3) {
+  while (timed < 5) {
     cudaEventRecord(e0, st);
     k_fma_probe<T><<<blocks, kThreads, 0, st>>>(iters, m, c, sink);
     cudaEventRecord(e1, st);
@@ -73,11 +80,11 @@ lb_status run_probe(cudaStream_t st, double* flops_per_s) {
     }
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
-    if (ms < 20.f && iters < (1ll << 26)) {  // too short to time: lengthen
+    if (ms < 50.f && iters < (1 << 24)) {  // too short to time: lengthen
       iters *= 2;
       continue;
     }
-    const double f = 2.0 * kChains * double(iters) * threads / (ms * 1e-3);
+    const double f = 2.0 * 4 * kChains * double(iters) * threads / (ms * 1e-3);
     if (f > best) best = f;
     ++timed;
   }
