@@ -74,6 +74,13 @@ def measured_traffic():
     return profile_value(PROFILE_FILE, "dram_bytes_per_launch")
 
 
+def measured_fp32_flops():
+    """FP32 flops per lattice update of the region-split FP32 step, both
+    kernels (ncu FFMA, FADD, FMUL thread-instruction counts, committed
+    summary)."""
+    return profile_value(PROFILE_FILE, "fp32_flops_per_update")
+
+
 def measured_fp64_flops():
     """FP64 flops per lattice update executed by k_step<double> (ncu DFMA,
     DADD and DMUL thread-instruction counts, committed summary)."""
@@ -496,6 +503,15 @@ def main():
                 "unit": "GB/s", "frac": round(achieved / peak, 4),
                 "traffic": traffic, "peak_source": peak_kind,
                 "kernel": runner.kernel, "algorithmic_bytes_per_launch": bpu * cells}
+    fpu32 = measured_fp32_flops() if runner.profiled else None
+    if fpu32 is not None:
+        # the other roof: FP32 arithmetic against the FMA peak measured on
+        # this GPU (outside the timed region); the HBM roof is the binding one
+        alu_peak = L.lb_fma_peak("fp32", stream) / 1e12
+        alu = fpu32 * cells / per_launch / 1e12
+        roofline["alu"] = {"achieved": round(alu, 3), "peak": round(alu_peak, 3), "unit": "TFLOP/s",
+                           "frac": round(alu / alu_peak, 4), "fp32_flops_per_update": fpu32,
+                           "peak_source": "measured (lb_fma_peak, FP32 FMA chains on this GPU)"}
     fpu = measured_fp64_flops() if (args.precision == "fp64" and args.step_kernel == "plain"
                                     and args.workload == "sweep") else None
     if fpu is not None:

@@ -333,39 +333,48 @@ def critical_dean_decay(deans, sigmas, npoints=4):
     return float(-icpt / slope) if slope > 0 else float("nan")
 
 
-def continuation_sweep(spec: L.ChannelSpec, tau, deans, donor_dean, donor_steps=400_000,
-                       steps=400_000, sample_every=2000, precision="fp32", seed=20241111,
-                       noise_amp=1e-4):
-    """De_c of a sharp (supercritical) Dean bifurcation by continuation: one
-    instance at donor_dean (above threshold) develops the 2-cell vortex from
-    the laminar profile plus noise; its populations then start every instance
-    of a batch at the Dean numbers `deans` (each with its own force). Above
-    threshold the vortex settles at its saturated amplitude (A^2 ~ De - De_c);
-    below it decays exponentially at a rate ~ De_c - De, far above the
-    round-off floor. Returns {"dean", "a_final", "saturated", "sigma",
-    "De_c_saturation", "De_c_decay", "donor_amp", "seconds"}."""
+def develop_donor(spec: L.ChannelSpec, tau, donor_dean, donor_steps=400_000, precision="fp32",
+                  seed=20241111, noise_amp=1e-4):
+    """One instance at donor_dean (above threshold), started from the laminar
+    profile plus seeded noise and run donor_steps: returns its populations
+    (host FP64, shape (1, Q, N)) and its vortex amplitude."""
+    desc = spec.desc()
+    donor = L.LBContext(spec, batch=1, precision=precision)
+    try:
+        donor.lb_set_option(L.LB_OPT_USE_GRAPH, 1)
+        donor.lb_set_option(L.LB_OPT_CHECK_EVERY, 0)
+        donor.lb_init([L.make_params(tau, L.lb_force_for_dean(spec.metric, desc, tau, donor_dean), False,
+                                     seed, noise_amp, True)])
+        donor.lb_step(donor_steps)
+        amp = donor.lb_diagnostics()[0]["vortex_amp_x3"]
+        return donor.lb_get_populations(), amp
+    finally:
+        donor.close()
+
+
+def continue_from(spec: L.ChannelSpec, tau, deans, f_donor, steps=400_000, sample_every=2000,
+                  precision="fp32"):
+    """Every instance of a batch (one per Dean number, each with its own
+    force and, for 2-byte storage, its own laminar reference table) starts
+    from the donor populations and runs `steps`. Above threshold the vortex
+    settles at its saturated amplitude (A^2 ~ De - De_c); below it decays
+    exponentially at a rate ~ De_c - De, far above the round-off floor.
+    Returns {"dean", "a_final", "saturated", "sigma", "De_c_saturation",
+    "De_c_decay", "De_c_bracket", "seconds"}."""
     import time
 
     import torch
 
     desc = spec.desc()
-    t0 = time.perf_counter()
-    donor = L.LBContext(spec, batch=1, precision=precision)
-    donor.lb_set_option(L.LB_OPT_USE_GRAPH, 1)
-    donor.lb_set_option(L.LB_OPT_CHECK_EVERY, 0)
-    donor.lb_init([L.make_params(tau, L.lb_force_for_dean(spec.metric, desc, tau, donor_dean), False,
-                                 seed, noise_amp, True)])
-    donor.lb_step(donor_steps)
-    donor_amp = donor.lb_diagnostics()[0]["vortex_amp_x3"]
-    f = donor.lb_get_populations()
-    donor.close()
-    params = [L.make_params(tau, L.lb_force_for_dean(spec.metric, desc, tau, de), False, seed + 1 + i,
-                            0.0, True) for i, de in enumerate(deans)]
+    params = [L.make_params(tau, L.lb_force_for_dean(spec.metric, desc, tau, de), False, 0, 0.0, True)
+              for de in deans]
     ctx = L.LBContext(spec, batch=len(deans), precision=precision)
     ctx.lb_set_option(L.LB_OPT_USE_GRAPH, 1)
     ctx.lb_set_option(L.LB_OPT_CHECK_EVERY, 0)
     ctx.lb_init(params)
-    ctx.lb_set_populations(np.ascontiguousarray(np.repeat(f, len(deans), axis=0)))
+    ctx.lb_set_populations(np.ascontiguousarray(np.repeat(f_donor, len(deans), axis=0)))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
     ts, amps, des = [], [], []
     done = 0
     while done < steps:
@@ -377,6 +386,7 @@ def continuation_sweep(spec: L.ChannelSpec, tau, deans, donor_dean, donor_steps=
         amps.append([x["vortex_amp_x3"] for x in dg])
         des.append([x["dean"] for x in dg])
     torch.cuda.synchronize()
+    sec = time.perf_counter() - t0
     ctx.close()
     A = np.array(amps)
     S = len(A)
@@ -387,10 +397,62 @@ def continuation_sweep(spec: L.ChannelSpec, tau, deans, donor_dean, donor_steps=
     sig = np.array([decay_rate(ts, A[:, i], floor) if not sat[i] else float("nan")
                     for i in range(A.shape[1])])
     return {"dean": de.tolist(), "a_final": a_fin.tolist(), "saturated": sat.tolist(),
-            "sigma": sig.tolist(), "donor_amp": donor_amp,
+            "sigma": sig.tolist(), "times": ts, "amp": A.tolist(),
             "De_c_saturation": critical_dean_saturation(de, a_fin, floor, saturated=sat),
             "De_c_decay": critical_dean_decay(de, sig),
-            "seconds": time.perf_counter() - t0}
+            "De_c_bracket": dean_bracket(de, sat),
+            "seconds": sec}
+
+
+def dean_bracket(deans, saturated):
+    """(largest De that did not saturate below the first saturated one, first
+    saturated De): the interval holding De_c; NaN ends when missing."""
+    d = np.asarray(deans, float)
+    s = np.asarray(saturated, bool)
+    order = np.argsort(d)
+    d, s = d[order], s[order]
+    if not s.any():
+        return [float(d[-1]) if len(d) else float("nan"), float("nan")]
+    k = int(np.argmax(s))
+    return [float(d[k - 1]) if k > 0 else float("nan"), float(d[k])]
+
+
+def continuation_sweep(spec: L.ChannelSpec, tau, deans, donor_dean, donor_steps=400_000,
+                       steps=400_000, sample_every=2000, precision="fp32", seed=20241111,
+                       noise_amp=1e-4):
+    """De_c of a sharp (supercritical) Dean bifurcation by continuation from
+    a developed 2-cell vortex (develop_donor, then continue_from). Adds
+    "donor_amp" and the total "seconds" of both phases to continue_from's
+    result."""
+    import time
+    t0 = time.perf_counter()
+    f, amp = develop_donor(spec, tau, donor_dean, donor_steps, precision, seed, noise_amp)
+    r = continue_from(spec, tau, deans, f, steps, sample_every, precision)
+    r["donor_amp"] = amp
+    r["seconds"] = time.perf_counter() - t0
+    return r
+
+
+def compare_precisions_continuation(modes=("fp64", "fp32", "fp16_shifted", "bf16_shifted"), tau=0.6,
+                                    deans=None, donor_dean=44.0, donor_steps=300_000, steps=500_000,
+                                    sample_every=2000):
+    """The 64 x 4 x 256 narrow-gap sweep (eta = 0.975) by continuation, one
+    batched run per storage precision from the same FP32 donor: De_c per
+    precision, its deviation from the FP64 run, and each run's wall time."""
+    spec = L.ChannelSpec("cylindrical", 1.0, 1 / 0.975, 64, 4, 256)
+    deans = list(np.linspace(35.0, 41.0, 10)) if deans is None else list(deans)
+    f, amp = develop_donor(spec, tau, donor_dean, donor_steps, "fp32")
+    out = {"donor_amp": amp, "tau": tau, "steps": steps}
+    for m in modes:
+        r = continue_from(spec, tau, deans, f, steps, sample_every, m)
+        out[m] = {k: v for k, v in r.items() if k not in ("amp", "times")}
+    if "fp64" in out:
+        ref = out["fp64"]
+        for m in modes:
+            for k in ("De_c_saturation", "De_c_decay"):
+                out[m][k + "_rel_err"] = out[m][k] / ref[k] - 1.0 if np.isfinite(ref[k]) else float("nan")
+            out[m]["speedup_vs_fp64"] = ref["seconds"] / out[m]["seconds"]
+    return out
 
 
 def double_curved_study(cases, deans=None, steps=300_000, sample_every=2000, tau=1.0, eta=0.9,
@@ -487,8 +549,17 @@ if __name__ == "__main__":
     ap.add_argument("--continuation", default=None, metavar="ETA",
                     help="De_c of the cylinder of aspect ratio ETA (128 x 1 x 256, tau 0.9, Sec. III) "
                          "by continuation from a developed vortex")
+    ap.add_argument("--precisions", action="store_true",
+                    help="De_c of the 64 x 4 x 256 narrow-gap sweep by continuation in every storage precision")
     a = ap.parse_args()
     L.load_library()
+    if a.precisions:
+        r = compare_precisions_continuation(steps=a.steps, sample_every=a.sample_every)
+        print(json.dumps(r, indent=1))
+        if a.out:
+            with open(a.out, "w") as f:
+                json.dump(r, f)
+        raise SystemExit(0)
     if a.double_curved:
         r = double_curved_study(streamwise_curvature_cases() + cross_section_curvature_cases(),
                                 steps=a.steps, sample_every=a.sample_every)
@@ -505,7 +576,7 @@ if __name__ == "__main__":
         spec = L.ChannelSpec("cylindrical", 1.0, 1.0 / eta, 129, 1, 256, wall="equilibrium")
         r = continuation_sweep(spec, 0.9, list(np.linspace(38.0, 53.0, 16)), donor_dean=54.0,
                                donor_steps=a.steps, steps=a.steps, sample_every=a.sample_every)
-        print(json.dumps({k: v for k, v in r.items()}, indent=1))
+        print(json.dumps({k: v for k, v in r.items() if k not in ("amp", "times")}, indent=1))
         if a.out:
             with open(a.out, "w") as f:
                 json.dump(r, f)

@@ -141,3 +141,12 @@ def test_double_curved_case_lists_follow_the_paper():
         assert ri == 1.0 and 0.6 <= b * b * ri <= 1.5
     for label, ri, b in cross_section_curvature_cases():
         assert ri * b * b == pytest.approx(1.0)
+
+
+def test_dean_bracket_between_last_decaying_and_first_saturated():
+    from paper_1411_3133_gb300.sweep import dean_bracket
+    assert dean_bracket([43.0, 40.0, 42.0, 41.0], [True, False, True, False]) == [41.0, 42.0]
+    lo, hi = dean_bracket([40.0, 41.0], [False, False])
+    assert lo == 41.0 and np.isnan(hi)
+    lo, hi = dean_bracket([40.0, 41.0], [True, True])
+    assert np.isnan(lo) and hi == 40.0
