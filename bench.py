@@ -360,15 +360,17 @@ class EllipsoidRunner(SweepRunner):
 class MixedRunner:
     """128 channels of mixed metric and size (cylinders and double-curved
     channels, N_r in {32, 48, 64}, N_3 in 128..512, De in 20..150) in one
-    lb_batch: one k_step_list launch per metric kind per step, autotuned."""
+    lb_batch: per metric kind and step, one k_step_list launch over the
+    interior tiles and one over the wall-node tiles; autotuned."""
     profiled = False
-    launches_per_step = 2
 
     def __init__(self, args, L, rank):
         from paper_1411_3133_gb300.sweep import mixed_contexts
         from paper_1411_3133_gb300.workloads import mixed_batch
         self.args, self.L = args, L
         self.insts = mixed_batch(seed=rank_seed(20241111, rank))
+        # every channel has interior and wall nodes: two launches per metric kind
+        self.launches_per_step = 2 * len({i.metric for i in self.insts})
         self.ctxs, self.batch = mixed_contexts(self.insts, args.precision)
         self.batch.lb_batch_set_option(L.LB_OPT_USE_GRAPH, 1)
         self.cells = self.batch.lb_batch_nodes()
