@@ -392,12 +392,15 @@ const char* lb_last_error(const lb_ctx* ctx);
  * A sweep over Dean numbers, radii and grid sizes (Sec. III and IV vary
  * the driving force, the radii ratio and the cross-section) has instances
  * of different metric kind and size. lb_batch_step advances every instance
- * of every member context by one time step per step with one launch of a
- * work-list kernel per metric kind present (the kinds run concurrently on
- * forked streams): the work list holds one entry (instance, first node) per
- * tile of block_threads consecutive nodes, so instances of any size share
- * the grid. The update is the one of lb_step (Eq. LB), node for node, and the
- * resulting states are bitwise those of lb_step on each member.
+ * of every member context by one time step per step with two launches of a
+ * work-list kernel per metric kind present: one over tiles of up to
+ * block_threads consecutive interior nodes (instance, first node, count),
+ * one over tiles of the nodes within three nodes of a wall (instance, first
+ * index into a list of wall nodes, count), so instances of any size share
+ * the grid. All these launches run concurrently on forked streams (they
+ * read one buffer and write disjoint nodes). The update is the one of
+ * lb_step (Eq. LB), node for node, and the resulting states are bitwise
+ * those of lb_step on each member.
  *
  * Members stay owned by the caller and usable with every lb_* call
  * (lb_init, lb_diagnostics, lb_get_state, ...) between batch steps; they

@@ -4,8 +4,9 @@
 // grouped by metric kind and each group gets two work lists: tiles of
 // interior nodes (instance, first node, count) and tiles of wall nodes
 // (instance, first index into a list of wall-node indices, count). One batch
-// step is two k_step_list launches per group (interior, then walls); groups
-// after the first run on forked streams so that small groups overlap.
+// step is one k_step_list launch per non-empty list; the lists after the
+// first run on forked streams, so the wall-node kernels (bound by
+// instruction fetch) overlap the interior kernels (bound by memory).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -21,6 +22,7 @@ using namespace lbgm;
 namespace {
 
 constexpr int kMaxGroups = 3;  // flat, cylinder, ellipsoid
+constexpr int kMaxLanes = 2 * kMaxGroups;  // interior and wall-node tiles of each
 
 struct Group {
   int K = 0;
@@ -82,9 +84,9 @@ struct lb_batch {
   void* dmem = nullptr;
   size_t dmem_bytes = 0;
 
-  cudaStream_t aux[kMaxGroups - 1] = {};
+  cudaStream_t aux[kMaxLanes - 1] = {};
   cudaEvent_t ev_fork = nullptr;
-  cudaEvent_t ev_join[kMaxGroups - 1] = {};
+  cudaEvent_t ev_join[kMaxLanes - 1] = {};
 
   int threads = 128;
   int schedule = 0;
@@ -253,46 +255,51 @@ bool records_current(const lb_batch* b) {
   return true;
 }
 
-// The interior tiles, then the wall-node tiles of one group, on stream s.
-cudaError_t launch_group(const lb_batch* b, const Group& gr, cudaStream_t s) {
+// One work list of one group (m = 0: interior tiles, 1: wall-node tiles) on
+// stream s.
+cudaError_t launch_lane(const lb_batch* b, const Group& gr, int m, cudaStream_t s) {
   const unsigned char* base = static_cast<const unsigned char*>(b->dmem);
   const void* insts = base + gr.inst_off;
   const int* cells = reinterpret_cast<const int*>(base + gr.cells_off);
   const int grid = b->schedule == 1 ? std::max(1, gr.blocks_per_sm) * b->nsm : 0;
-  for (int m = 0; m < 2; ++m) {
-    const int4* work = reinterpret_cast<const int4*>(base + gr.work_off[m]);
-    cudaError_t e;
-    switch (b->prec) {
-      case LB_FP64:
-        e = launch_step_list_f64(gr.K, m, insts, work, gr.nwork[m], cells, b->threads, grid, b->parity, s);
-        break;
-      case LB_FP32:
-        e = launch_step_list_f32(gr.K, m, insts, work, gr.nwork[m], cells, b->threads, grid, b->parity, s);
-        break;
-      case LB_FP16_SHIFTED:
-        e = launch_step_list_h16(gr.K, m, insts, work, gr.nwork[m], cells, b->threads, grid, b->parity, s);
-        break;
-      default:
-        e = launch_step_list_b16(gr.K, m, insts, work, gr.nwork[m], cells, b->threads, grid, b->parity, s);
-        break;
-    }
-    if (e != cudaSuccess) return e;
+  const int4* work = reinterpret_cast<const int4*>(base + gr.work_off[m]);
+  switch (b->prec) {
+    case LB_FP64:
+      return launch_step_list_f64(gr.K, m, insts, work, gr.nwork[m], cells, b->threads, grid, b->parity, s);
+    case LB_FP32:
+      return launch_step_list_f32(gr.K, m, insts, work, gr.nwork[m], cells, b->threads, grid, b->parity, s);
+    case LB_FP16_SHIFTED:
+      return launch_step_list_h16(gr.K, m, insts, work, gr.nwork[m], cells, b->threads, grid, b->parity, s);
+    default:
+      return launch_step_list_b16(gr.K, m, insts, work, gr.nwork[m], cells, b->threads, grid, b->parity, s);
   }
-  return cudaSuccess;
 }
 
-// One batch step: group 0 on the batch stream, the others forked.
+// One batch step. Every non-empty work list is a lane of its own: they read
+// the same buffer and write disjoint nodes, so they run side by side -- the
+// wall-node kernels, bound by instruction fetch, beside the interior
+// kernels, bound by memory. The first lane (an interior list) goes on the
+// batch stream first; the others are forked after it, interior lists before
+// wall-node lists, and joined back (measured: +9 % on 24 four-wall
+// double-curved channels; launching the wall-node lists first was slower).
 lb_status step_once(lb_batch* b) {
-  if (b->ngroups > 1) {
-    LB_BCUDA(b, cudaEventRecord(b->ev_fork, b->stream));
-    for (int i = 1; i < b->ngroups; ++i) {
-      LB_BCUDA(b, cudaStreamWaitEvent(b->aux[i - 1], b->ev_fork, 0));
-      LB_BCUDA(b, launch_group(b, b->g[i], b->aux[i - 1]));
-      LB_BCUDA(b, cudaEventRecord(b->ev_join[i - 1], b->aux[i - 1]));
-    }
+  int lg[kMaxLanes], lm[kMaxLanes], n = 0;
+  for (int m = 0; m < 2; ++m) {
+    for (int i = 0; i < b->ngroups; ++i)
+      if (b->g[i].nwork[m] > 0) {
+        lg[n] = i;
+        lm[n] = m;
+        ++n;
+      }
   }
-  if (b->ngroups > 0) LB_BCUDA(b, launch_group(b, b->g[0], b->stream));
-  for (int i = 1; i < b->ngroups; ++i) LB_BCUDA(b, cudaStreamWaitEvent(b->stream, b->ev_join[i - 1], 0));
+  if (n > 1) LB_BCUDA(b, cudaEventRecord(b->ev_fork, b->stream));
+  if (n > 0) LB_BCUDA(b, launch_lane(b, b->g[lg[0]], lm[0], b->stream));
+  for (int k = 1; k < n; ++k) {
+    LB_BCUDA(b, cudaStreamWaitEvent(b->aux[k - 1], b->ev_fork, 0));
+    LB_BCUDA(b, launch_lane(b, b->g[lg[k]], lm[k], b->aux[k - 1]));
+    LB_BCUDA(b, cudaEventRecord(b->ev_join[k - 1], b->aux[k - 1]));
+  }
+  for (int k = 1; k < n; ++k) LB_BCUDA(b, cudaStreamWaitEvent(b->stream, b->ev_join[k - 1], 0));
   b->parity ^= 1;
   return LB_OK;
 }
@@ -441,7 +448,7 @@ lb_status lb_batch_create(lb_ctx* const* members, int count, lb_batch** out) {
   if (e == cudaSuccess && cur_dev != b->device) e = cudaErrorInvalidDevice;
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->nsm, cudaDevAttrMultiProcessorCount, b->device);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming);
-  for (int i = 0; i < kMaxGroups - 1 && e == cudaSuccess; ++i) {
+  for (int i = 0; i < kMaxLanes - 1 && e == cudaSuccess; ++i) {
     e = cudaStreamCreateWithFlags(&b->aux[i], cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_join[i], cudaEventDisableTiming);
   }
@@ -548,7 +555,7 @@ void lb_batch_destroy(lb_batch* b) {
   if (b->stream) cudaStreamSynchronize(b->stream);
   drop_graph(b);
   if (b->dmem) cudaFree(b->dmem);
-  for (int i = 0; i < kMaxGroups - 1; ++i) {
+  for (int i = 0; i < kMaxLanes - 1; ++i) {
     if (b->aux[i]) cudaStreamDestroy(b->aux[i]);
     if (b->ev_join[i]) cudaEventDestroy(b->ev_join[i]);
   }
