@@ -223,25 +223,43 @@ def forcing(a0, a1, A2, F, cs2=L.CS2):
     return L.W[:, None] * (t0 + t1 + t2)
 
 
-def collide(f, Delta, Gamma_hat, fext, tau, old_forcing=False, cs2=L.CS2):
+def collide(f, Delta, Gamma_hat, fext, tau, old_forcing=False, cs2=L.CS2, half_force_shift=False):
     """BGK collision with the metric forcing term, one step (Eq. LB, RHS).
 
     f (Q, n) are the streamed (pre-collision) populations.
     Returns the post-collision populations (Q, n).
+
+    half_force_shift selects a variant that is not the paper's printed
+    scheme (Sec. II takes u = sum c f / rho'): the velocity of f^eq and of
+    the forcing term is u_s with u_s = u + M(u_s) / (2 rho'), M the forcing
+    term's first moment, taken by two fixed-point iterations from u
+    (u_1 = u + M(u) / (2 rho'), u_s = u + M(u_1) / (2 rho')), and the
+    forcing term is scaled by 1 - 1/(2 tau) -- the usual second-order
+    treatment of a force in a discrete-time BGK update.
     """
     rho, u = moments(f)
-    a0, a1, a2eq, _ = equilibrium_coefficients(rho, u, Delta, cs2)
-    feq = equilibrium(rho, u, Delta, cs2)
-    if old_forcing:
-        A2 = a2eq
-    else:
-        # sigma^ij = -(1 - 1/(2 tau)) sum_l c^i c^j (f_l - f^eq_l);  a2 = a2^eq - sigma
-        c = L.C.astype(np.float64)
-        sigma = -(1.0 - 1.0 / (2.0 * tau)) * _es("li,lj,ln->nij", c, c, f - feq)
-        A2 = a2eq - sigma
     F = force_vectors(Gamma_hat, fext)
-    Fl = forcing(a0, a1, A2, F, cs2)
-    return f - (f - feq) / tau + Fl
+    c = L.C.astype(np.float64)
+
+    def equilibrium_and_forcing(u):
+        a0, a1, a2eq, _ = equilibrium_coefficients(rho, u, Delta, cs2)
+        feq = equilibrium(rho, u, Delta, cs2)
+        if old_forcing:
+            A2 = a2eq
+        else:
+            # sigma^ij = -(1 - 1/(2 tau)) sum_l c^i c^j (f_l - f^eq_l);  a2 = a2^eq - sigma
+            sigma = -(1.0 - 1.0 / (2.0 * tau)) * _es("li,lj,ln->nij", c, c, f - feq)
+            A2 = a2eq - sigma
+        return feq, forcing(a0, a1, A2, F, cs2)
+
+    feq, Fl = equilibrium_and_forcing(u)
+    if not half_force_shift:
+        return f - (f - feq) / tau + Fl
+    u0 = u
+    for _ in range(2):
+        u = u0 + 0.5 * _es("li,ln->ni", c, Fl) / rho[:, None]
+        feq, Fl = equilibrium_and_forcing(u)
+    return f - (f - feq) / tau + (1.0 - 1.0 / (2.0 * tau)) * Fl
 
 
 # --------------------------------------------------------------------------
@@ -254,6 +272,7 @@ class Params:
     tau: float
     G: float = 0.0
     old_forcing: bool = False
+    half_force_shift: bool = False
 
 
 class Simulation:
@@ -304,7 +323,7 @@ class Simulation:
 
     def _collide(self, fs, cells=slice(None)):
         out = collide(fs, self.Delta[cells], self.Gamma_hat[cells], self.fext[cells],
-                      self.p.tau, self.p.old_forcing)
+                      self.p.tau, self.p.old_forcing, half_force_shift=self.p.half_force_shift)
         wall = self.wall_nodes[cells]
         if wall.any():  # Dirichlet walls: f^eq(rho', u = 0) of the wall node
             rho, _ = moments(fs[:, wall])
