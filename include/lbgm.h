@@ -121,7 +121,19 @@ typedef struct {
   double force_G;           /* constant covariant streamwise force per step:
                                F^i_ext = g^{i theta} * force_G */
   int old_forcing;          /* 0: improved forcing a2 = a2^eq - sigma (Sec. II);
-                               1: the earlier method, a2 = a2^eq */
+                               1: the earlier method, a2 = a2^eq;
+                               2: improved forcing with the half-force
+                               velocity -- not the paper's printed scheme:
+                               f^eq and the forcing term take
+                               u_s = u + M(u_s) / (2 rho'), M the forcing
+                               term's first moment (two fixed-point
+                               iterations from u = sum c f / rho'), and the
+                               forcing term is scaled by 1 - 1/(2 tau).
+                               FP64 and FP32 storage only; a context with
+                               any such instance runs the plain step kernel
+                               (LB_OPT_STEP_KERNEL is ignored) and cannot
+                               join an lb_batch. lb_macros still reports
+                               u = sum c f / rho'. */
   unsigned long long seed;  /* velocity noise seed (see lb_init) */
   double noise_amp;         /* noise amplitude (lattice velocity units) */
   int init_base_flow;       /* 1: start from the laminar profile for force_G

@@ -88,9 +88,9 @@ void fill_inst(const lb_params* p, int batch, std::vector<InstParams<Real>>& out
   out.resize(batch);
   for (int b = 0; b < batch; ++b) {
     out[b].omega = Real(1.0 / p[b].tau);
-    out[b].kappa = p[b].old_forcing ? Real(0) : Real(1.0 - 1.0 / (2.0 * p[b].tau));
+    out[b].kappa = p[b].old_forcing == 1 ? Real(0) : Real(1.0 - 1.0 / (2.0 * p[b].tau));
     out[b].G = Real(p[b].force_G);
-    out[b].pad = Real(0);
+    out[b].pad = p[b].old_forcing == 2 ? Real(1) : Real(0);  // the half-force velocity variant
   }
 }
 
@@ -100,7 +100,14 @@ lb_status upload_params(lb_ctx* c, const lb_params* p) {
       return fail(c, LB_ERR_ARG, "instance " + std::to_string(b) + ": need tau > 1/2");
     if (!std::isfinite(p[b].force_G) || !std::isfinite(p[b].noise_amp))
       return fail(c, LB_ERR_ARG, "instance " + std::to_string(b) + ": non-finite force or noise");
+    if (p[b].old_forcing < 0 || p[b].old_forcing > 2)
+      return fail(c, LB_ERR_ARG, "instance " + std::to_string(b) + ": old_forcing must be 0, 1 or 2");
+    if (p[b].old_forcing == 2 && c->prec != LB_FP64 && c->prec != LB_FP32)
+      return fail(c, LB_ERR_ARG, "instance " + std::to_string(b) +
+                                     ": the half-force velocity (old_forcing 2) needs FP64 or FP32 storage");
   }
+  c->any_shift = false;
+  for (int b = 0; b < c->batch; ++b) c->any_shift = c->any_shift || p[b].old_forcing == 2;
   if (c->prec == LB_FP64) {
     std::vector<InstParams<double>> h;
     fill_inst(p, c->batch, h);
@@ -236,6 +243,7 @@ cudaError_t launch_split(lb_ctx* c, int src, int dst) {
 // LB_OPT_STEP_KERNEL 0 (auto): the region split where x3 is periodic and the
 // arithmetic is FP32 (measured fastest there), the one-kernel step otherwise.
 int resolved_kernel(const lb_ctx* c) {
+  if (c->any_shift) return 1;  // the half-force variant runs in the plain kernel only
   if (c->step_kernel != 0) return c->step_kernel;
   if (c->prec == LB_FP64) return 1;
   return (c->geom.periodic3 && c->geom.wall == LB_WALL_BOUNCEBACK) ? 4 : 5;
@@ -270,6 +278,14 @@ lb_status launch_step_once(lb_ctx* c) {
     if (st != LB_OK) return st;
     e = cudaSuccess;
   }
+  else if (c->any_shift && c->prec == LB_FP64)
+    e = launch_step_shift_f64(c->K, static_cast<const double*>(c->f[src]), static_cast<double*>(c->f[dst]),
+                              c->geo_d, static_cast<const InstParams<double>*>(c->inst), c->dims, c->flag,
+                              c->block_threads, c->stream);
+  else if (c->any_shift)
+    e = launch_step_shift_f32(c->K, static_cast<const float*>(c->f[src]), static_cast<float*>(c->f[dst]),
+                              c->geo_f, static_cast<const InstParams<float>*>(c->inst), c->dims, c->flag,
+                              c->block_threads, c->stream);
   else if (use_tma(c))
     e = launch_step_tma_f32(c->K, c->tmap[src], static_cast<const float*>(c->f[src]),
                             static_cast<float*>(c->f[dst]), c->geo_f,
@@ -833,12 +849,14 @@ lb_status lb_autotune(lb_ctx* c, int steps_per_trial, lb_tune* best, lb_tune* tr
     for (int t : {64, 128, 192, 256}) cand.push_back({t, 1, 0, 0.0});
   else
     for (int t : {64, 96, 128}) cand.push_back({t, 1, 0, 0.0});
-  if (c->geom.periodic3 && c->geom.wall == LB_WALL_BOUNCEBACK)
-    for (int t : {64, 96, 128}) cand.push_back({t, 4, 0, 0.0});
-  for (int t : {64, 96, 128}) cand.push_back({t, 5, 0, 0.0});
-  if (c->tma_ok) cand.push_back({0, 2, 0, 0.0});  // the TMA kernel fixes its own block shape
-  for (int t : {128, 256})
-    for (int npt : {2, 4, 8}) cand.push_back({t, 3, npt, 0.0});
+  if (!c->any_shift) {  // the half-force variant has the plain kernel only
+    if (c->geom.periodic3 && c->geom.wall == LB_WALL_BOUNCEBACK)
+      for (int t : {64, 96, 128}) cand.push_back({t, 4, 0, 0.0});
+    for (int t : {64, 96, 128}) cand.push_back({t, 5, 0, 0.0});
+    if (c->tma_ok) cand.push_back({0, 2, 0, 0.0});  // the TMA kernel fixes its own block shape
+    for (int t : {128, 256})
+      for (int npt : {2, 4, 8}) cand.push_back({t, 3, npt, 0.0});
+  }
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   LB_CUDA(c, cudaEventCreate(&e0));
   cudaError_t e = cudaEventCreate(&e1);

@@ -64,6 +64,7 @@ struct lb_ctx {
   int graph_threads = 0;
   int graph_kernel = -1;
   int step_kernel = 0;               // LB_OPT_STEP_KERNEL
+  bool any_shift = false;            // an instance uses the half-force velocity (old_forcing 2)
   int nodes_per_thread = 4;          // LB_OPT_NODES_PER_THREAD
   int graph_npt = 0;
   lb_batch* tiles = nullptr;         // private single-member batch of the tiled step

@@ -26,6 +26,15 @@ cudaError_t launch_step_b16(int K, const __nv_bfloat16* fin, __nv_bfloat16* fout
                             const InstParams<float>* inst, const Dims& d, int* flag, int threads,
                             cudaStream_t s);
 
+// Plain step whose instances may use the half-force velocity variant
+// (InstParams::pad = 1); see step_shift.cu.
+cudaError_t launch_step_shift_f64(int K, const double* fin, double* fout, const GeoDev<double>& geo,
+                                  const InstParams<double>* inst, const Dims& d, int* flag, int threads,
+                                  cudaStream_t s);
+cudaError_t launch_step_shift_f32(int K, const float* fin, float* fout, const GeoDev<float>& geo,
+                                  const InstParams<float>* inst, const Dims& d, int* flag, int threads,
+                                  cudaStream_t s);
+
 // Region-split step (periodic x3): wall layers on stream se, interior on s.
 cudaError_t launch_step_split_f64(int K, const double* fin, double* fout, const GeoDev<double>& geo,
                                   const InstParams<double>* inst, const Dims& d, int* flag, int threads,

@@ -219,9 +219,14 @@ def lb_force_for_dean(metric: str, desc: lb_geometry_desc, tau: float, De: float
     return G.value
 
 
+FORCING_IMPROVED, FORCING_OLD, FORCING_HALF_FORCE_VELOCITY = 0, 1, 2
+
+
 def make_params(tau, force_G=0.0, old_forcing=False, seed=0, noise_amp=0.0,
                 init_base_flow=False) -> lb_params:
-    return lb_params(float(tau), float(force_G), int(bool(old_forcing)), int(seed),
+    """old_forcing: False / 0 improved forcing (Sec. II), True / 1 the earlier
+    method, 2 the half-force velocity variant (see include/lbgm.h)."""
+    return lb_params(float(tau), float(force_G), int(old_forcing), int(seed),
                      float(noise_amp), int(bool(init_base_flow)))
 
 

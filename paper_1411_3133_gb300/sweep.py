@@ -334,16 +334,18 @@ def critical_dean_decay(deans, sigmas, npoints=4):
 
 
 def develop_donor(spec: L.ChannelSpec, tau, donor_dean, donor_steps=400_000, precision="fp32",
-                  seed=20241111, noise_amp=1e-4):
+                  seed=20241111, noise_amp=1e-4, forcing=0):
     """One instance at donor_dean (above threshold), started from the laminar
     profile plus seeded noise and run donor_steps: returns its populations
-    (host FP64, shape (1, Q, N)) and its vortex amplitude."""
+    (host FP64, shape (1, Q, N)) and its vortex amplitude. `forcing` is
+    lb_params.old_forcing (0 the paper's improved forcing, 2 the half-force
+    velocity variant)."""
     desc = spec.desc()
     donor = L.LBContext(spec, batch=1, precision=precision)
     try:
         donor.lb_set_option(L.LB_OPT_USE_GRAPH, 1)
         donor.lb_set_option(L.LB_OPT_CHECK_EVERY, 0)
-        donor.lb_init([L.make_params(tau, L.lb_force_for_dean(spec.metric, desc, tau, donor_dean), False,
+        donor.lb_init([L.make_params(tau, L.lb_force_for_dean(spec.metric, desc, tau, donor_dean), forcing,
                                      seed, noise_amp, True)])
         donor.lb_step(donor_steps)
         amp = donor.lb_diagnostics()[0]["vortex_amp_x3"]
@@ -353,7 +355,7 @@ def develop_donor(spec: L.ChannelSpec, tau, donor_dean, donor_steps=400_000, pre
 
 
 def continue_from(spec: L.ChannelSpec, tau, deans, f_donor, steps=400_000, sample_every=2000,
-                  precision="fp32", recapture_every=50_000):
+                  precision="fp32", recapture_every=50_000, forcing=0):
     """Every instance of a batch (one per Dean number, each with its own
     force and, for 2-byte storage, its own laminar reference table) starts
     from the donor populations and runs `steps`. Above threshold the vortex
@@ -373,7 +375,7 @@ def continue_from(spec: L.ChannelSpec, tau, deans, f_donor, steps=400_000, sampl
     import torch
 
     desc = spec.desc()
-    params = [L.make_params(tau, L.lb_force_for_dean(spec.metric, desc, tau, de), False, 0, 0.0, True)
+    params = [L.make_params(tau, L.lb_force_for_dean(spec.metric, desc, tau, de), forcing, 0, 0.0, True)
               for de in deans]
     ctx = L.LBContext(spec, batch=len(deans), precision=precision)
     ctx.lb_set_option(L.LB_OPT_USE_GRAPH, 1)
@@ -435,15 +437,15 @@ def dean_bracket(deans, saturated):
 
 def continuation_sweep(spec: L.ChannelSpec, tau, deans, donor_dean, donor_steps=400_000,
                        steps=400_000, sample_every=2000, precision="fp32", seed=20241111,
-                       noise_amp=1e-4):
+                       noise_amp=1e-4, forcing=0):
     """De_c of a sharp (supercritical) Dean bifurcation by continuation from
     a developed 2-cell vortex (develop_donor, then continue_from). Adds
     "donor_amp" and the total "seconds" of both phases to continue_from's
     result."""
     import time
     t0 = time.perf_counter()
-    f, amp = develop_donor(spec, tau, donor_dean, donor_steps, precision, seed, noise_amp)
-    r = continue_from(spec, tau, deans, f, steps, sample_every, precision)
+    f, amp = develop_donor(spec, tau, donor_dean, donor_steps, precision, seed, noise_amp, forcing)
+    r = continue_from(spec, tau, deans, f, steps, sample_every, precision, forcing=forcing)
     r["donor_amp"] = amp
     r["seconds"] = time.perf_counter() - t0
     return r
@@ -565,6 +567,11 @@ if __name__ == "__main__":
     ap.add_argument("--continuation", default=None, metavar="ETA",
                     help="De_c of the cylinder of aspect ratio ETA (128 x 1 x 256, tau 0.9, Sec. III) "
                          "by continuation from a developed vortex")
+    ap.add_argument("--deans", default="38,53", help="--continuation: lowest,highest target De (16 values)")
+    ap.add_argument("--donor", type=float, default=54.0, help="--continuation: the donor's target De")
+    ap.add_argument("--forcing", type=int, default=0,
+                    help="lb_params.old_forcing for --continuation: 0 the paper's improved forcing, "
+                         "2 the half-force velocity variant")
     ap.add_argument("--precisions", action="store_true",
                     help="De_c of the 64 x 4 x 256 narrow-gap sweep by continuation in every storage precision")
     a = ap.parse_args()
@@ -593,8 +600,10 @@ if __name__ == "__main__":
     if a.continuation:
         eta = float(a.continuation)
         spec = L.ChannelSpec("cylindrical", 1.0, 1.0 / eta, 129, 1, 256, wall="equilibrium")
-        r = continuation_sweep(spec, 0.9, list(np.linspace(38.0, 53.0, 16)), donor_dean=54.0,
-                               donor_steps=a.steps, steps=a.steps, sample_every=a.sample_every)
+        lo, hi = (float(x) for x in a.deans.split(","))
+        r = continuation_sweep(spec, 0.9, list(np.linspace(lo, hi, 16)), donor_dean=a.donor,
+                               donor_steps=a.steps, steps=a.steps, sample_every=a.sample_every,
+                               forcing=a.forcing)
         print(json.dumps({k: v for k, v in r.items() if k not in ("amp", "times")}, indent=1))
         if a.out:
             with open(a.out, "w") as f:

@@ -29,7 +29,8 @@ def spec_of(ch: Channel):
 class Twin:
     """The same channel batch on the GPU (library) and in the oracle.
 
-    params: list of dicts with keys tau, G, old, seed, amp, base.
+    params: list of dicts with keys tau, G, old, shift, seed, amp, base
+    (shift: the half-force velocity variant, old_forcing 2 of the library).
     """
 
     def __init__(self, ch: Channel, params, precision="fp64", stream=None):
@@ -41,9 +42,10 @@ class Twin:
         self.ctx = L.LBContext(spec_of(ch), batch=self.B, precision=precision, stream=stream)
         self.geo = channel_geometry(ch)
         smap = StreamMap(ch)
-        self.sims = [Simulation(ch, Params(p["tau"], p.get("G", 0.0), p.get("old", False)),
+        self.sims = [Simulation(ch, Params(p["tau"], p.get("G", 0.0), p.get("old", False),
+                                           half_force_shift=p.get("shift", False)),
                                 self.geo, smap) for p in params]
-        self.lparams = [L.make_params(p["tau"], p.get("G", 0.0), p.get("old", False),
+        self.lparams = [L.make_params(p["tau"], p.get("G", 0.0), 2 if p.get("shift") else p.get("old", False),
                                       p.get("seed", 0), p.get("amp", 0.0), p.get("base", False))
                         for p in params]
 

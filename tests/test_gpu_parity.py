@@ -91,6 +91,16 @@ CASES = {
                             [dict(tau=0.8, G=2e-4, seed=24, amp=1e-2)]),
     "cyl_eqwall_nr3": (Channel("cylindrical", 1.0, 1.02, 3, 2, 8, wall="equilibrium"),
                        [dict(tau=0.9, G=1e-4, seed=25, amp=1e-2)]),
+    # the half-force velocity variant (old_forcing 2), alone and mixed with the literal step
+    "cyl_shift": (Channel("cylindrical", 1.0, 1 / 0.8, 10, 2, 20),
+                  [dict(tau=0.75, G=3e-4, seed=8, amp=1e-2, shift=True)]),
+    "ell_shift_mixed": (Channel("ellipsoidal", 1.0, 1.1, 10, 4, 14, b=0.9, periodic3=False),
+                        [dict(tau=0.7, G=3e-4, seed=10, amp=1e-2, shift=True),
+                         dict(tau=0.9, G=2e-4, seed=14, amp=1e-2)]),
+    "cyl_eqwall_shift": (Channel("cylindrical", 1.0, 1 / ETA, 17, 4, 32, wall="equilibrium"),
+                         [dict(tau=0.8, G=2e-4, seed=21, amp=1e-2, shift=True)]),
+    "flat_shift": (Channel("flat", 0.0, 1.0, 8, 2, 9, periodic3=False),
+                   [dict(tau=0.6, G=1e-3, seed=9, amp=1e-2, shift=True)]),
     "batch3": (Channel("cylindrical", 1.0, 1 / ETA, 8, 4, 33),
                [dict(tau=0.8, G=1e-4, seed=1, amp=1e-3), dict(tau=0.6, G=3e-4, seed=2, amp=2e-3),
                 dict(tau=1.1, G=0.0, seed=3, amp=5e-3, old=True)]),
@@ -162,6 +172,47 @@ def test_fp32_step_parity(ch):
         done = n
         _compare_macros(tw, 1e-5, 1e-5)
     tw.close()
+
+
+@pytest.mark.parametrize("ch", [CYL1, Channel("ellipsoidal", 1.0, 1.1, 10, 4, 40, b=0.9,
+                                              periodic3=False, wall="equilibrium")],
+                         ids=["cyl", "ell_eqwall"])
+def test_fp32_half_force_variant_parity(ch):
+    """The half-force velocity variant in FP32 against the FP64 oracle's
+    variant, 1e-5 of u_max."""
+    params = [dict(tau=0.8, G=G_LAMINAR, shift=True)]
+    tw = Twin(ch, params, "fp32")
+    rho = np.stack([1.0 / tw.sims[0].sqrtg])
+    u = (_smooth_flow(ch) + noise_field(32, tw.N, 1e-3))[None]
+    tw.init_fields(rho, u)
+    done = 0
+    for n in (1, 10, 100):
+        tw.step(n - done)
+        done = n
+        _compare_macros(tw, 1e-5, 1e-5)
+    tw.close()
+
+
+def test_half_force_variant_rules():
+    """2-byte storage rejects the variant; a batch refuses a member using it;
+    the autotuner keeps to the plain kernel."""
+    L = lib()
+    spec = L.ChannelSpec("cylindrical", 1.0, 1 / ETA, 8, 4, 32)
+    p2 = [L.make_params(0.8, 1e-4, 2, 1, 1e-3, False)]
+    with L.LBContext(spec, 1, "fp16_shifted") as c:
+        with pytest.raises(L.LBError) as e:
+            c.lb_init(p2)
+        assert "half-force" in str(e.value)
+    with L.LBContext(spec, 1, "fp32") as c, L.LBContext(spec, 1, "fp32", stream=c.stream) as d:
+        c.lb_init(p2)
+        d.lb_init([L.make_params(0.8, 1e-4, 0, 1, 1e-3, False)])
+        best, trials = c.lb_autotune(2)
+        assert {t["schedule"] for t in trials} == {1}
+        b = L.LBBatch([c, d])
+        with pytest.raises(L.LBError) as e:
+            b.lb_batch_step(1)
+        assert "half-force" in str(e.value)
+        b.close()
 
 
 def test_init_fields_matches_oracle():
