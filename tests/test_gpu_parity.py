@@ -203,6 +203,10 @@ def test_half_force_variant_rules():
         with pytest.raises(L.LBError) as e:
             c.lb_init(p2)
         assert "half-force" in str(e.value)
+    with L.LBContext(spec, 1, "fp32") as c:
+        with pytest.raises(L.LBError) as e:
+            c.lb_init([L.make_params(0.8, 1e-4, 3, 1, 1e-3, False)])
+        assert "0, 1 or 2" in str(e.value)
     with L.LBContext(spec, 1, "fp32") as c, L.LBContext(spec, 1, "fp32", stream=c.stream) as d:
         c.lb_init(p2)
         d.lb_init([L.make_params(0.8, 1e-4, 0, 1, 1e-3, False)])
