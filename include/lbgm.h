@@ -192,7 +192,10 @@ typedef enum {
                                wall code; 5: tiled: runs of interior nodes
                                and the wall nodes in two kernels (the
                                lb_batch work-list kernels over this context
-                               alone), for any geometry.
+                               alone), for any geometry. With instances
+                               of the half-force velocity variant
+                               (lb_params.old_forcing 2) the context runs
+                               kernel 1 whatever is set here.
                                Unsupported choices return LB_ERR_ARG. All
                                give bitwise identical states. */
   LB_OPT_SCHEDULE = 4,      /* batches only (lb_batch_set_option): 0: one
