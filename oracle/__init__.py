@@ -19,6 +19,8 @@ Modules
 -------
 lattice      D3Q41 velocity set and weights (Table I), Hermite tensors.
 geometry     embeddings, metric, Christoffel symbols (Sec. III-IV).
-lbm          streaming with walls, equilibrium, forcing, BGK step (Sec. II).
+lbm          streaming with walls, equilibrium, forcing, BGK step (Sec. II);
+             the half-force velocity variant of the collision as a flag (not
+             the paper's printed scheme).
 diagnostics  Dean number, mean velocity, vorticity, mass (Sec. III-IV).
 """
