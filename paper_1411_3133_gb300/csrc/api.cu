@@ -607,7 +607,10 @@ lb_status lb_step(lb_ctx* c, long long n) {
       s = ctx_tiled_prepare(c);
       if (s != LB_OK) return s;
     }
-    if (!c->graph || c->graph_threads != c->block_threads || c->graph_kernel != c->step_kernel ||
+    // the captured kernels depend on the resolved step kernel and on whether
+    // an instance uses the half-force variant (both can change with lb_init)
+    const int gk = 2 * resolved_kernel(c) + (c->any_shift ? 1 : 0);
+    if (!c->graph || c->graph_threads != c->block_threads || c->graph_kernel != gk ||
         c->graph_npt != c->nodes_per_thread) {
       if (c->graph) cudaGraphExecDestroy(c->graph);
       c->graph = nullptr;
@@ -622,7 +625,7 @@ lb_status lb_step(lb_ctx* c, long long n) {
       cudaGraphDestroy(g);
       if (e != cudaSuccess) return cuda_fail(c, e, "cudaGraphInstantiate");
       c->graph_threads = c->block_threads;
-      c->graph_kernel = c->step_kernel;
+      c->graph_kernel = gk;
       c->graph_npt = c->nodes_per_thread;
     }
     for (long long i = 0; i + 1 < n; i += 2) {

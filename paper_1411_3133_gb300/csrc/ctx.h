@@ -62,7 +62,7 @@ struct lb_ctx {
   int use_graph = 0;
   cudaGraphExec_t graph = nullptr;   // two steps, buffer 0 -> 1 -> 0
   int graph_threads = 0;
-  int graph_kernel = -1;
+  int graph_kernel = -1;             // 2 x resolved step kernel + any_shift of the captured graph
   int step_kernel = 0;               // LB_OPT_STEP_KERNEL
   bool any_shift = false;            // an instance uses the half-force velocity (old_forcing 2)
   int nodes_per_thread = 4;          // LB_OPT_NODES_PER_THREAD
