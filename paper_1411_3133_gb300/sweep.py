@@ -19,7 +19,15 @@ Here:
   * secondary: sigma = slope of ln A(t) over the window where the leading
     mode dominates and the amplitude is still small; the first sign change of
     sigma(De). Below threshold A sits on the FP32 round-off floor, so this
-    estimate is noisy near De_c.
+    estimate is noisy near De_c;
+  * continuation (continuation_sweep, continue_from): a developed vortex
+    starts every Dean number, so decay rates below threshold are measured
+    far above the round-off floor and the saturated amplitudes above it
+    settle quickly; the bracket and both lines are reported;
+  * the double-curved channel carries a secondary flow at every De
+    (imperfect bifurcation): De_c is the knee of the mean vorticity curve
+    (critical_dean_knee; double_curved_study runs the Sec. IV.A and IV.B
+    curvature families).
 
 All stepping and reductions run in the CUDA library; this module only
 orchestrates calls and fits a straight line.
