@@ -1,0 +1,34 @@
+"""Host logic of bench.py's roofline inputs: figures are read from a committed
+ncu summary only while its kernel-source hash matches the current sources."""
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+
+def _summary(tmp_path, sha, body):
+    p = tmp_path / "summary.md"
+    p.write_text(f"# a kernel\n\n    kernel_source_sha: {sha}\n{body}\n")
+    return str(p)
+
+
+def test_profile_value_needs_the_current_source_hash(tmp_path):
+    sha = bench.kernel_source_hash()
+    good = _summary(tmp_path, sha, "    dram_bytes_per_launch: 449384448\n    fp32_flops_per_update: 1090.19")
+    assert bench.profile_value(good, "dram_bytes_per_launch") == 449384448.0
+    assert bench.profile_value(good, "fp32_flops_per_update") == 1090.19
+    assert bench.profile_value(good, "missing_key") is None
+    stale = _summary(tmp_path, "0" * 16, "    dram_bytes_per_launch: 1")
+    assert bench.profile_value(stale, "dram_bytes_per_launch") is None
+    assert bench.profile_value(str(tmp_path / "absent.md"), "dram_bytes_per_launch") is None
+
+
+def test_fp64_figures_hash_only_the_fp64_kernel_body(tmp_path):
+    sha = bench.kernel_source_hash(bench.FP64_KERNEL_SOURCES)
+    assert sha != bench.kernel_source_hash()
+    p = _summary(tmp_path, sha, "    fp64_flops_per_update: 1085")
+    assert bench.profile_value(p, "fp64_flops_per_update", bench.FP64_KERNEL_SOURCES) == 1085.0
+    assert bench.profile_value(p, "fp64_flops_per_update") is None
