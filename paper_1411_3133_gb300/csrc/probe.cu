@@ -79,7 +79,10 @@ lb_status run_probe(cudaStream_t st, double* flops_per_s) {
       break;
     }
     float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
+    if (cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess || !(ms > 0.f)) {
+      status = probe_fail(LB_ERR_CUDA, "lb_fma_peak: event timing failed");
+      break;
+    }
     if (ms < 50.f && iters < (1 << 24)) {  // too short to time: lengthen
       iters *= 2;
       continue;
