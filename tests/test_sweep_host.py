@@ -150,3 +150,21 @@ def test_dean_bracket_between_last_decaying_and_first_saturated():
     assert lo == 41.0 and np.isnan(hi)
     lo, hi = dean_bracket([40.0, 41.0], [True, True])
     assert np.isnan(lo) and hi == 40.0
+
+
+def test_vortex_cells_counts_sign_bands_along_x3():
+    from paper_1411_3133_gb300.sweep import vortex_cells
+    nr, nt, n3 = 9, 4, 128
+    rng = np.random.default_rng(5)
+    z = np.arange(n3)
+    r = np.sin(np.pi * (np.arange(nr) + 0.5) / nr)[:, None, None]
+    for k, cells in ((1, 2), (2, 4), (3, 6)):
+        ur = r * np.sin(2 * np.pi * k * (z + 0.3) / n3)[None, None, :] * np.ones((nr, nt, 1))
+        ur = ur * 1e-3 + 1e-6 * rng.standard_normal(ur.shape)
+        assert vortex_cells(ur.ravel(), nr, nt, n3) == cells
+        # an x3-uniform radial drift is not a vortex
+        assert vortex_cells((ur + 5e-3).ravel(), nr, nt, n3) == cells
+    assert vortex_cells(np.zeros(nr * nt * n3), nr, nt, n3) == 0
+    # the 6-cell state of Sec. IV.B: one of the three wavelengths weaker
+    ur = (np.sin(2 * np.pi * 3 * z / n3) * (1 + 0.4 * np.cos(2 * np.pi * z / n3)))[None, None, :]
+    assert vortex_cells((r * ur * np.ones((nr, nt, 1))).ravel(), nr, nt, n3) == 6
