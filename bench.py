@@ -238,6 +238,22 @@ def rank_seed(base: int, rank: int) -> int:
     return base + 1000 * rank
 
 
+def timed_windows(runner, stream, steps: int, min_seconds: float, min_windows: int):
+    """Durations (ms, CUDA events on the launching stream) of back-to-back
+    windows of `steps` steps each, until their sum reaches min_seconds and
+    there are at least min_windows of them."""
+    import torch
+    out = []
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    while len(out) < min_windows or sum(out) < 1e3 * min_seconds:
+        ev0.record(stream)
+        runner.step(steps)
+        ev1.record(stream)
+        ev1.synchronize()
+        out.append(ev0.elapsed_time(ev1))
+    return out
+
+
 # ---------------------------------------------------------------------------
 # workloads
 # ---------------------------------------------------------------------------
@@ -430,7 +446,7 @@ class MixedRunner:
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20000)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=200)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=20)
@@ -444,6 +460,9 @@ def main():
                     help="sweep: 24-instance 64x4x256 cylinder Dean sweep; mixed: 128 channels "
                          "of mixed metric and size in one lb_batch; ellipsoid: 24 instances of the "
                          "64x4x256 double-curved channel with four walls")
+    ap.add_argument("--min-seconds", type=float, default=1.0,
+                    help="repeat the K-step window until this much GPU time has accumulated")
+    ap.add_argument("--min-windows", type=int, default=5, help="at least this many K-step windows")
     ap.add_argument("--tune-steps", type=int, default=20,
                     help="mixed: steps per autotuner trial (taken inside the warm-up)")
     args = ap.parse_args()
@@ -484,14 +503,14 @@ def main():
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    runner.step(args.steps)
-    ev1.record(stream)
+    # the K-step window, repeated until at least --min-seconds of GPU time
+    # (and --min-windows windows) have accumulated; the median window is the
+    # measurement, so a short --steps still gives a stable number
+    windows = timed_windows(runner, stream, args.steps, args.min_seconds, args.min_windows)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
-    ms = ev0.elapsed_time(ev1)
+    ms = statistics.median(windows)
     clocks = sampler.stop() if sampler else None
     d = runner.diagnostics()
     finite = all(x["nonfinite"] == 0 for x in d)
@@ -550,13 +569,16 @@ def main():
         line = {
             "metric": METRIC, "value": round(value, 2), "unit": "MLUPS", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 6),
+            "windows": {"count": len(windows), "steps_each": args.steps, "statistic": "median",
+                        "ms_min": round(min(windows), 4), "ms_median": round(ms, 4),
+                        "ms_max": round(max(windows), 4), "gpu_seconds": round(sum(windows) / 1e3, 3)},
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": DTYPE[args.precision], "data": "synthetic",
             "config": dict(runner.config(), bytes_per_update=bpu, parallelism=f"replicas x{world}"),
             "roofline": roofline,
             "e2e": {"value": round(e2e_value, 2), "unit": "MLUPS", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "steps": args.e2e_steps},
-            "gpu_launches": args.steps * runner.launches_per_step,
+            "gpu_launches": len(windows) * args.steps * runner.launches_per_step,
             "clocks": clocks,
             "cpu_baseline": cpu,
             "finite": finite,

@@ -354,10 +354,10 @@ long long lb_step_count(const lb_ctx* ctx);
  * Allocates no device memory: its working memory is one file-scope device
  * array of LB_NOALLOC_SCRATCH_BYTES bytes, held by every GPU that loads the
  * library until the process exits. Sizes needing more return LB_ERR_ARG.
- * The first call on a device (with it current) looks the array's address up;
- * make that call before any stream capture. All calls share the array, so
- * calls that overlap on the GPU race. Synchronises cuda_stream. Errors are
- * reported through lb_last_error(NULL). */
+ * Every call looks the array's address up on the current device (the one
+ * rho and u live on). All calls share the array, so calls that overlap on
+ * the GPU race. Synchronises cuda_stream. Errors are reported through
+ * lb_last_error(NULL). */
 #define LB_NOALLOC_SCRATCH_BYTES (4u << 20)
 #define LB_NOALLOC_MAX_BATCH 64
 lb_status lb_diagnostics_noalloc(lb_metric metric, const lb_geometry_desc* geom, int batch,

@@ -56,19 +56,6 @@ std::string validate_geometry(lb_metric metric, const lb_geometry_desc& g) {
   return "";
 }
 
-double lattice_h(const lb_geometry_desc& g) {
-  return (g.r_outer - g.r_inner) / (g.wall == LB_WALL_EQUILIBRIUM ? g.nr - 1 : g.nr);
-}
-
-double node_r(const lb_geometry_desc& g, int ir) {
-  return g.r_inner + (g.wall == LB_WALL_EQUILIBRIUM ? ir : ir + 0.5) * lattice_h(g);
-}
-
-double node_x3(const lb_geometry_desc& g, int i3) {
-  const bool on_walls = g.wall == LB_WALL_EQUILIBRIUM && !g.periodic3;
-  return (on_walls ? i3 - 0.5 * (g.n3 - 1) : i3 + 0.5 - 0.5 * g.n3) * lattice_h(g) * g.d3_scale;
-}
-
 double curvature_radius(lb_metric metric, const lb_geometry_desc& g) {
   if (metric == LB_METRIC_CYLINDRICAL) return g.r_inner;
   if (metric == LB_METRIC_ELLIPSOIDAL) return g.r_inner * g.b * g.b;
@@ -84,40 +71,30 @@ std::vector<double> evaluate_geometry(lb_metric metric, const lb_geometry_desc& 
     const double r = node_r(gd, ir);
     for (int i3 = 0; i3 < n3; ++i3) {
       const double x3 = node_x3(gd, i3);  // z or phi
-      double g[3] = {1.0, 1.0, 1.0};                               // physical, diagonal at theta = 0
-      double G[3][3][3] = {};                                      // physical Gamma^i_jk
-      double wA = 1.0, wOm = 1.0;
+      const NodeMetric nm = node_metric(metric, gd, r, x3);  // physical, diagonal at theta = 0
+      double G[3][3][3] = {};                                  // physical Gamma^i_jk
       if (metric == LB_METRIC_CYLINDRICAL) {
-        g[1] = r * r;
         G[0][1][1] = -r;
         G[1][0][1] = G[1][1][0] = 1.0 / r;
-        wOm = r;
       } else if (metric == LB_METRIC_ELLIPSOIDAL) {
         const double cp = std::cos(x3), sp = std::sin(x3);
-        g[1] = gd.b * gd.b * r * r * cp * cp;
-        g[2] = r * r;
         G[0][1][1] = -r * cp * cp;
         G[0][2][2] = -r;
         G[1][0][1] = G[1][1][0] = 1.0 / r;
         G[2][0][2] = G[2][2][0] = 1.0 / r;
         G[1][1][2] = G[1][2][1] = -sp / cp;
         G[2][1][1] = sp * cp;
-        wA = r;
-        wOm = gd.b * r * cp;
       }
       double* row = &out[(size_t(ir) * n3 + i3) * LB_GEO_STRIDE];
       double gs[3];
-      for (int i = 0; i < 3; ++i) gs[i] = g[i] * s[i] * s[i];
+      scaled_metric(nm, gd, gs);
       for (int i = 0; i < 3; ++i) row[GEO_DELTA + i * 3 + i] = 1.0 / gs[i] - 1.0;
       for (int i = 0; i < 3; ++i)
         for (int j = 0; j < 3; ++j)
           for (int k = 0; k < 3; ++k)
             row[GEO_GAMMA + (i * 3 + j) * 3 + k] = h * G[i][j][k] * s[j] * s[k] / s[i];
       row[GEO_FDIR + 1] = 1.0 / gs[1];
-      row[GEO_SQRTG] = std::sqrt(gs[0] * gs[1] * gs[2]);
-      row[GEO_SPEED] = std::sqrt(gs[1]);
-      row[GEO_WA] = wA;
-      row[GEO_WOMEGA] = wOm;
+      observable_weights(metric, gd, ir, i3, &row[GEO_SQRTG]);  // sqrt g', speed, wA, wOmega
       row[GEO_RPHYS] = r;
     }
   }

@@ -14,18 +14,18 @@
 // same call, so nothing has to be cleared. Two calls whose work overlaps on
 // the GPU (different streams, or different host threads) race on it.
 //
-// Host code cannot use the array's name as a device address, so the first
-// call on each device, with that device current, looks the address up with
-// cudaGetSymbolAddress and keeps it; make that first call before any stream
-// capture.
+// Host code cannot use the array's name as a device address: every call
+// looks the address up with cudaGetSymbolAddress on the current device, so
+// the pointer it passes to the kernels is always that device's copy (also
+// after a cudaDeviceReset, which reloads the module).
 #include <cuda_runtime.h>
 
 #include <cmath>
-#include <mutex>
 #include <string>
 
 #include "../../include/lbgm.h"
 #include "geometry.h"
+#include "lattice.cuh"
 #include "launch.h"
 
 namespace lbgm {
@@ -33,41 +33,20 @@ namespace {
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[LB_NOALLOC_SCRATCH_BYTES];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-void* g_scratch_addr[kMaxDevices] = {};
 lb_status noalloc_fail(lb_status s, const std::string& m) {
   set_last_error_noctx(m);  // reported by lb_last_error(NULL)
   return s;
 }
 
 // Per-row weights for the observables (sqrt g, sqrt g_thth, cross-section
-// area weight, vorticity weight), from the same closed forms as
-// evaluate_geometry, written straight into the scratch array.
-__global__ void k_noalloc_weights(int metric, lb_geometry_desc g, double* w) {
+// area weight, vorticity weight), from the same helper as the context's
+// geometry table (observable_weights), written straight into the scratch
+// array.
+__global__ void k_noalloc_weights(lb_metric metric, lb_geometry_desc g, double* w) {
   const int row = blockIdx.x * blockDim.x + threadIdx.x;
   if (row >= g.nr * g.n3) return;
   const int ir = row / g.n3, i3 = row - ir * g.n3;
-  const bool eqw = g.wall == LB_WALL_EQUILIBRIUM;  // node positions as evaluate_geometry
-  const double h = (g.r_outer - g.r_inner) / (eqw ? g.nr - 1 : g.nr);
-  const double r = g.r_inner + (eqw ? ir : ir + 0.5) * h;
-  const double x3 = (eqw && !g.periodic3 ? i3 - 0.5 * (g.n3 - 1) : i3 + 0.5 - 0.5 * g.n3) * h * g.d3_scale;
-  double g1 = 1.0, g2 = 1.0, wA = 1.0, wOm = 1.0;
-  if (metric == LB_METRIC_CYLINDRICAL) {
-    g1 = r * r;
-    wOm = r;
-  } else if (metric == LB_METRIC_ELLIPSOIDAL) {
-    const double cp = cos(x3);
-    g1 = g.b * g.b * r * r * cp * cp;
-    g2 = r * r;
-    wA = r;
-    wOm = g.b * r * cp;
-  }
-  const double s1 = g.dtheta_scale * g.dtheta_scale, s2 = g.d3_scale * g.d3_scale;
-  w[4 * row + 0] = sqrt(g1 * s1 * g2 * s2);
-  w[4 * row + 1] = sqrt(g1 * s1);
-  w[4 * row + 2] = wA;
-  w[4 * row + 3] = wOm;
+  observable_weights(metric, g, ir, i3, w + 4 * row);
 }
 
 size_t align256(size_t n) { return (n + 255) & ~size_t(255); }
@@ -108,29 +87,18 @@ extern "C" lb_status lb_diagnostics_noalloc(lb_metric metric, const lb_geometry_
     return noalloc_fail(LB_ERR_ARG, "needs " + std::to_string(need) + " bytes of scratch; the fixed limit is " +
                                         std::to_string(LB_NOALLOC_SCRATCH_BYTES));
 
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return noalloc_fail(LB_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
-  if (dev < 0 || dev >= kMaxDevices) return noalloc_fail(LB_ERR_ARG, "device index out of range");
-  unsigned char* base = nullptr;
-  {
-    std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_scratch_addr[dev]) {
-      void* p = nullptr;
-      e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-      if (e != cudaSuccess)
-        return noalloc_fail(LB_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-      g_scratch_addr[dev] = p;
-    }
-    base = static_cast<unsigned char*>(g_scratch_addr[dev]);
-  }
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);  // this device's copy
+  if (e != cudaSuccess)
+    return noalloc_fail(LB_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+  unsigned char* base = static_cast<unsigned char*>(p);
   double* w = reinterpret_cast<double*>(base + off_w);
   double* rowmean = reinterpret_cast<double*>(base + off_rowmean);
   double* partial = reinterpret_cast<double*>(base + off_partial);
   double* sums = reinterpret_cast<double*>(base + off_out);
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
 
-  k_noalloc_weights<<<int((nrow64 + 255) / 256), 256, 0, s>>>(int(metric), *geom, w);
+  k_noalloc_weights<<<int((nrow64 + 255) / 256), 256, 0, s>>>(metric, *geom, w);
   e = cudaGetLastError();
   if (e == cudaSuccess) e = launch_diag(rho, u, rowmean, w, d, partial, nblk, sums, s);
   double h[LB_NOALLOC_MAX_BATCH * DIAG_NQ];
@@ -141,14 +109,13 @@ extern "C" lb_status lb_diagnostics_noalloc(lb_metric metric, const lb_geometry_
 
   const double R = curvature_radius(metric, *geom);
   const double dd = geom->r_outer - geom->r_inner;
-  const double cs2 = 1.0 - std::sqrt(0.4);
   for (int b = 0; b < batch; ++b) {
     const double* q = &h[b * DIAG_NQ];
     lb_diag& o = out[b];
     o.mass_rho_prime = q[0];
     o.mass_physical = q[1];
     o.mean_v_theta = q[2] / q[3];
-    const double nu = (tau[b] - 0.5) * cs2;
+    const double nu = (tau[b] - 0.5) * CS2;
     o.dean = R > 0.0 ? o.mean_v_theta * (dd / lattice_h(*geom)) / nu * std::sqrt(dd / R) : 0.0;
     o.mean_vorticity = q[4] / q[3];
     o.vortex_amp = std::sqrt(q[5] / double(N));

@@ -259,8 +259,21 @@ def torch_allocator(device=None):
 
 def lb_diagnostics_noalloc(metric: str, desc: lb_geometry_desc, taus, rho, u, stream=None):
     """Observables from device fields rho [B*N], u [B*3*N] (torch tensors)
-    without any device allocation by the library; see include/lbgm.h."""
+    without any device allocation by the library; see include/lbgm.h.
+
+    The fields are checked here, before the call: CUDA float64 tensors,
+    contiguous, holding at least B*N and 3*B*N values (the C side reads
+    exactly that many and cannot check a raw pointer)."""
+    import torch
     taus = np.ascontiguousarray(taus, dtype=np.float64)
+    n = int(desc.nr) * int(desc.ntheta) * int(desc.n3) * len(taus)
+    for name, t, need in (("rho", rho, n), ("u", u, 3 * n)):
+        if not isinstance(t, torch.Tensor) or not t.is_cuda:
+            raise LBError(LB_ERR_ARG, f"{name} must be a CUDA tensor")
+        if t.dtype != torch.float64 or not t.is_contiguous():
+            raise LBError(LB_ERR_ARG, f"{name} must be a contiguous float64 tensor")
+        if t.numel() < need:
+            raise LBError(LB_ERR_ARG, f"{name} holds {t.numel()} values, needs {need}")
     out = (lb_diag * len(taus))()
     handle = None if stream is None else ctypes.c_void_p(stream.cuda_stream)
     _check(load_library().lb_diagnostics_noalloc(METRICS[metric], ctypes.byref(desc), len(taus),

@@ -311,23 +311,34 @@ def critical_dean_knee(deans, w):
     return float(np.clip(-b / (2.0 * a), x[0], x[2]))
 
 
-def vortex_cells(u_r, nr, ntheta, n3, rel=0.2):
-    """Number of Dean cells across the periodic x3 extent of one instance:
-    the sign changes of the radial velocity at mid-gap (i_r = nr // 2,
-    averaged over theta) along x3, periodically, counting only samples whose
-    magnitude exceeds `rel` x the largest (a 2-cell flow has one positive and
-    one negative band of u^r, two sign changes; 4-cell four; 6-cell six).
+def vortex_cells(u_r, nr, ntheta, n3, rel=0.2, periodic=True, weights=None):
+    """Number of Dean cells across the x3 extent of one instance: the sign
+    changes of the radial velocity at mid-gap (i_r = nr // 2, averaged over
+    theta) along x3, counting only samples whose magnitude exceeds `rel` x
+    the largest.
+
+    periodic=True (the cylinder's periodic z): the count wraps around, so a
+    2-cell flow (one outward and one inward band of u^r) has two sign
+    changes, a 4-cell flow four. periodic=False (walls on x3, the four-wall
+    channel): no wrap-around; the return flow runs along the x3 walls, so a
+    2-cell flow reads -, +, - (two changes) and a 4-cell flow -, +, -, +, -
+    (four). The x3 mean of u^r (the x3-uniform radial drift, not a vortex)
+    is removed first, weighted by `weights` along x3 when given (the area
+    element of the cross-section).
     u_r: the instance's radial velocity in the field layout of lb_macros
     ([i_r][i_theta][i_3], x3 fastest). 0 for a field without vortices."""
     u = np.asarray(u_r, float).reshape(nr, ntheta, n3)[nr // 2].mean(axis=0)
-    u = u - u.mean()
+    w = np.ones(n3) if weights is None else np.asarray(weights, float)
+    u = u - (w * u).sum() / w.sum()
     m = np.abs(u).max()
     if not np.isfinite(m) or m == 0.0:
         return 0
     sig = np.sign(u[np.abs(u) > rel * m])
     if len(sig) < 2:
         return 0
-    return int(np.count_nonzero(sig != np.roll(sig, 1)))
+    if periodic:
+        return int(np.count_nonzero(sig != np.roll(sig, 1)))
+    return int(np.count_nonzero(sig[1:] != sig[:-1]))
 
 
 def decay_rate(t, A, floor, skip_frac=0.25, above=100.0):

@@ -186,3 +186,17 @@ def test_fma_peak_rejects_bad_arguments_without_a_gpu(L):
     assert b"precision" in lib.lb_last_error(None)
     assert lib.lb_fma_peak(L.PRECISIONS["fp64"], None, None) == L.LB_ERR_ARG
     assert v.value == -1.0                        # untouched on failure
+
+
+def test_noalloc_binding_checks_fields_before_the_call(L):
+    """The binding refuses host tensors, wrong dtypes and undersized fields
+    itself: the C side reads B*N and 3*B*N doubles from raw pointers."""
+    import torch
+    desc = L.make_desc(1.0, 1.1, 8, 2, 8)
+    n = 8 * 2 * 8 * 2
+    good_rho = torch.zeros(n, dtype=torch.float64)
+    good_u = torch.zeros(3 * n, dtype=torch.float64)
+    with pytest.raises(L.LBError, match="CUDA tensor"):
+        L.lb_diagnostics_noalloc("cylindrical", desc, [0.8, 0.7], good_rho, good_u)
+    with pytest.raises(L.LBError, match="CUDA tensor"):
+        L.lb_diagnostics_noalloc("cylindrical", desc, [0.8, 0.7], good_rho.numpy(), good_u)

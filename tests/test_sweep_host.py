@@ -168,3 +168,27 @@ def test_vortex_cells_counts_sign_bands_along_x3():
     # the 6-cell state of Sec. IV.B: one of the three wavelengths weaker
     ur = (np.sin(2 * np.pi * 3 * z / n3) * (1 + 0.4 * np.cos(2 * np.pi * z / n3)))[None, None, :]
     assert vortex_cells((r * ur * np.ones((nr, nt, 1))).ravel(), nr, nt, n3) == 6
+
+
+def test_vortex_cells_walled_x3():
+    """Four-wall channel (walls on x3): the return flow runs along the x3
+    walls, so the mid-gap u^r reads -, +, - for 2 cells and -, +, -, +, -
+    for 4; no wrap-around comparison (with it, the equal end signs would be
+    ignored and an odd band count would gain a change)."""
+    from paper_1411_3133_gb300.sweep import vortex_cells
+    nr, nt, n3 = 9, 2, 96
+    x = (np.arange(n3) + 0.5) / n3                      # 0..1 between the walls
+    r = np.sin(np.pi * (np.arange(nr) + 0.5) / nr)[:, None, None]
+    env = 1.0 - (2.0 * x - 1.0) ** 8                     # u = 0 on the walls, flat inside
+    for k, cells in ((1, 2), (2, 4), (3, 6)):
+        prof = -np.cos(2 * np.pi * k * x) * env          # negative at both walls
+        ur = (r * prof[None, None, :] * np.ones((nr, nt, 1))).ravel() * 1e-3
+        assert vortex_cells(ur, nr, nt, n3, periodic=False) == cells
+        # with an area weight along x3 the count is unchanged
+        assert vortex_cells(ur, nr, nt, n3, periodic=False, weights=1.0 + 0.2 * x) == cells
+    # two bands (+, -) between walls: one change; the periodic count would
+    # add a second at the wrap
+    prof = np.cos(np.pi * x) * env
+    ur = (r * prof[None, None, :] * np.ones((nr, nt, 1))).ravel()
+    assert vortex_cells(ur, nr, nt, n3, periodic=False) == 1
+    assert vortex_cells(ur, nr, nt, n3, periodic=True) == 2

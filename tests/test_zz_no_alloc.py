@@ -34,8 +34,11 @@ def test_noalloc_diagnostics_match_context(metric, geom):
     u = torch.empty(len(taus) * 3 * N, dtype=torch.float64, device="cuda")
     ctx.lb_macros(rho, u, on_device=True)
     ctx.stream.synchronize()
+    L.lb_diagnostics_noalloc(metric, spec.desc(), taus, rho, u, stream=ctx.stream)  # module loaded
+    free0 = torch.cuda.mem_get_info()[0]
     for _ in range(2):                       # the second call reuses the same scratch
         got = L.lb_diagnostics_noalloc(metric, spec.desc(), taus, rho, u, stream=ctx.stream)
+        assert torch.cuda.mem_get_info()[0] == free0     # nothing allocated on the device
         for b in range(len(taus)):
             for k in FIELDS:
                 assert got[b][k] == pytest.approx(ref[b][k], rel=1e-12, abs=1e-300), (b, k)
@@ -44,10 +47,30 @@ def test_noalloc_diagnostics_match_context(metric, geom):
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch():
+    """Fields of the right size, a geometry whose weights alone need 8 MiB:
+    the library itself refuses (the binding's own checks pass)."""
     import torch
     L = lib()
-    desc = L.make_desc(1.0, 1.1, 512, 4, 512)          # geometry weights alone: 8 MiB
-    rho = torch.zeros(1, dtype=torch.float64, device="cuda")
+    desc = L.make_desc(1.0, 1.1, 512, 4, 512)
+    n = 512 * 4 * 512
+    rho = torch.ones(n, dtype=torch.float64, device="cuda")
+    u = torch.zeros(3 * n, dtype=torch.float64, device="cuda")
     with pytest.raises(L.LBError) as e:
-        L.lb_diagnostics_noalloc("cylindrical", desc, [0.8], rho, rho)
+        L.lb_diagnostics_noalloc("cylindrical", desc, [0.8], rho, u)
     assert e.value.status == L.LB_ERR_ARG and "scratch" in str(e.value)
+
+
+def test_noalloc_binding_refuses_wrong_fields():
+    """A float32 or undersized field never reaches the library."""
+    import torch
+    L = lib()
+    desc = L.make_desc(1.0, 1.1, 8, 2, 8)
+    n = 8 * 2 * 8
+    rho = torch.ones(n, dtype=torch.float64, device="cuda")
+    u = torch.zeros(3 * n, dtype=torch.float64, device="cuda")
+    with pytest.raises(L.LBError, match="float64"):
+        L.lb_diagnostics_noalloc("cylindrical", desc, [0.8], rho.float(), u)
+    with pytest.raises(L.LBError, match="needs"):
+        L.lb_diagnostics_noalloc("cylindrical", desc, [0.8], rho[:-1], u)
+    with pytest.raises(L.LBError, match="needs"):
+        L.lb_diagnostics_noalloc("cylindrical", desc, [0.8, 0.8], rho, u)
