@@ -181,10 +181,6 @@ typedef enum {
                                from global memory; 2: the TMA-pipelined
                                kernel (FP32, bounce-back walls and n3 in
                                {128, 256} only);
-                               3: the prefetching kernel: each thread updates
-                               LB_OPT_NODES_PER_THREAD nodes and copies the
-                               next node's sources into shared memory
-                               (cp.async) while it computes the current one;
                                4: the region split (periodic x3 and
                                bounce-back walls only): one
                                kernel for the 3 node layers next to each
@@ -204,8 +200,11 @@ typedef enum {
                                blocks per SM) x (SMs) blocks that walks the
                                tile list. Both give bitwise identical
                                states. */
-  LB_OPT_NODES_PER_THREAD = 5, /* nodes per thread of the prefetching step
-                               kernel (1..64; default 4) */
+  LB_OPT_TILE_BLOCKS = 5,   /* batches only (lb_batch_set_option): nodes per
+                               work-list tile, in blocks' worth: 1
+                               (default), 2 or 4; each thread of a tile's
+                               block takes every blockDim-th node of it.
+                               Bitwise neutral. */
   LB_OPT_STORAGE_REFERENCE = 6 /* FP16/BF16 storage only: the reference
                                r_l of the stored deviation (f_l - r_l)/w_l.
                                0: r_l = w_l (the rest state of unit
@@ -226,9 +225,10 @@ typedef enum {
 /* One configuration measured by lb_autotune / lb_batch_autotune. */
 typedef struct {
   int block_threads;   /* LB_OPT_BLOCK_THREADS */
-  int schedule;        /* contexts: LB_OPT_STEP_KERNEL (1, 2 or 3);
+  int schedule;        /* contexts: LB_OPT_STEP_KERNEL (1, 2, 4 or 5);
                           batches: LB_OPT_SCHEDULE (0 or 1) */
-  int nodes_per_thread; /* LB_OPT_NODES_PER_THREAD (prefetching kernel) */
+  int tile_nodes;      /* batches: nodes per work-list tile (block_threads x
+                          LB_OPT_TILE_BLOCKS); contexts: 0 */
   double ms_per_step;  /* measured with CUDA events on the stream */
 } lb_tune;
 
@@ -381,10 +381,8 @@ lb_status lb_fma_peak(lb_precision precision, void* cuda_stream, double* flops_p
 /* Autotuner of the step launch. Runs steps_per_trial (>= 1) time steps in
  * each configuration -- block_threads in {64, 96, 128} (FP64: {64, 128, 192,
  * 256}) with the plain step kernel, {64, 96, 128} with the region split
- * where x3 is periodic and with the tiled step, the TMA kernel where the
- * context supports it, and the
- * prefetching kernel with block_threads in {128, 256} x
- * nodes_per_thread in {2, 4, 8} -- timed with
+ * where x3 is periodic and with the tiled step, and the TMA kernel where the
+ * context supports it -- timed with
  * CUDA events on the context's stream, then keeps the fastest. Every
  * configuration computes bitwise the same states, so the trial steps are
  * real time steps: they advance the simulation and the step count. best
@@ -431,13 +429,15 @@ lb_status lb_batch_create(lb_ctx* const* members, int count, lb_batch** out);
 
 /* n >= 0 time steps of every member (each must be initialised). Options:
  * LB_OPT_CHECK_EVERY, LB_OPT_BLOCK_THREADS, LB_OPT_USE_GRAPH (a captured
- * graph of two batch steps), LB_OPT_SCHEDULE. A non-finite density found by
+ * graph of two batch steps), LB_OPT_SCHEDULE, LB_OPT_TILE_BLOCKS. A
+ * non-finite density found by
  * a check poisons that member and returns LB_ERR_NONFINITE. */
 lb_status lb_batch_step(lb_batch* batch, long long n);
 lb_status lb_batch_set_option(lb_batch* batch, int option, long long value);
 
 /* As lb_autotune over block_threads in {64, 96, 128} (FP64: {64, 96, 128,
- * 192, 256}) x LB_OPT_SCHEDULE in {0, 1}; the trial steps are real batch
+ * 192, 256}) x LB_OPT_SCHEDULE in {0, 1} x LB_OPT_TILE_BLOCKS in {1, 2, 4}
+ * (the tile length: nodes per work-list item); the trial steps are real batch
  * steps. With FP32 arithmetic the work-list kernel runs at most 128 threads
  * per block (LB_OPT_BLOCK_THREADS above that runs as 128). */
 lb_status lb_batch_autotune(lb_batch* batch, int steps_per_trial, lb_tune* best, lb_tune* trials,
@@ -457,20 +457,21 @@ const char* lb_batch_last_error(const lb_batch* batch);
 
 /* --------------------------------------------------------------------- */
 /* Surrogate of developed channel flow, for warm starts (no counterpart in
- * the paper). A multilayer perceptron maps x = (De, r, z) -- a Dean number
- * and a node's position, each scaled by the caller (typically De / 100,
- * (r - r_i)/d and x3 / L_3 in [0, 1)) -- to the node's fields y = (rho',
- * u^r, u^theta, u^3) of a converged LB run. Features (De, r, sin(2 pi k z),
- * cos(2 pi k z), k = 1..n_fourier) feed depth - 1 hidden layers of `width`
- * SiLU units and a linear layer of 4 outputs, which predicts (y - mean)/std
- * per field (lb_mlp_set_output_scale). Weights: FP32 master copy and Adam
- * moments, BF16 in every product, FP32 accumulation; He-uniform initial
- * weights from a SplitMix64 stream seeded with `seed`, zero biases.
- * Parameters are laid out layer by layer as W (fan_out x fan_in, row-major)
- * then b. All x, y arrays are device FP32, row-major ([n][3], [n][4]);
- * calls are ordered on `cuda_stream` (NULL: legacy default stream). */
+ * the paper). A multilayer perceptron maps an input row x = (p_1 .. p_P, z)
+ * -- n_plain = P channel parameters and coordinates, each scaled by the
+ * caller (typically De / 100, a curvature ratio, (r - r_i)/d), then x3 / L_3
+ * in [0, 1) -- to the node's fields y = (rho', u^r, u^theta, u^3) of a
+ * converged LB run. Features (p_1 .. p_P, sin(2 pi k z), cos(2 pi k z), k =
+ * 1..n_fourier) feed depth - 1 hidden layers of `width` SiLU units and a
+ * linear layer of 4 outputs, which predicts (y - mean)/std per field
+ * (lb_mlp_set_output_scale). Weights: FP32 master copy and Adam moments,
+ * BF16 in every product, FP32 accumulation; He-uniform initial weights from
+ * a SplitMix64 stream seeded with `seed`, zero biases. Parameters are laid
+ * out layer by layer as W (fan_out x fan_in, row-major) then b. All x, y
+ * arrays are device FP32, row-major ([n][n_plain + 1], [n][4]); calls are
+ * ordered on `cuda_stream` (NULL: legacy default stream). */
 typedef struct lb_mlp lb_mlp;
-lb_status lb_mlp_create(int n_fourier, int width, int depth, int max_batch, unsigned long long seed,
+lb_status lb_mlp_create(int n_plain, int n_fourier, int width, int depth, int max_batch, unsigned long long seed,
                         void* cuda_stream, lb_mlp** out);
 size_t lb_mlp_param_count(const lb_mlp* net);
 /* host arrays mean[4], std[4] (std > 0) */

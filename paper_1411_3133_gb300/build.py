@@ -20,7 +20,7 @@ LIB_DIR = os.path.join(HERE, "_lib")
 LIB_PATH = os.path.join(LIB_DIR, "liblbgm.so")
 
 SOURCES = ["api.cu", "aux.cu", "step_f64.cu", "step_f32.cu", "step_h16.cu", "step_b16.cu",
-           "step_tma.cu", "step_async.cu", "noalloc.cu", "batch.cu", "mlp.cu", "probe.cu", "step_shift.cu", "geometry.cpp"]
+           "step_tma.cu", "noalloc.cu", "batch.cu", "mlp.cu", "probe.cu", "step_shift.cu", "geometry.cpp"]
 HEADERS = ["lattice.cuh", "lbm_device.cuh", "kernels.cuh", "step_launch.cuh", "launch.h", "geometry.h",
            "ctx.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

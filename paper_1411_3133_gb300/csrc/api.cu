@@ -253,24 +253,7 @@ lb_status launch_step_once(lb_ctx* c) {
   const int src = c->cur, dst = 1 - c->cur;
   const int kern = resolved_kernel(c);
   cudaError_t e;
-  if (kern == 3 && c->prec == LB_FP32)
-    e = launch_step_async_f32(c->K, static_cast<const float*>(c->f[src]), static_cast<float*>(c->f[dst]),
-                              c->geo_f, static_cast<const InstParams<float>*>(c->inst), c->dims, c->flag,
-                              c->block_threads, c->nodes_per_thread, c->stream);
-  else if (kern == 3 && c->prec == LB_FP64)
-    e = launch_step_async_f64(c->K, static_cast<const double*>(c->f[src]), static_cast<double*>(c->f[dst]),
-                              c->geo_d, static_cast<const InstParams<double>*>(c->inst), c->dims, c->flag,
-                              c->block_threads, c->nodes_per_thread, c->stream);
-  else if (kern == 3 && c->prec == LB_FP16_SHIFTED)
-    e = launch_step_async_h16(c->K, static_cast<const __half*>(c->f[src]), static_cast<__half*>(c->f[dst]),
-                              c->geo_f, static_cast<const InstParams<float>*>(c->inst), c->dims, c->flag,
-                              c->block_threads, c->nodes_per_thread, c->stream);
-  else if (kern == 3)
-    e = launch_step_async_b16(c->K, static_cast<const __nv_bfloat16*>(c->f[src]),
-                              static_cast<__nv_bfloat16*>(c->f[dst]), c->geo_f,
-                              static_cast<const InstParams<float>*>(c->inst), c->dims, c->flag,
-                              c->block_threads, c->nodes_per_thread, c->stream);
-  else if (kern == 4)
+  if (kern == 4)
     e = launch_split(c, src, dst);
   else if (kern == 5) {
     lb_status st = ctx_tiled_prepare(c);  // a no-op once the tiles are current
@@ -463,9 +446,8 @@ lb_status lb_create_geometry(lb_metric metric, const lb_geometry_desc* geom, int
   const size_t nrows = size_t(geom->nr) * d.geo_rows3;
   const size_t nrow64 = size_t(geom->nr) * geom->n3;
   c->nblk = int(std::min<size_t>(1024, (c->ncell + 255) / 256));
-  // 16 bytes of padding: the prefetching kernel copies whole 4-byte words
-  c->f[0] = dalloc(c, c->state_elems * c->elem_bytes + 16);
-  c->f[1] = dalloc(c, c->state_elems * c->elem_bytes + 16);
+  c->f[0] = dalloc(c, c->state_elems * c->elem_bytes);
+  c->f[1] = dalloc(c, c->state_elems * c->elem_bytes);
   c->geo_real = dalloc(c, 9 * nrows * (prec == LB_FP64 ? sizeof(double) : sizeof(float)));
   c->geo64 = static_cast<double*>(dalloc(c, nrow64 * 4 * sizeof(double)));
   c->sqrtg = static_cast<double*>(dalloc(c, nrow64 * sizeof(double)));
@@ -478,10 +460,14 @@ lb_status lb_create_geometry(lb_metric metric, const lb_geometry_desc* geom, int
   c->partial = static_cast<double*>(dalloc(c, size_t(batch) * c->nblk * DIAG_NQ * sizeof(double)));
   c->diag_out = static_cast<double*>(dalloc(c, size_t(batch) * DIAG_NQ * sizeof(double)));
   c->flag = static_cast<int*>(dalloc(c, sizeof(int)));
+  d.st_rows3 = c->K == KELL ? d.geo_rows3 : (d.periodic3 ? 1 : 7);
   if (c->elem_bytes == 2) {
     c->ref_tab = static_cast<float*>(dalloc(c, size_t(batch) * Q * nrows * sizeof(float)));
-    if (!c->ref_tab) return bail(LB_ERR_CUDA, "device allocation failed");
+    c->st_tab = static_cast<float4*>(
+        dalloc(c, size_t(batch) * ST_K * size_t(geom->nr) * size_t(d.st_rows3) * sizeof(float4)));
+    if (!c->ref_tab || !c->st_tab) return bail(LB_ERR_CUDA, "device allocation failed");
     d.ref = c->ref_tab;
+    d.st = c->st_tab;
   }
   if (!c->f[0] || !c->f[1] || !c->geo_real || !c->geo64 || !c->sqrtg || !c->base_uth || !c->ini ||
       !c->inst || !c->rho_s || !c->u_s || !c->rowmean || !c->partial || !c->diag_out || !c->flag)
@@ -562,9 +548,12 @@ lb_status lb_init(lb_ctx* c, const lb_params* p) {
   LB_CUDA(c, cudaMemcpyAsync(c->ini, ini.data(), ini.size() * sizeof(InitInst), cudaMemcpyHostToDevice,
                              c->stream));
   c->cur = 0;
-  if (c->ref_tab)
+  if (c->ref_tab) {
     LB_CUDA(c, launch_ref_table(c->K, c->ref_tab, c->geo_f, c->sqrtg, any_base ? c->base_uth : nullptr, nullptr,
                                 nullptr, c->dims, c->ref_mode, c->stream));
+    LB_CUDA(c, launch_stream_table(int(c->prec), c->K, c->st_tab, c->ref_tab,
+                                   static_cast<const InstParams<float>*>(c->inst), c->f[0], c->dims, c->stream));
+  }
   LB_CUDA(c, launch_init(int(c->prec), c->K, c->f[0], geo_ptr(c), c->sqrtg,
                          any_base ? c->base_uth : nullptr, c->ini, nullptr, nullptr, c->dims, c->stream));
   return reset_after_init(c);
@@ -584,9 +573,12 @@ lb_status lb_init_fields(lb_ctx* c, const lb_params* p, const double* rho, const
     du = c->u_s;
   }
   c->cur = 0;
-  if (c->ref_tab)
+  if (c->ref_tab) {
     LB_CUDA(c, launch_ref_table(c->K, c->ref_tab, c->geo_f, c->sqrtg, nullptr, drho, du, c->dims, c->ref_mode,
                                 c->stream));
+    LB_CUDA(c, launch_stream_table(int(c->prec), c->K, c->st_tab, c->ref_tab,
+                                   static_cast<const InstParams<float>*>(c->inst), c->f[0], c->dims, c->stream));
+  }
   LB_CUDA(c, launch_init(int(c->prec), c->K, c->f[0], geo_ptr(c), c->sqrtg, nullptr, c->ini,
                          drho, du, c->dims, c->stream));
   return reset_after_init(c);
@@ -610,8 +602,7 @@ lb_status lb_step(lb_ctx* c, long long n) {
     // the captured kernels depend on the resolved step kernel and on whether
     // an instance uses the half-force variant (both can change with lb_init)
     const int gk = 2 * resolved_kernel(c) + (c->any_shift ? 1 : 0);
-    if (!c->graph || c->graph_threads != c->block_threads || c->graph_kernel != gk ||
-        c->graph_npt != c->nodes_per_thread) {
+    if (!c->graph || c->graph_threads != c->block_threads || c->graph_kernel != gk) {
       if (c->graph) cudaGraphExecDestroy(c->graph);
       c->graph = nullptr;
       cudaGraph_t g = nullptr;
@@ -626,7 +617,6 @@ lb_status lb_step(lb_ctx* c, long long n) {
       if (e != cudaSuccess) return cuda_fail(c, e, "cudaGraphInstantiate");
       c->graph_threads = c->block_threads;
       c->graph_kernel = gk;
-      c->graph_npt = c->nodes_per_thread;
     }
     for (long long i = 0; i + 1 < n; i += 2) {
       LB_CUDA(c, cudaGraphLaunch(c->graph, c->stream));
@@ -746,6 +736,8 @@ lb_status lb_capture_reference(lb_ctx* c) {
   // decode with the old table, average, re-encode with the new one
   LB_CUDA(c, launch_convert(int(c->prec), 1, c->f[c->cur], c->dbl_stage, n, c->dims, c->stream));
   LB_CUDA(c, launch_ref_from_state(c->dbl_stage, c->ref_tab, c->dims, c->stream));
+  LB_CUDA(c, launch_stream_table(int(c->prec), c->K, c->st_tab, c->ref_tab,
+                                 static_cast<const InstParams<float>*>(c->inst), c->f[0], c->dims, c->stream));
   LB_CUDA(c, launch_convert(int(c->prec), 0, c->f[c->cur], c->dbl_stage, n, c->dims, c->stream));
   LB_CUDA(c, cudaStreamSynchronize(c->stream));
   return LB_OK;
@@ -815,18 +807,13 @@ lb_status lb_set_option(lb_ctx* c, int option, long long value) {
       c->use_graph = value ? 1 : 0;
       return LB_OK;
     case LB_OPT_STEP_KERNEL:
-      if (value < 0 || value > 5)
-        return fail(c, LB_ERR_ARG,
-                    "need 0 (auto), 1 (plain), 2 (TMA), 3 (prefetching), 4 (region split) or 5 (tiled)");
+      if (value < 0 || value > 5 || value == 3)
+        return fail(c, LB_ERR_ARG, "need 0 (auto), 1 (plain), 2 (TMA), 4 (region split) or 5 (tiled)");
       if (value == 4 && (!c->geom.periodic3 || c->geom.wall != LB_WALL_BOUNCEBACK))
         return fail(c, LB_ERR_ARG, "the region-split step kernel needs a periodic x3 axis and bounce-back walls");
       if (value == 2 && !c->tma_ok)
         return fail(c, LB_ERR_ARG, "the TMA step kernel needs FP32 and n3 in {128, 256}");
       c->step_kernel = int(value);
-      return LB_OK;
-    case LB_OPT_NODES_PER_THREAD:
-      if (value < 1 || value > 64) return fail(c, LB_ERR_ARG, "need 1..64 nodes per thread");
-      c->nodes_per_thread = int(value);
       return LB_OK;
     case LB_OPT_STORAGE_REFERENCE:
       if (value < 0 || value > 1) return fail(c, LB_ERR_ARG, "need 0 (weights) or 1 (initial rows)");
@@ -857,8 +844,6 @@ lb_status lb_autotune(lb_ctx* c, int steps_per_trial, lb_tune* best, lb_tune* tr
       for (int t : {64, 96, 128}) cand.push_back({t, 4, 0, 0.0});
     for (int t : {64, 96, 128}) cand.push_back({t, 5, 0, 0.0});
     if (c->tma_ok) cand.push_back({0, 2, 0, 0.0});  // the TMA kernel fixes its own block shape
-    for (int t : {128, 256})
-      for (int npt : {2, 4, 8}) cand.push_back({t, 3, npt, 0.0});
   }
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   LB_CUDA(c, cudaEventCreate(&e0));
@@ -867,12 +852,11 @@ lb_status lb_autotune(lb_ctx* c, int steps_per_trial, lb_tune* best, lb_tune* tr
     cudaEventDestroy(e0);
     return cuda_fail(c, e, "cudaEventCreate");
   }
-  const int keep_threads = c->block_threads, keep_npt = c->nodes_per_thread;
+  const int keep_threads = c->block_threads;
   lb_status st = LB_OK;
   for (lb_tune& k : cand) {
     c->block_threads = k.block_threads > 0 ? k.block_threads : keep_threads;
     c->step_kernel = k.schedule;
-    c->nodes_per_thread = k.nodes_per_thread > 0 ? k.nodes_per_thread : keep_npt;
     for (int i = 0; i <= steps_per_trial && st == LB_OK; ++i) {  // step 0 is the untimed warm-up
       if (i == 1 && (e = cudaEventRecord(e0, c->stream)) != cudaSuccess) st = cuda_fail(c, e, "cudaEventRecord");
       if (st == LB_OK) st = launch_step_once(c);
@@ -895,11 +879,9 @@ lb_status lb_autotune(lb_ctx* c, int steps_per_trial, lb_tune* best, lb_tune* tr
   if (cand[ib].block_threads == 0) cand[ib].block_threads = keep_threads;
   for (lb_tune& k : cand) {
     if (k.block_threads == 0) k.block_threads = keep_threads;
-    if (k.nodes_per_thread == 0) k.nodes_per_thread = keep_npt;
   }
   c->block_threads = cand[ib].block_threads;
   c->step_kernel = cand[ib].schedule;
-  c->nodes_per_thread = cand[ib].nodes_per_thread;
   if (best) *best = cand[ib];
   const int n = int(cand.size());
   for (int i = 0; i < n && i < max_trials; ++i) trials[i] = cand[i];

@@ -366,6 +366,29 @@ cudaError_t launch_ref_table(int K, float* ref, const GeoDev<float>& geo, const 
   return cudaGetLastError();
 }
 
+template <class S>
+cudaError_t launch_stream_table_t(int K, float4* st, const float* ref, const InstParams<float>* inst,
+                                  const void* fin, const Dims& d, cudaStream_t s) {
+  const uint32_t n = uint32_t(d.batch) * uint32_t(d.nr) * uint32_t(d.st_rows3);
+  const uint32_t nb = (n + 127) / 128;
+  const S* f = static_cast<const S*>(fin);
+  switch (K) {
+    case KFLAT: k_stream_table<KFLAT, S><<<nb, 128, 0, s>>>(st, ref, inst, f, d); break;
+    case KCYL: k_stream_table<KCYL, S><<<nb, 128, 0, s>>>(st, ref, inst, f, d); break;
+    case KELL: k_stream_table<KELL, S><<<nb, 128, 0, s>>>(st, ref, inst, f, d); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_stream_table(int prec, int K, float4* st, const float* ref, const InstParams<float>* inst,
+                                const void* fin, const Dims& d, cudaStream_t s) {
+  if (!st || !ref || d.st != st) return cudaErrorInvalidValue;
+  if (prec == 2) return launch_stream_table_t<__half>(K, st, ref, inst, fin, d, s);
+  if (prec == 3) return launch_stream_table_t<__nv_bfloat16>(K, st, ref, inst, fin, d, s);
+  return cudaErrorInvalidValue;
+}
+
 cudaError_t launch_diag(const double* rho, const double* u, double* rowmean, const double* geo64,
                         const Dims& d, double* partial, int nblk, double* out, cudaStream_t s) {
   const int rows = d.batch * d.nr * d.nt;

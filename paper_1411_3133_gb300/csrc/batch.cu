@@ -36,15 +36,15 @@ struct Group {
 
 // Tiles of one instance (group-local index li): runs of interior nodes (no
 // wall within 3 nodes) as (li, first node, count), and the wall nodes' indices
-// appended to `cells` as (li, first index, count); counts <= threads.
-void instance_tiles(const Dims& d, int li, int threads, std::vector<int4>& interior, std::vector<int4>& wall,
+// appended to `cells` as (li, first index, count); counts <= tile.
+void instance_tiles(const Dims& d, int li, int tile, std::vector<int4>& interior, std::vector<int4>& wall,
                     std::vector<int>& cells) {
   const int nr = d.nr, nt = d.nt, n3 = d.n3;
   auto inner_r = [&](int ir) { return ir >= 3 && ir <= nr - 4; };
   auto inner_3 = [&](int i3) { return d.periodic3 || (i3 >= 3 && i3 <= n3 - 4); };
   int run_start = -1;
   auto close_run = [&](int end) {
-    for (int a = run_start; a < end; a += threads) interior.push_back(make_int4(li, a, std::min(threads, end - a), 0));
+    for (int a = run_start; a < end; a += tile) interior.push_back(make_int4(li, a, std::min(tile, end - a), 0));
     run_start = -1;
   };
   const size_t w0 = cells.size();
@@ -60,8 +60,8 @@ void instance_tiles(const Dims& d, int li, int threads, std::vector<int4>& inter
         }
       }
   if (run_start >= 0) close_run(nr * nt * n3);
-  for (size_t a = w0; a < cells.size(); a += size_t(threads))
-    wall.push_back(make_int4(li, int(a), int(std::min(size_t(threads), cells.size() - a)), 0));
+  for (size_t a = w0; a < cells.size(); a += size_t(tile))
+    wall.push_back(make_int4(li, int(a), int(std::min(size_t(tile), cells.size() - a)), 0));
 }
 
 }  // namespace
@@ -77,6 +77,7 @@ struct lb_batch {
   // work list, valid while built
   bool built = false;
   int built_threads = 0;
+  int built_tile_blocks = 0;
   std::vector<int> base_cur;  // member buffer parity when the records were written
   int parity = 0;             // batch steps since then, mod 2
   Group g[kMaxGroups];
@@ -89,11 +90,13 @@ struct lb_batch {
   cudaEvent_t ev_join[kMaxLanes - 1] = {};
 
   int threads = 128;
+  int tile_blocks = 1;  // LB_OPT_TILE_BLOCKS: nodes per tile = tile_blocks x threads
   int schedule = 0;
   int use_graph = 0;
   long long check_every = 0;
   cudaGraphExec_t graph = nullptr;  // two batch steps, parity 0 then 1
   int graph_threads = 0;
+  int graph_tile_blocks = 0;
   int graph_schedule = -1;
 
   long long step = 0;
@@ -131,6 +134,7 @@ ListInst<S, R> record(const lb_ctx* c, int bi, int cur, const GeoDev<R>& geo) {
   r.d = c->dims;
   r.d.batch = 1;
   if (c->dims.ref) r.d.ref = c->dims.ref + size_t(bi) * Q * size_t(c->dims.nr) * size_t(c->dims.geo_rows3);
+  if (c->dims.st) r.d.st = c->dims.st + size_t(bi) * ST_K * size_t(c->dims.nr) * size_t(c->dims.st_rows3);
   r.geo = geo;
   r.ip = static_cast<const InstParams<R>*>(c->inst) + bi;
   const size_t off = size_t(bi) * Q * c->ncell;
@@ -173,7 +177,8 @@ cudaError_t occupancy(lb_precision p, int K, int threads, int* out) {
 }
 
 // Write the instance records (with the members' current buffer parity) and
-// the tile lists for block size b->threads, and upload them.
+// the tile lists for block size b->threads (tiles of b->tile_blocks blocks'
+// worth of nodes), and upload them.
 lb_status build(lb_batch* b) {
   drop_graph(b);
   b->built = false;
@@ -199,7 +204,7 @@ lb_status build(lb_batch* b) {
     for (const lb_ctx* c : b->m) {
       if (c->K != K) continue;
       for (int bi = 0; bi < c->batch; ++bi, ++local)
-        instance_tiles(c->dims, local, b->threads, tiles[gi][0], tiles[gi][1], cells[gi]);
+        instance_tiles(c->dims, local, b->threads * b->tile_blocks, tiles[gi][0], tiles[gi][1], cells[gi]);
     }
     gr.nwork[0] = int(tiles[gi][0].size());
     gr.nwork[1] = int(tiles[gi][1].size());
@@ -242,6 +247,7 @@ lb_status build(lb_batch* b) {
   for (size_t i = 0; i < b->m.size(); ++i) b->base_cur[i] = b->m[i]->cur;
   b->parity = 0;
   b->built_threads = b->threads;
+  b->built_tile_blocks = b->tile_blocks;
   b->built = true;
   return LB_OK;
 }
@@ -249,7 +255,7 @@ lb_status build(lb_batch* b) {
 // The records hold f0 = the buffer each member read when they were written;
 // they stay valid while every member has taken exactly the batch's steps.
 bool records_current(const lb_batch* b) {
-  if (!b->built || b->built_threads != b->threads) return false;
+  if (!b->built || b->built_threads != b->threads || b->built_tile_blocks != b->tile_blocks) return false;
   for (size_t i = 0; i < b->m.size(); ++i)
     if (b->m[i]->cur != (b->base_cur[i] ^ b->parity)) return false;
   return true;
@@ -356,7 +362,8 @@ lb_status run(lb_batch* b, long long n, bool graph) {
       advance_members(b, 1);
       --n;
     }
-    if (!b->graph || b->graph_threads != b->threads || b->graph_schedule != b->schedule) {
+    if (!b->graph || b->graph_threads != b->threads || b->graph_schedule != b->schedule ||
+        b->graph_tile_blocks != b->tile_blocks) {
       drop_graph(b);
       cudaGraph_t g = nullptr;
       LB_BCUDA(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
@@ -369,6 +376,7 @@ lb_status run(lb_batch* b, long long n, bool graph) {
       cudaGraphDestroy(g);
       if (e != cudaSuccess) return bcuda(b, e, "cudaGraphInstantiate");
       b->graph_threads = b->threads;
+      b->graph_tile_blocks = b->tile_blocks;
       b->graph_schedule = b->schedule;
     }
     const long long pairs = n / 2;
@@ -488,6 +496,10 @@ lb_status lb_batch_set_option(lb_batch* b, int option, long long value) {
       if (value < 0 || value > 1) return bfail(b, LB_ERR_ARG, "need 0 (tile per block) or 1 (persistent)");
       b->schedule = int(value);
       return LB_OK;
+    case LB_OPT_TILE_BLOCKS:
+      if (value != 1 && value != 2 && value != 4) return bfail(b, LB_ERR_ARG, "need 1, 2 or 4 blocks per tile");
+      b->tile_blocks = int(value);
+      return LB_OK;
     default:
       return bfail(b, LB_ERR_ARG, "option not available for batches");
   }
@@ -502,7 +514,8 @@ lb_status lb_batch_autotune(lb_batch* b, int steps_per_trial, lb_tune* best, lb_
   std::vector<lb_tune> cand;
   for (int t : {64, 96, 128, 192, 256})
     if (t <= max_threads(b->prec))
-      for (int sc : {0, 1}) cand.push_back({t, sc, 0, 0.0});
+      for (int sc : {0, 1})
+        for (int tb : {1, 2, 4}) cand.push_back({t, sc, t * tb, 0.0});
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   LB_BCUDA(b, cudaEventCreate(&e0));
   cudaError_t e = cudaEventCreate(&e1);
@@ -515,6 +528,7 @@ lb_status lb_batch_autotune(lb_batch* b, int steps_per_trial, lb_tune* best, lb_
   for (lb_tune& k : cand) {
     b->threads = k.block_threads;
     b->schedule = k.schedule;
+    b->tile_blocks = k.tile_nodes / k.block_threads;
     s = run(b, 1, false);  // rebuilds the tiles for this block size; untimed
     if (s != LB_OK) break;
     if ((e = cudaEventRecord(e0, b->stream)) != cudaSuccess) {
@@ -542,6 +556,7 @@ lb_status lb_batch_autotune(lb_batch* b, int steps_per_trial, lb_tune* best, lb_
     if (cand[i].ms_per_step < cand[ib].ms_per_step) ib = i;
   b->threads = cand[ib].block_threads;
   b->schedule = cand[ib].schedule;
+  b->tile_blocks = cand[ib].tile_nodes / cand[ib].block_threads;
   if (best) *best = cand[ib];
   const int n = int(cand.size());
   for (int i = 0; i < n && i < max_trials; ++i) trials[i] = cand[i];

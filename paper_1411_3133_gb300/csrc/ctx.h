@@ -46,6 +46,7 @@ struct lb_ctx {
   double* diag_out = nullptr;      // [batch * DIAG_NQ]
   double* dbl_stage = nullptr;     // conversion staging (FP32 populations), lazily allocated
   float* ref_tab = nullptr;        // 2-byte storage: reference populations [batch][Q][rows]
+  float4* st_tab = nullptr;        // 2-byte storage: stream table [batch][ST_K][stream rows]
   int ref_mode = 1;                // LB_OPT_STORAGE_REFERENCE
   int* flag = nullptr;
   int nblk = 0;
@@ -65,8 +66,6 @@ struct lb_ctx {
   int graph_kernel = -1;             // 2 x resolved step kernel + any_shift of the captured graph
   int step_kernel = 0;               // LB_OPT_STEP_KERNEL
   bool any_shift = false;            // an instance uses the half-force velocity (old_forcing 2)
-  int nodes_per_thread = 4;          // LB_OPT_NODES_PER_THREAD
-  int graph_npt = 0;
   lb_batch* tiles = nullptr;         // private single-member batch of the tiled step
   cudaStream_t aux = nullptr;        // second stream of the region-split step
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;

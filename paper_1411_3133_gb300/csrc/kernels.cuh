@@ -13,10 +13,37 @@ namespace lbgm {
 // the node's density is not finite.
 // Nodes on an equilibrium wall (the end nodes of the walled axes) leave the
 // step as f^eq(rho', 0) of their own density and metric (Sec. III).
+//
+// 2-byte storage (Codec uses_ref): f holds the stored deviations g of the
+// streamed populations (gather with RAW), and the collision runs on them
+// through the stream table of the node's row: moments from the table's
+// reference moments plus the weighted deviations, post-collision
+// deviations from collide_dev. Only equilibrium-wall nodes, which store
+// f^eq, encode against the reference table.
 template <typename S, typename Real, int K>
 __device__ __forceinline__ void collide_store(Real (&f)[Q], S* __restrict__ fout, const float* ref,
                                               const GeoDev<Real>& geo, const InstParams<Real>& ip, const Dims& d,
                                               const CellPos& p, int* __restrict__ flag) {
+  if constexpr (Codec<S, Real>::uses_ref) {
+    const uint32_t stride = uint32_t(d.nr) * uint32_t(d.st_rows3);
+    const float4* st = stream_of(d, p.b) + stream_row<K>(d, p.ir, p.i3);
+    const float4 ta = __ldg(st), tb = __ldg(st + stride), tc = __ldg(st + 2 * stride);
+    const Moments<float> m = moments_dev(f, ta, tb, tc);
+    if (!finite_v(m.rho)) {
+      if (*flag == 0) atomicExch(flag, 1);
+    }
+    const int row = K == KELL ? p.ir * d.geo_rows3 + p.i3 : p.ir;
+    const NodeGeo<float, K> g = load_geo<float, K>(geo, row);
+    if (d.wall_eq && (p.ir == 0 || p.ir == d.nr - 1 || (!d.periodic3 && (p.i3 == 0 || p.i3 == d.n3 - 1)))) {
+      equilibrium<float, K>(m.rho, 0.0f, 0.0f, 0.0f, g, f);
+      store_node<K>(fout, ref, p, d, f);
+      return;
+    }
+    const Coef<float> k = coefficients<float, K>(m, g, ip.kappa, ip.G);
+    collide_dev<K>(f, k, g, ip.omega, st, stride, tc.z);
+    store_raw<S>(fout, p, d, f);
+    return;
+  }
   const Moments<Real> m = moments(f);
   if (!finite_v(m.rho)) {  // NaN or Inf
     if (*flag == 0) atomicExch(flag, 1);
@@ -41,7 +68,7 @@ __device__ __forceinline__ void step_node(const S* __restrict__ fin, S* __restri
                                           const GeoDev<Real>& geo, const InstParams<Real>& ip, const Dims& d,
                                           const CellPos& p, int* __restrict__ flag) {
   Real f[Q];
-  gather<K, S, Real, WALLS>(fin, ref, p, d, f);
+  gather<K, S, Real, WALLS, Codec<S, Real>::uses_ref>(fin, ref, p, d, f);
   collide_store<S, Real, K>(f, fout, ref, geo, ip, d, p, flag);
 }
 
@@ -125,7 +152,7 @@ __global__ void __launch_bounds__(KBounds<S, Real, K>::maxt, KBounds<S, Real, K>
   const size_t base = size_t(b) * Q * uint32_t(d.ncell);
   const float* ref = ref_of(d, b);
   Real f[Q];
-  gather_edge<K>(fin + base, ref, p, d, f);
+  gather_edge<K, S, Real, Codec<S, Real>::uses_ref>(fin + base, ref, p, d, f);
   collide_store<S, Real, K>(f, fout + base, ref, geo, inst[b], d, p, flag);
 }
 
@@ -143,7 +170,8 @@ struct ListInst {
 };
 
 // Work-list step over instances of one metric kind. Work item j = (instance,
-// first, count) covers `count` <= blockDim.x nodes of one instance: with
+// first, count) covers `count` nodes of one instance (a tile of one or more
+// blocks' worth; thread t takes nodes t, t + blockDim.x, ...): with
 // WALLS = 0 the interior nodes first .. first + count - 1 (no wall within 3
 // nodes: the far-from-wall gather alone), with WALLS = 2 the nodes
 // cells[first .. first + count - 1] (the wall nodes: folds, or clamps for
@@ -172,8 +200,8 @@ __global__ void __launch_bounds__(KBounds<S, Real, K>::maxt, KBounds<S, Real, K>
       sh.w[threadIdx.x] = reinterpret_cast<const uint32_t*>(insts + w.x)[threadIdx.x];
     __syncthreads();
     const ListInst<S, Real>& I = sh.rec;
-    if (int(threadIdx.x) < w.z) {
-      const uint32_t t = WALLS == 0 ? uint32_t(w.y) + threadIdx.x : uint32_t(cells[w.y + threadIdx.x]);
+    for (int i = int(threadIdx.x); i < w.z; i += int(blockDim.x)) {
+      const uint32_t t = WALLS == 0 ? uint32_t(w.y + i) : uint32_t(cells[w.y + i]);
       const Dims d = I.d;
       const CellPos p = locate(d, t);
       const S* fin = parity ? I.f1 : I.f0;
@@ -181,121 +209,6 @@ __global__ void __launch_bounds__(KBounds<S, Real, K>::maxt, KBounds<S, Real, K>
       step_node<S, Real, K, WALLS>(fin, fout, d.ref, I.geo, *I.ip, d, p, I.flag);
     }
   }
-}
-
-// cp.async of one 4- or 8-byte element from global into shared memory.
-template <class Real>
-__device__ __forceinline__ void cp_async_elem(Real* smem_dst, const Real* gsrc) {
-  static_assert(sizeof(Real) == 4 || sizeof(Real) == 8, "cp.async copies 4, 8 or 16 bytes");
-  const uint32_t dst = uint32_t(__cvta_generic_to_shared(smem_dst));
-  if constexpr (sizeof(Real) == 4)
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(gsrc) : "memory");
-  else
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(gsrc) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
-}
-
-// Unit copied per population by the prefetching kernel: the element itself
-// (4 or 8 bytes), or for 2-byte storage the aligned 4-byte word holding it
-// (cp.async has no 2-byte form); the state buffers carry 16 bytes of padding
-// so that the word of the last element stays inside the allocation.
-template <class S>
-struct AsyncUnit {
-  using T = S;
-  static constexpr bool half = false;
-};
-template <>
-struct AsyncUnit<__half> {
-  using T = uint32_t;
-  static constexpr bool half = true;
-  __device__ static __forceinline__ float to_float(unsigned short b) { return __half2float(__ushort_as_half(b)); }
-};
-template <>
-struct AsyncUnit<__nv_bfloat16> {
-  using T = uint32_t;
-  static constexpr bool half = true;
-  __device__ static __forceinline__ float to_float(unsigned short b) {
-    return __bfloat162float(__ushort_as_bfloat16(b));
-  }
-};
-
-// Prefetching step: thread j of block B updates the nodes
-// (B npt + k) blockDim + j, k = 0 .. npt - 1. While node k is computed, the 41
-// sources of node k + 1 are already being copied (cp.async) into the thread's
-// own shared-memory slots [buffer][l][j], so the next node's loads are in
-// flight during the arithmetic without holding registers. A thread reads only
-// slots it filled itself after its own wait_group: no block barrier. For
-// 2-byte storage a 64-bit mask records which half of each copied word holds
-// the population, and the reference population of each source row is copied
-// alongside. Shared memory: (2-byte storage: 2 x) 2 * Q * blockDim *
-// sizeof(unit) bytes.
-template <typename S, typename Real, int K>
-__global__ void __launch_bounds__(256) k_step_async(const S* __restrict__ fin, S* __restrict__ fout,
-                                                    GeoDev<Real> geo, const InstParams<Real>* __restrict__ inst,
-                                                    Dims d, int npt, int* __restrict__ flag) {
-  using U = typename AsyncUnit<S>::T;
-  using Cd = Codec<S, Real>;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  U* sm = reinterpret_cast<U*>(smem_raw);
-  const uint32_t bd = blockDim.x, tid = threadIdx.x;
-  float* sref = reinterpret_cast<float*>(sm + 2 * Q * bd);  // 2-byte storage: [buffer][l][j] references
-  const uint32_t total = uint32_t(d.batch) * uint32_t(d.ncell);
-  const uint32_t first = blockIdx.x * uint32_t(npt) * bd + tid;
-  uint64_t sel_next = 0;
-  auto issue = [&](uint32_t t, uint32_t buf) {
-    if (t >= total) return;
-    const CellPos p = locate(d, t);
-    U* slot = sm + buf * Q * bd + tid;
-    float* rslot = sref + buf * Q * bd + tid;
-    const float* ref = ref_of(d, p.b);
-    for_each_source<K>(fin + size_t(p.b) * Q * d.ncell, p, d, [&](auto L_, const S* src, int sl, int row) {
-      constexpr int L = decltype(L_)::value;
-      if constexpr (AsyncUnit<S>::half) {
-        const uintptr_t a = reinterpret_cast<uintptr_t>(src);
-        sel_next |= uint64_t((a >> 1) & 1u) << L;
-        cp_async_elem(slot + L * bd, reinterpret_cast<const uint32_t*>(a & ~uintptr_t(3)));
-        cp_async_elem(rslot + L * bd, ref + ref_index<K>(d, sl, row));
-      } else {
-        cp_async_elem(slot + L * bd, src);
-      }
-    });
-  };
-  issue(first, 0);
-  cp_async_commit();
-  for (int k = 0; k < npt; ++k) {
-    const uint32_t t = first + uint32_t(k) * bd;
-    if (t >= total) break;  // later nodes of this thread are out of range too
-    const uint64_t sel = sel_next;
-    sel_next = 0;
-    if (k + 1 < npt) {
-      issue(t + bd, uint32_t(k + 1) & 1u);
-      cp_async_commit();
-      cp_async_wait<1>();  // node k's group has landed
-    } else {
-      cp_async_wait<0>();
-    }
-    const CellPos p = locate(d, t);
-    const U* slot = sm + (uint32_t(k) & 1u) * Q * bd + tid;
-    const float* rslot = sref + (uint32_t(k) & 1u) * Q * bd + tid;
-    Real f[Q];
-    static_for<0, Q>([&](auto L_) {
-      constexpr int L = decltype(L_)::value;
-      const U w = slot[L * bd];
-      if constexpr (AsyncUnit<S>::half) {
-        const unsigned short h = (sel >> L) & 1u ? (unsigned short)(w >> 16) : (unsigned short)(w & 0xffffu);
-        // the reference was copied into shared memory: decode from there
-        f[L] = fmaf(float(WeightOf<L>::w), float(AsyncUnit<S>::to_float(h)), rslot[L * bd]);
-      } else {
-        f[L] = Cd::template dec<L>(w, nullptr);
-      }
-    });
-    collide_store<S, Real, K>(f, fout + size_t(p.b) * Q * d.ncell, ref_of(d, p.b), geo, inst[p.b], d, p, flag);
-  }
-  cp_async_wait<0>();  // nothing of this thread stays in flight at exit
 }
 
 // rho' and u of the streamed populations (moments only).
@@ -420,6 +333,76 @@ __global__ void __launch_bounds__(256) k_ref_table(float* __restrict__ ref, GeoD
   float* rb = ref + size_t(b) * Q * nrows;
 #pragma unroll
   for (int l = 0; l < Q; ++l) rb[ref_index<K>(d, l, int(row))] = fe[l];
+}
+
+// Stream table of 2-byte storage (stream_of): one thread per instance and
+// stream row. The sources of a representative node of the row (theta = 0;
+// i_3 the row's own, or any inside / the class's layer for walls on x3) give,
+// for every population l, the stored population index and geometry row whose
+// reference rho_l it receives -- from the same source functions as the step
+// (for_each_source; the compile-time edge folds select the same sources).
+// fin is any state block of the context: its addresses are formed, never read.
+template <int K, class S>
+__global__ void __launch_bounds__(128) k_stream_table(float4* __restrict__ st, const float* __restrict__ ref,
+                                                      const InstParams<float>* __restrict__ inst, const S* fin,
+                                                      Dims d) {
+  const uint32_t nrows = uint32_t(d.nr) * uint32_t(d.st_rows3);
+  const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= uint32_t(d.batch) * nrows) return;
+  const int b = int(t / nrows), srow = int(t - uint32_t(b) * nrows);
+  CellPos p;
+  p.b = b;
+  p.it = 0;
+  if constexpr (K == KELL) {
+    p.ir = srow / d.geo_rows3;
+    p.i3 = srow - p.ir * d.geo_rows3;
+  } else if (d.st_rows3 == 1) {
+    p.ir = srow;
+    p.i3 = 0;
+  } else {
+    p.ir = srow / 7;
+    const int c = srow - p.ir * 7;
+    p.i3 = c < 3 ? c : (c == 3 ? 3 : d.n3 - 7 + c);
+  }
+  p.cell = (p.ir * d.nt + p.it) * d.n3 + p.i3;
+  const float* rb = ref + size_t(b) * Q * size_t(d.nr) * size_t(d.geo_rows3);
+  double rho_l[Q];
+  for_each_source<K, S>(fin, p, d, [&](auto L_, const S*, int sl, int row) {
+    constexpr int L = decltype(L_)::value;
+    rho_l[L] = double(rb[ref_index<K>(d, sl, row)]);
+  });
+  const float om1 = 1.0f - inst[b].omega;  // as the step computes it
+  const int own = geo_row<K>(d, p.ir, p.i3);
+  double tl[Q];
+  double m[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  static_for<0, Q>([&](auto L_) {
+    constexpr int L = decltype(L_)::value;
+    constexpr int cx = L == 0 ? 0 : ((L - 1) % 2 == 0 ? 1 : -1) * PAIRS[L == 0 ? 0 : (L - 1) / 2].x;
+    constexpr int cy = L == 0 ? 0 : ((L - 1) % 2 == 0 ? 1 : -1) * PAIRS[L == 0 ? 0 : (L - 1) / 2].y;
+    constexpr int cz = L == 0 ? 0 : ((L - 1) % 2 == 0 ? 1 : -1) * PAIRS[L == 0 ? 0 : (L - 1) / 2].z;
+    const double r = rho_l[L];
+    m[0] += r;
+    m[1] += cx * r;
+    m[2] += cy * r;
+    m[3] += cz * r;
+    m[4] += cx * cx * r;
+    m[5] += cy * cy * r;
+    m[6] += cz * cz * r;
+    m[7] += cx * cy * r;
+    m[8] += cx * cz * r;
+    m[9] += cy * cz * r;
+    tl[L] = (double(om1) * r - double(rb[ref_index<K>(d, L, own)])) / WeightOf<L>::w;
+  });
+  float4* out = st + size_t(b) * ST_K * nrows + uint32_t(srow);
+  out[0] = make_float4(float(m[0]), float(m[1]), float(m[2]), float(m[3]));
+  out[nrows] = make_float4(float(m[4]), float(m[5]), float(m[6]), float(m[7]));
+  out[2 * nrows] = make_float4(float(m[8]), float(m[9]), float(tl[0]), 0.0f);
+#pragma unroll
+  for (int j = 0; j < NPAIR / 2; ++j) {
+    const double tp0 = tl[4 * j + 1], tm0 = tl[4 * j + 2], tp1 = tl[4 * j + 3], tm1 = tl[4 * j + 4];
+    out[(3 + j) * nrows] = make_float4(float(0.5 * (tp0 + tm0)), float(0.5 * (tp0 - tm0)),
+                                       float(0.5 * (tp1 + tm1)), float(0.5 * (tp1 - tm1)));
+  }
 }
 
 }  // namespace lbgm

@@ -69,21 +69,6 @@ cudaError_t launch_step_list_b16(int K, int walls, const void* insts, const int4
 cudaError_t step_list_occupancy_b16(int K, int threads, int* blocks_per_sm);
 int step_list_max_threads_b16();
 
-// Prefetching step kernel (cp.async into shared memory); each thread updates
-// npt nodes.
-cudaError_t launch_step_async_f32(int K, const float* fin, float* fout, const GeoDev<float>& geo,
-                                  const InstParams<float>* inst, const Dims& d, int* flag, int threads,
-                                  int npt, cudaStream_t s);
-cudaError_t launch_step_async_f64(int K, const double* fin, double* fout, const GeoDev<double>& geo,
-                                  const InstParams<double>* inst, const Dims& d, int* flag, int threads,
-                                  int npt, cudaStream_t s);
-cudaError_t launch_step_async_h16(int K, const __half* fin, __half* fout, const GeoDev<float>& geo,
-                                  const InstParams<float>* inst, const Dims& d, int* flag, int threads,
-                                  int npt, cudaStream_t s);
-cudaError_t launch_step_async_b16(int K, const __nv_bfloat16* fin, __nv_bfloat16* fout,
-                                  const GeoDev<float>& geo, const InstParams<float>* inst, const Dims& d,
-                                  int* flag, int threads, int npt, cudaStream_t s);
-
 // TMA-pipelined FP32 step (n3 in {128, 256}); map is a CUtensorMap over the
 // input state (make_state_tensor_map).
 bool tma_step_supported(const Dims& d);
@@ -114,6 +99,11 @@ cudaError_t launch_ref_from_state(const double* dbl, float* ref, const Dims& d, 
 cudaError_t launch_ref_table(int K, float* ref, const GeoDev<float>& geo, const double* sqrtg,
                              const double* base_uth, const double* rho_in, const double* u_in, const Dims& d,
                              int mode, cudaStream_t s);
+
+// Stream table of 2-byte storage (k_stream_table) from the reference table
+// and the instances' omega; prec 2 (FP16) or 3 (BF16), fin any state block.
+cudaError_t launch_stream_table(int prec, int K, float4* st, const float* ref, const InstParams<float>* inst,
+                                const void* fin, const Dims& d, cudaStream_t s);
 
 // Observables: NQ sums per instance written to out[batch * DIAG_NQ].
 constexpr int DIAG_NQ = 9;

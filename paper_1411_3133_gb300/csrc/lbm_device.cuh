@@ -52,6 +52,10 @@ struct Dims {
   // rows, per instance (ref_index; NULL for FP32 / FP64 storage)
   const float* ref;
   int wall_eq;     // 1: equilibrium (Dirichlet) walls on the end nodes
+  // 2-byte storage: the stream table of each instance (stream_index; NULL
+  // for FP32 / FP64 storage) over nr * st_rows3 stream rows
+  const float4* st;
+  int st_rows3;    // n3 (ellipsoid), 1 (periodic x3), 7 (walls on x3)
 };
 
 // Index of reference population l of geometry row r in an instance's table:
@@ -76,6 +80,38 @@ __device__ __forceinline__ int geo_row(const Dims& d, int ir, int i3) {
 // Reference table of instance b (see Dims::ref).
 __device__ __forceinline__ const float* ref_of(const Dims& d, int b) {
   return d.ref ? d.ref + size_t(b) * 41 * size_t(d.nr) * size_t(d.geo_rows3) : nullptr;
+}
+
+// Stream rows of 2-byte storage. Which stored population (and whose
+// geometry row's reference) a node receives in streaming depends on its
+// position only through i_r and, with walls on x3, through its distance to
+// them; theta is periodic and the references do not depend on it. A stream
+// row groups the nodes that receive alike: (i_r, i_3) for the ellipsoid
+// (its references vary along x3), i_r for a periodic x3, and (i_r, class of
+// i_3) with classes 0, 1, 2 (first layers), 3 (inside), 4, 5, 6 (last
+// layers) for walls on x3.
+template <int K>
+__device__ __forceinline__ int stream_row(const Dims& d, int ir, int i3) {
+  if constexpr (K == KELL) return ir * d.geo_rows3 + i3;
+  if (d.st_rows3 == 1) return ir;
+  const int c = i3 < 3 ? i3 : (i3 > d.n3 - 4 ? i3 - d.n3 + 7 : 3);
+  return ir * 7 + c;
+}
+
+// Stream table of instance b: 13 float4 per stream row, stored [k][row]
+// (consecutive rows are consecutive float4, so a warp of consecutive i_3
+// reads coalesced). Entry k of row s (f_l = w_l g_l + rho_l: g the stored
+// deviation, rho_l the reference population of the stored value a node of
+// row s receives as population l, t_l = ((1 - omega) rho_l - r_l) / w_l with
+// r_l the node's own reference):
+//   k = 0: sum rho_l, sum c^x rho_l, sum c^y rho_l, sum c^z rho_l
+//   k = 1: sum c^x c^x rho_l, c^y c^y, c^z c^z, c^x c^y
+//   k = 2: sum c^x c^z rho_l, sum c^y c^z rho_l, t_0, 0
+//   k = 3 + j, j = 0..9: (t_+ + t_-) / 2 and (t_+ - t_-) / 2 of pair 2 j,
+//           then of pair 2 j + 1 (t_+ of population 2 P + 1, t_- of 2 P + 2)
+constexpr int ST_K = 13;
+__device__ __forceinline__ const float4* stream_of(const Dims& d, int b) {
+  return d.st + size_t(b) * ST_K * size_t(d.nr) * size_t(d.st_rows3);
 }
 
 // Geometry rows in the compute precision. A row is i_r * geo_rows3 + i_3 (or
@@ -197,6 +233,17 @@ struct Codec<__nv_bfloat16, float> {
     return __float2bfloat16_rn((f - __ldg(ref)) * iw);
   }
 };
+
+// The stored number itself (2-byte storage: the deviation g) in FP32 and
+// back, round to nearest.
+__device__ __forceinline__ float raw_dec(__half v) { return __half2float(v); }
+__device__ __forceinline__ float raw_dec(__nv_bfloat16 v) { return __bfloat162float(v); }
+template <class S>
+__device__ __forceinline__ S raw_enc(float x);
+template <>
+__device__ __forceinline__ __half raw_enc<__half>(float x) { return __float2half_rn(x); }
+template <>
+__device__ __forceinline__ __nv_bfloat16 raw_enc<__nv_bfloat16>(float x) { return __float2bfloat16_rn(x); }
 
 // ---------------------------------------------------------------------------
 // pull streaming
@@ -435,12 +482,23 @@ struct DecodeInto {
   }
 };
 
+// Raw visitor of 2-byte storage: f[L] holds the stored deviation g itself
+// (the step works on deviations; see collide_store).
+template <class S>
+struct RawInto {
+  float (&f)[Q];
+  template <class LC>
+  __device__ __forceinline__ void operator()(LC, const S* src, int, int) const {
+    f[LC::value] = raw_dec(__ldg(src));
+  }
+};
+
 // Streamed populations of a node within 3 layers of an r-wall of a channel
-// periodic in x3 (nr >= 7), through the per-layer constant folds.
-template <int K, class S, class R>
-__device__ __forceinline__ void gather_edge(const S* __restrict__ fin, const float* ref, const CellPos& p,
-                                            const Dims& d, R (&f)[Q]) {
-  DecodeInto<K, S, R> put{f, ref, d};
+// periodic in x3 (nr >= 7), through the per-layer constant folds, into the
+// visitor put (DecodeInto or RawInto).
+template <int K, class S, class Put>
+__device__ __forceinline__ void gather_edge_v(const S* __restrict__ fin, const CellPos& p, const Dims& d,
+                                              const Put& put) {
   put(std::integral_constant<int, 0>{}, fin + uint32_t(p.cell), 0, geo_row<K>(d, p.ir, p.i3));
   const int side = p.ir < 3 ? 0 : 1;
   const int j = side == 0 ? p.ir : d.nr - 1 - p.ir;
@@ -454,23 +512,55 @@ __device__ __forceinline__ void gather_edge(const S* __restrict__ fin, const flo
   }
 }
 
+// The visitor of a gather: decoded populations f, or with RAW (2-byte
+// storage only) the stored deviations.
+template <int K, class S, class R, bool RAW>
+struct GatherPut {
+  using type = DecodeInto<K, S, R>;
+  __device__ static __forceinline__ type make(R (&f)[Q], const float* ref, const Dims& d) { return {f, ref, d}; }
+};
+template <int K, class S>
+struct GatherPut<K, S, float, true> {
+  using type = RawInto<S>;
+  __device__ static __forceinline__ type make(float (&f)[Q], const float*, const Dims&) { return {f}; }
+};
+
+template <int K, class S, class R, bool RAW = false>
+__device__ __forceinline__ void gather_edge(const S* __restrict__ fin, const float* ref, const CellPos& p,
+                                            const Dims& d, R (&f)[Q]) {
+  gather_edge_v<K>(fin, p, d, GatherPut<K, S, R, RAW>::make(f, ref, d));
+}
+
 // Load the 41 streamed populations of node p from the post-collision state
 // (instance block fin, reference table ref).
 // WALLS = 2 (either path): near an r-wall with bounce-back walls, at least 3
 // nodes away from any x3 wall, only the r-wall can lie on a population's
 // path, and the compile-time folds of gather_edge replace the general wall
 // rule (the same sources, fewer instructions).
-template <int K, class S, class R, int WALLS = 2>
+// RAW (2-byte storage only): f receives the stored deviations g instead of
+// the decoded populations.
+template <int K, class S, class R, int WALLS = 2, bool RAW = false>
 __device__ __forceinline__ void gather(const S* __restrict__ fin, const float* ref, const CellPos& p,
                                        const Dims& d, R (&f)[Q]) {
   if constexpr (WALLS == 2) {
     const bool x3_clear = d.periodic3 || (p.i3 >= 3 && p.i3 <= d.n3 - 4);
     if (!d.wall_eq && d.nr >= 7 && x3_clear && (p.ir < 3 || p.ir > d.nr - 4)) {
-      gather_edge<K>(fin, ref, p, d, f);
+      gather_edge<K, S, R, RAW>(fin, ref, p, d, f);
       return;
     }
   }
-  for_each_source<K, S, WALLS>(fin, p, d, DecodeInto<K, S, R>{f, ref, d});
+  for_each_source<K, S, WALLS>(fin, p, d, GatherPut<K, S, R, RAW>::make(f, ref, d));
+}
+
+// Store the 41 post-collision deviations g of node p (2-byte storage).
+template <class S>
+__device__ __forceinline__ void store_raw(S* __restrict__ out, const CellPos& p, const Dims& d,
+                                          const float (&g)[Q]) {
+  const uint32_t N = uint32_t(d.ncell), cell = uint32_t(p.cell);
+  static_for<0, Q>([&](auto L_) {
+    constexpr int L = decltype(L_)::value;
+    out[uint32_t(L) * N + cell] = raw_enc<S>(g[L]);
+  });
 }
 
 // Store the 41 post-collision populations of node p into the instance block
@@ -579,6 +669,50 @@ __device__ __forceinline__ Moments<V> moments(const V (&f)[Q]) {
     m.sxy = mac<C::x * C::y>(m.sxy, s);
     m.sxz = mac<C::x * C::z>(m.sxz, s);
     m.syz = mac<C::y * C::z>(m.syz, s);
+  });
+  return m;
+}
+
+// acc + (C w_P) x: a lattice-integer coefficient times pair P's weight
+template <int C, int P, class V>
+__device__ __forceinline__ V macw(const V& acc, const V& x) {
+  if constexpr (C == 0) return acc;
+  else return fmav(V(double(C) * Pair<P>::w), x, acc);
+}
+
+// Moments of the streamed populations f_l = w_l g_l + rho_l from the stored
+// deviations g of 2-byte storage: the streamed references' moments (stream
+// table entries a, b, c) start the sums, and every weight is folded into the
+// multiply-add that accumulates it.
+template <typename V>
+__device__ __forceinline__ Moments<V> moments_dev(const V (&g)[Q], const float4& a, const float4& b,
+                                                  const float4& c) {
+  Moments<V> m;
+  m.rho = fmav(V(W_REST), g[0], V(a.x));
+  m.jx = V(a.y);
+  m.jy = V(a.z);
+  m.jz = V(a.w);
+  m.sxx = V(b.x);
+  m.syy = V(b.y);
+  m.szz = V(b.z);
+  m.sxy = V(b.w);
+  m.sxz = V(c.x);
+  m.syz = V(c.y);
+  static_for<0, NPAIR>([&](auto P_) {
+    constexpr int P = decltype(P_)::value;
+    using C = Pair<P>;
+    const V s = g[2 * P + 1] + g[2 * P + 2];
+    const V df = g[2 * P + 1] - g[2 * P + 2];
+    m.rho = macw<1, P>(m.rho, s);
+    m.jx = macw<C::x, P>(m.jx, df);
+    m.jy = macw<C::y, P>(m.jy, df);
+    m.jz = macw<C::z, P>(m.jz, df);
+    m.sxx = macw<C::x * C::x, P>(m.sxx, s);
+    m.syy = macw<C::y * C::y, P>(m.syy, s);
+    m.szz = macw<C::z * C::z, P>(m.szz, s);
+    m.sxy = macw<C::x * C::y, P>(m.sxy, s);
+    m.sxz = macw<C::x * C::z, P>(m.sxz, s);
+    m.syz = macw<C::y * C::z, P>(m.syz, s);
   });
   return m;
 }
@@ -713,9 +847,17 @@ __device__ __forceinline__ Coef<V> coefficients(const Moments<V>& m, const NodeG
 // BGK collision with the forcing term for the pair (c, -c), in place:
 //   f* = (1 - omega) f + omega f^eq + F
 //      = (1 - omega) f + w (omega E + Fe) +- w (omega O + Fo)
-template <typename V, int K, int P>
+//
+// DEV (2-byte storage): fp, fm are the stored deviations g = (f - r) / w and
+// the result is the post-collision deviation
+//   g* = (1 - omega) g + (omega E + Fe + te) +- (omega O + Fo + to)
+// with te, to the even and odd parts of t = ((1 - omega) rho - r) / w from the
+// stream table; te and to start the sums of Fe and Fo, so they cost no
+// instruction, and the weight multiply of the pair drops out.
+template <typename V, int K, int P, bool DEV = false>
 __device__ __forceinline__ void collide_pair(V& fp, V& fm, const Coef<V>& k, const NodeGeo<V, K>& g,
-                                             const V& omega, const V& om1) {
+                                             const V& omega, const V& om1, const V& te = V(0.0),
+                                             const V& to = V(0.0)) {
   using C = Pair<P>;
   constexpr int cx = C::x, cy = C::y, cz = C::z;
   constexpr bool curv = K != KFLAT;
@@ -759,22 +901,33 @@ __device__ __forceinline__ void collide_pair(V& fp, V& fm, const Coef<V>& k, con
   const V nax = dot3<cx, cy, cz>(k.naxx, k.naxy, k.naxz);
   const V nay = dot3<cx, cy, cz>(k.naxy, k.nayy, k.nayz);
   const V naz = dot3<cx, cy, cz>(k.naxz, k.nayz, k.nazz);
-  V FnA = Ft * nay;
+  V FnA;
+  if constexpr (DEV) FnA = fmav(Ft, nay, to);
+  else FnA = Ft * nay;
   if constexpr (hasFr) FnA = fmav(Fr, nax, FnA);
   if constexpr (hasFz) FnA = fmav(Fz, naz, FnA);
   // Fe = fA uc Fc - fB uF,  Fo = Fc (t0 + cAc / (2 cs^2)) - F.A2s c
-  V Fe = k.nfB * uF;
+  V Fe;
+  if constexpr (DEV) Fe = fmav(k.nfB, uF, te);
+  else Fe = k.nfB * uF;
   V Fo = FnA;
   if constexpr (hasFc) {
     Fe = fmav(k.fA * uc, Fc, Fe);
     const V ncAc = dot3<cx, cy, cz>(nax, nay, naz);
     Fo = fmav(Fc, fmav(V(-0.5 / CS2), ncAc, k.t0), FnA);
   }
-  const V w = V(C::w);
-  const V Bw = fmav(omega, O, Fo) * w;
-  const V a = fmav(omega, E, Fe);
-  fp = fmav(om1, fp, fmav(a, w, Bw));
-  fm = fmav(om1, fm, fmav(a, w, -Bw));
+  if constexpr (DEV) {
+    const V B = fmav(omega, O, Fo);
+    const V a = fmav(omega, E, Fe);
+    fp = fmav(om1, fp, a + B);
+    fm = fmav(om1, fm, a - B);
+  } else {
+    const V w = V(C::w);
+    const V Bw = fmav(omega, O, Fo) * w;
+    const V a = fmav(omega, E, Fe);
+    fp = fmav(om1, fp, fmav(a, w, Bw));
+    fm = fmav(om1, fm, fmav(a, w, -Bw));
+  }
 }
 
 template <typename V, int K>
@@ -785,6 +938,28 @@ __device__ __forceinline__ void collide(V (&f)[Q], const Coef<V>& k, const NodeG
   static_for<0, NPAIR>([&](auto P_) {
     constexpr int P = decltype(P_)::value;
     collide_pair<V, K, P>(f[2 * P + 1], f[2 * P + 2], k, g, omega, om1);
+  });
+}
+
+// BGK collision with forcing on the stored deviations g of 2-byte storage,
+// in place (collide_pair with DEV): st points at the node's stream row (k =
+// 0 entry), stride the table's rows.
+template <int K>
+__device__ __forceinline__ void collide_dev(float (&g)[Q], const Coef<float>& k, const NodeGeo<float, K>& geo,
+                                            float omega, const float4* __restrict__ st, uint32_t stride,
+                                            float t0) {
+  const float om1 = 1.0f - omega;
+  g[0] = fmaf(om1, g[0], fmaf(omega, k.e0, fmaf(k.nfB, k.uy * k.fext_t, t0)));
+  // each table entry is requested one pair group ahead of its use, so its
+  // load overlaps the arithmetic of the group before
+  float4 t = __ldg(st + 3 * stride);
+  static_for<0, NPAIR / 2>([&](auto J_) {
+    constexpr int J = decltype(J_)::value;
+    float4 tn = t;
+    if constexpr (J + 1 < NPAIR / 2) tn = __ldg(st + (4 + J) * stride);
+    collide_pair<float, K, 2 * J, true>(g[4 * J + 1], g[4 * J + 2], k, geo, omega, om1, t.x, t.y);
+    collide_pair<float, K, 2 * J + 1, true>(g[4 * J + 3], g[4 * J + 4], k, geo, omega, om1, t.z, t.w);
+    t = tn;
   });
 }
 

@@ -1,12 +1,13 @@
 // Surrogate of developed channel flow: a multilayer perceptron mapping
-// (Dean number, radial position, streamwise-normal position) to the
-// macroscopic fields (rho', u^r, u^theta, u^3) of a converged LB run, used
-// to warm-start the LB (lb_init_fields). Hand-written kernels for the
-// forward pass, the backward pass and the Adam update; weights are kept in
-// FP32 (master copy, Adam moments) and used in BF16 by every product, which
-// accumulates in FP32.
+// channel parameters (Dean number, curvature ratio, ...) and a node's
+// position to the macroscopic fields (rho', u^r, u^theta, u^3) of a
+// converged LB run, used to warm-start the LB (lb_init_fields). Hand-written
+// kernels for the forward pass, the backward pass and the Adam update;
+// weights are kept in FP32 (master copy, Adam moments) and used in BF16 by
+// every product, which accumulates in FP32.
 //
-// Layers: features phi(x) = (De, r, sin(2 pi k z), cos(2 pi k z), k = 1..F),
+// Layers: features phi(x) = (p_1 .. p_P, sin(2 pi k z), cos(2 pi k z), k =
+// 1..F) of an input row (p_1 .. p_P, z),
 // then depth - 1 hidden layers of `width` units with SiLU, then a linear
 // output layer of 4 units. Outputs are normalised per field: the network
 // predicts (y - mean) / std.
@@ -28,19 +29,21 @@ constexpr int NOUT = 4;
 // --------------------------------------------------------------------------
 // kernels
 // --------------------------------------------------------------------------
-__global__ void k_features(const float* __restrict__ x, int n, int nf, float* __restrict__ phi) {
+// Row i of x holds np plain inputs then z; its features are the plain
+// inputs then sin(2 pi k z), cos(2 pi k z), k = 1..nf.
+__global__ void k_features(const float* __restrict__ x, int n, int np, int nf, float* __restrict__ phi) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const int nin = 2 + 2 * nf;
-  const float de = x[3 * i], r = x[3 * i + 1], z = x[3 * i + 2];
+  const int nin = np + 2 * nf;
+  const float* xi = x + size_t(i) * (np + 1);
   float* o = phi + size_t(i) * nin;
-  o[0] = de;
-  o[1] = r;
+  for (int j = 0; j < np; ++j) o[j] = xi[j];
+  const float z = xi[np];
   for (int k = 1; k <= nf; ++k) {
     float s, c;
     sincospif(2.0f * float(k) * z, &s, &c);
-    o[2 * k] = s;
-    o[2 * k + 1] = c;
+    o[np + 2 * k - 2] = s;
+    o[np + 2 * k - 1] = c;
   }
 }
 
@@ -201,7 +204,7 @@ unsigned nblk(size_t n, int t = 256) { return unsigned((n + t - 1) / t); }
 }  // namespace
 
 struct lb_mlp {
-  int nf = 0, width = 0, depth = 0, max_batch = 0, nin = 0;
+  int np = 0, nf = 0, width = 0, depth = 0, max_batch = 0, nin = 0;
   cudaStream_t stream = nullptr;
   std::vector<int> fan_in, fan_out;       // per layer
   std::vector<size_t> w_off, b_off;       // offsets into the parameter arrays
@@ -255,7 +258,7 @@ cudaError_t gemm(cudaStream_t s, int M, int N, int K, const TA* A, long sam, lon
 // Forward pass of n rows; the outputs (normalised) land in n->Yout.
 cudaError_t forward(lb_mlp* net, const float* x, int n) {
   cudaStream_t s = net->stream;
-  k_features<<<nblk(n), 256, 0, s>>>(x, n, net->nf, net->phi);
+  k_features<<<nblk(n), 256, 0, s>>>(x, n, net->np, net->nf, net->phi);
   const float* in = net->phi;
   for (int l = 0; l < net->depth; ++l) {
     const int fi = net->fan_in[l], fo = net->fan_out[l];
@@ -275,20 +278,21 @@ cudaError_t forward(lb_mlp* net, const float* x, int n) {
 
 extern "C" {
 
-lb_status lb_mlp_create(int n_fourier, int width, int depth, int max_batch, unsigned long long seed,
+lb_status lb_mlp_create(int n_plain, int n_fourier, int width, int depth, int max_batch, unsigned long long seed,
                         void* cuda_stream, lb_mlp** out) {
   if (!out) return mfail(nullptr, LB_ERR_ARG, "null argument");
   *out = nullptr;
-  if (n_fourier < 0 || n_fourier > 16 || width < 4 || width > 4096 || depth < 2 || depth > 16 ||
-      max_batch < 1 || max_batch > (1 << 22))
-    return mfail(nullptr, LB_ERR_ARG, "need 0 <= n_fourier <= 16, 4 <= width <= 4096, 2 <= depth <= 16, "
-                                      "1 <= max_batch <= 4M");
+  if (n_plain < 1 || n_plain > 16 || n_fourier < 0 || n_fourier > 16 || width < 4 || width > 4096 || depth < 2 ||
+      depth > 16 || max_batch < 1 || max_batch > (1 << 22))
+    return mfail(nullptr, LB_ERR_ARG, "need 1 <= n_plain <= 16, 0 <= n_fourier <= 16, 4 <= width <= 4096, "
+                                      "2 <= depth <= 16, 1 <= max_batch <= 4M");
   lb_mlp* n = new lb_mlp();
+  n->np = n_plain;
   n->nf = n_fourier;
   n->width = width;
   n->depth = depth;
   n->max_batch = max_batch;
-  n->nin = 2 + 2 * n_fourier;
+  n->nin = n_plain + 2 * n_fourier;
   n->stream = static_cast<cudaStream_t>(cuda_stream);
   for (int l = 0; l < depth; ++l) {
     n->fan_in.push_back(l == 0 ? n->nin : width);
