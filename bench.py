@@ -276,18 +276,15 @@ class SweepRunner:
         self.ctx = L.LBContext(spec, batch=wl.batch, precision=wl.precision)
         self.ctx.lb_set_option(L.LB_OPT_USE_GRAPH, 1)
         self.ctx.lb_set_option(L.LB_OPT_STEP_KERNEL,
-                               {"auto": 0, "plain": 1, "tma": 2, "async": 3, "split": 4, "tiled": 5}[args.step_kernel])
+                               {"auto": 0, "plain": 1, "tma": 2, "split": 4, "tiled": 5}[args.step_kernel])
         self.ctx.lb_set_option(L.LB_OPT_BLOCK_THREADS, args.threads)
-        self.ctx.lb_set_option(L.LB_OPT_NODES_PER_THREAD, args.npt)
         self.ctx.lb_init(params)
         self.cells = wl.batch * wl.ncells
         self.stream = self.ctx.stream
         if args.step_kernel == "auto":      # the library's automatic choice for this workload
             args.step_kernel = "plain" if args.precision == "fp64" else "split"
         self.kernel = {"tma": "k_step_tma<KCYL,256>",
-                       "split": f"k_step_bulk<{args.precision},KCYL> + k_step_edge ({args.threads} threads)",
-                       "async": f"k_step_async<{args.precision},KCYL> ({args.threads} threads, "
-                                f"{args.npt} nodes per thread)"}.get(
+                       "split": f"k_step_bulk<{args.precision},KCYL> + k_step_edge ({args.threads} threads)"}.get(
             args.step_kernel, f"k_step<{args.precision},KCYL> ({args.threads} threads)")
         self.profiled = args.precision == "fp32" and args.step_kernel == "split"
         self.launches_per_step = 2 if args.step_kernel == "split" else 1
@@ -352,7 +349,7 @@ class EllipsoidRunner(SweepRunner):
         self.ctx = L.LBContext(spec, batch=24, precision=args.precision)
         self.ctx.lb_set_option(L.LB_OPT_USE_GRAPH, 1)
         self.ctx.lb_set_option(L.LB_OPT_STEP_KERNEL,
-                               {"auto": 0, "plain": 1, "tma": 2, "async": 3, "split": 4, "tiled": 5}[args.step_kernel])
+                               {"auto": 0, "plain": 1, "tma": 2, "split": 4, "tiled": 5}[args.step_kernel])
         self.ctx.lb_set_option(L.LB_OPT_BLOCK_THREADS, args.threads)
         self.ctx.lb_init(params)
         self.cells = 24 * wl.ncells
@@ -452,8 +449,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--cpu-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--step-kernel", default="auto", choices=["auto", "plain", "tma", "async", "split", "tiled"])
-    ap.add_argument("--npt", type=int, default=4, help="nodes per thread of the prefetching kernel")
+    ap.add_argument("--step-kernel", default="auto", choices=["auto", "plain", "tma", "split", "tiled"])
     ap.add_argument("--threads", type=int, default=128, help="threads per block of the step kernel")
     ap.add_argument("--precision", default="fp32", choices=sorted(BYTES_PER_UPDATE))
     ap.add_argument("--workload", default="sweep", choices=["sweep", "mixed", "ellipsoid"],

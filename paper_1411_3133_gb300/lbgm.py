@@ -26,7 +26,7 @@ STATUS_NAMES = {0: "LB_OK", 1: "LB_ERR_ARG", 2: "LB_ERR_CUDA", 3: "LB_ERR_NONFIN
 METRICS = {"flat": 0, "cylindrical": 1, "ellipsoidal": 2}
 PRECISIONS = {"fp64": 0, "fp32": 1, "fp16_shifted": 2, "bf16_shifted": 3}
 LB_OPT_CHECK_EVERY, LB_OPT_BLOCK_THREADS, LB_OPT_USE_GRAPH, LB_OPT_STEP_KERNEL = 0, 1, 2, 3
-LB_OPT_SCHEDULE, LB_OPT_NODES_PER_THREAD, LB_OPT_STORAGE_REFERENCE = 4, 5, 6
+LB_OPT_SCHEDULE, LB_OPT_TILE_BLOCKS, LB_OPT_STORAGE_REFERENCE = 4, 5, 6
 
 
 class lb_geometry_desc(ctypes.Structure):
@@ -56,7 +56,7 @@ class lb_diag(ctypes.Structure):
 
 class lb_tune(ctypes.Structure):
     _fields_ = [("block_threads", ctypes.c_int), ("schedule", ctypes.c_int),
-                ("nodes_per_thread", ctypes.c_int), ("ms_per_step", ctypes.c_double)]
+                ("tile_nodes", ctypes.c_int), ("ms_per_step", ctypes.c_double)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -115,7 +115,7 @@ SIGNATURES = {
     "lb_batch_step_count": (ctypes.c_longlong, [_P]),
     "lb_batch_destroy": (None, [_P]),
     "lb_batch_last_error": (ctypes.c_char_p, [_P]),
-    "lb_mlp_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+    "lb_mlp_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                      ctypes.c_ulonglong, _P, ctypes.POINTER(_P)]),
     "lb_mlp_param_count": (ctypes.c_size_t, [_P]),
     "lb_mlp_set_output_scale": (ctypes.c_int, [_P, _F, _F]),
@@ -166,10 +166,10 @@ def _check_batch(status, batch):
 
 def _tune_call(fn, handle, steps_per_trial, check):
     best = lb_tune()
-    trials = (lb_tune * 16)()
+    trials = (lb_tune * 64)()
     n = ctypes.c_int()
-    check(fn(handle, int(steps_per_trial), ctypes.byref(best), trials, 16, ctypes.byref(n)), handle)
-    return best.as_dict(), [trials[i].as_dict() for i in range(min(n.value, 16))]
+    check(fn(handle, int(steps_per_trial), ctypes.byref(best), trials, 64, ctypes.byref(n)), handle)
+    return best.as_dict(), [trials[i].as_dict() for i in range(min(n.value, 64))]
 
 
 def _ptr(a):
@@ -493,17 +493,18 @@ def _check_mlp(status, net):
 
 
 class LBMlp:
-    """One lb_mlp (see include/lbgm.h): inputs x (n, 3) and fields y (n, 4)
-    are torch CUDA float32 tensors."""
+    """One lb_mlp (see include/lbgm.h): inputs x (n, n_plain + 1) and fields
+    y (n, 4) are torch CUDA float32 tensors."""
 
-    def __init__(self, n_fourier=4, width=256, depth=5, max_batch=16384, seed=20241111, stream=None):
+    def __init__(self, n_fourier=4, width=256, depth=5, max_batch=16384, seed=20241111, stream=None, n_plain=2):
         import torch
         lib = load_library()
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         h = ctypes.c_void_p()
-        _check_mlp(lib.lb_mlp_create(int(n_fourier), int(width), int(depth), int(max_batch), int(seed),
-                                     ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h)), None)
+        _check_mlp(lib.lb_mlp_create(int(n_plain), int(n_fourier), int(width), int(depth), int(max_batch),
+                                     int(seed), ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h)), None)
         self.handle = h
+        self.n_plain = n_plain
         self.n_fourier, self.width, self.depth, self.max_batch = n_fourier, width, depth, max_batch
 
     def close(self):

@@ -279,6 +279,300 @@ def run(n_train=512, n_test=128, de_lo=20.0, de_hi=60.0, tau=0.55, chunk=512, to
     return rep
 
 
+# ---------------------------------------------------------------------------
+# the mixed-channel surrogate: cylinders and double-curved channels
+# ---------------------------------------------------------------------------
+NU_055 = (0.55 - 0.5) * (1.0 - math.sqrt(0.4))     # lattice viscosity at tau = 0.55
+N_PLAIN_MIXED = 6                                 # De, kind, curvature, aspect, r, theta (then z)
+N_FOURIER_MIXED = 12                              # up to 12 x3 periods: 2 N_3 / N_r <= 32 cells
+
+
+def laminar_speed(inst):
+    """Mean streamwise speed (lattice units) of a channel of workloads.Instance
+    inst at its target Dean number, from the Dean number's definition
+    (Sec. III / IV: De = <v> (d / h) / nu sqrt(d / R_theta)) with R_theta = 1
+    for both kinds and d / h = N_r (bounce-back walls)."""
+    d = inst.r_outer - inst.r_inner
+    nu = (inst.tau - 0.5) * (1.0 - math.sqrt(0.4))
+    return inst.dean * nu / (inst.nr * math.sqrt(d / 1.0))
+
+
+def draw_mixed(n, seed, speed_cap=0.25):
+    """n instances of the mixed-batch distribution (workloads.mixed_batch:
+    alternately cylinder and double-curved, N_r in {32, 48, 64}, N_3 in
+    128..512, De in 20..150, R2/R1 log-uniform in 0.25..4, tau 0.55), keeping
+    only draws whose laminar mean speed stays <= speed_cap (a converged state
+    at De = 150 and N_r = 32 would run at Mach ~ 0.9)."""
+    from .workloads import mixed_batch
+    out, k = [], 0
+    while len(out) < n:
+        for inst in mixed_batch(n=256, seed=seed + 7919 * k):
+            if laminar_speed(inst) <= speed_cap:
+                out.append(inst)
+        k += 1
+    return out[:n]
+
+
+def mixed_inputs(inst, nr, n3, ntheta=1):
+    """Network inputs of every (i_r, i_3) node of inst, rows i_r-major:
+    (De / 150, kind (0 cylinder, 1 double-curved), log2(R2/R1) / 2 (0 for a
+    cylinder, whose R2 is infinite), aspect N_3 / N_r / 16, (i_r + 1/2) / N_r,
+    theta = 1/2 (the fields are theta-uniform), then z = (i_3 + 1/2) / N_3)."""
+    ell = inst.metric == "ellipsoidal"
+    r = (np.arange(nr) + 0.5) / nr
+    z = (np.arange(n3) + 0.5) / n3
+    R, Z = np.meshgrid(r, z, indexing="ij")
+    m = R.size
+    cols = [np.full(m, inst.dean / 150.0), np.full(m, 1.0 if ell else 0.0),
+            np.full(m, math.log2(inst.R2_over_R1) / 2.0 if ell else 0.0), np.full(m, n3 / nr / 16.0),
+            R.ravel(), np.full(m, 0.5), Z.ravel()]
+    return np.stack(cols, axis=1).astype(np.float32)
+
+
+def _spec(inst, ntheta):
+    kw = inst.geometry_kwargs()
+    kw["ntheta"] = ntheta
+    return L.ChannelSpec(**kw)
+
+
+def _sqrtg(inst):
+    desc = _spec(inst, 1).desc()
+    return L.lb_geometry_eval(inst.metric, desc)[:, :, 39]      # (nr, n3): sqrt g of the lattice metric
+
+
+def mixed_targets(inst, rho, u):
+    """Normalised targets of one converged instance: rho' sqrt(g) (about 1)
+    and u / U (U = laminar_speed), theta-averaged; rho (nr, n3), u (3, nr, n3)
+    -> (nr * n3, 4)."""
+    U = laminar_speed(inst)
+    y = np.concatenate([(rho * _sqrtg(inst))[None], u / U], axis=0)
+    return np.moveaxis(y, 0, -1).reshape(-1, 4).astype(np.float32)
+
+
+def mixed_fields(inst, y, ntheta):
+    """Network outputs (nr * n3, 4) of one instance back to fields broadcast
+    over theta: rho (N,), u (3, N) in the field layout of lb_init_fields."""
+    nr, n3 = inst.nr, inst.n3
+    y = np.asarray(y, np.float64).reshape(nr, n3, 4)
+    rho = y[..., 0] / _sqrtg(inst)
+    u = np.moveaxis(y[..., 1:], -1, 0) * laminar_speed(inst)
+    rho = np.broadcast_to(rho[:, None, :], (nr, ntheta, n3)).reshape(-1)
+    u = np.broadcast_to(u[:, :, None, :], (3, nr, ntheta, n3)).reshape(3, -1)
+    return np.ascontiguousarray(rho), np.ascontiguousarray(u)
+
+
+def align_mixed(inst, rho, u):
+    """Phase alignment of a periodic channel's fields (the cylinders': the
+    vortex position along z is set by the noise) on the dominant x3 Fourier
+    mode of u^r; walled channels are returned unchanged. rho (nr, n3), u (3,
+    nr, n3)."""
+    if inst.periodic3:
+        n3 = rho.shape[-1]
+        F = np.abs(np.fft.rfft(u[0].sum(axis=0)))
+        k = int(np.argmax(F[1:]) + 1) if len(F) > 1 else 1
+        c = (u[0] * np.exp(-2j * np.pi * k * np.arange(n3) / n3)[None, :]).sum()
+        if np.isfinite(c) and abs(c) > 1e-12 * max(1e-300, np.abs(u[0]).max() * u[0].size):
+            shift = int(round(np.angle(c) / (2 * np.pi * k) * n3)) % n3
+            return np.roll(rho, shift, axis=-1), np.roll(u, shift, axis=-1)
+    return rho, u
+
+
+def converge_mixed(instances, ntheta=1, tol=1e-8, amp_tol=0.01, check_every=10_000, max_steps=600_000,
+                   warm=None, stream=None, log=None):
+    """Run every instance (one context each, one lb_batch over those still
+    running) until it is converged: the per-step velocity residual
+    max |u(t) - u(t - K)| / (K max |u|) <= tol (lb_velocity_change, K =
+    check_every) and the vortex amplitude (rms u^r minus its x3 mean) within
+    amp_tol of its value one and two checks earlier -- the residual alone
+    passes during the slow exponential growth of a vortex from noise. Cold
+    start (warm None): rest plus seeded noise, as the mixed sweep starts;
+    warm: per instance (rho (N,), u (3, N)) for lb_init_fields.
+    Returns (theta-mean rho (list of (nr, n3)), u (list of (3, nr, n3)),
+    steps (array), converged (bool array), seconds)."""
+    import torch
+
+    from .workloads import force_reference_cylinder
+    stream = stream if stream is not None else torch.cuda.Stream()
+    ctxs, uprev = [], []
+    for k, inst in enumerate(instances):
+        spec = _spec(inst, ntheta)
+        ref = force_reference_cylinder(inst)
+        G = L.lb_force_for_dean("cylindrical", L.make_desc(ref["r_inner"], ref["r_outer"], ref["nr"], 1, ref["n3"]),
+                                inst.tau, inst.dean)
+        ctx = L.LBContext(spec, batch=1, precision="fp32", stream=stream)
+        p = [L.make_params(inst.tau, G, False, inst.seed, inst.noise_amp, False)]
+        if warm is None:
+            ctx.lb_init(p)
+        else:
+            ctx.lb_init_fields(p, warm[k][0][None], warm[k][1][None])
+        u0 = torch.empty(3 * spec.ncells, dtype=torch.float64, device="cuda")
+        ctx.lb_macros(None, u0, on_device=True)
+        ctxs.append(ctx)
+        uprev.append(u0)
+    n = len(instances)
+    steps = np.full(n, max_steps)
+    done = np.zeros(n, dtype=bool)
+    amps = [[] for _ in range(n)]
+    t0 = time.perf_counter()
+    t = 0
+    while t < max_steps and not done.all():
+        live = [i for i in range(n) if not done[i]]
+        batch = L.LBBatch([ctxs[i] for i in live])
+        batch.lb_batch_set_option(L.LB_OPT_USE_GRAPH, 1)
+        batch.lb_batch_step(check_every)
+        batch.close()
+        t += check_every
+        for i in live:
+            change, umax = ctxs[i].lb_velocity_change(uprev[i])
+            a = ctxs[i].lb_diagnostics()[0]["vortex_amp_x3"]
+            amps[i].append(a)
+            h = amps[i][-3:]
+            steady = len(h) == 3 and max(abs(x - a) for x in h) <= amp_tol * a + 1e-12
+            if change[0] <= tol * check_every * max(umax[0], 1e-300) and steady:
+                steps[i] = t
+                done[i] = True
+        if log:
+            log(f"  step {t}: {int(done.sum())}/{n} converged")
+    torch.cuda.synchronize()
+    sec = time.perf_counter() - t0
+    rho_out, u_out = [], []
+    for inst, ctx in zip(instances, ctxs):
+        rho, u = ctx.lb_macros()
+        rho_out.append(rho[0].reshape(inst.nr, ntheta, inst.n3).mean(axis=1))
+        u_out.append(u[0].reshape(3, inst.nr, ntheta, inst.n3).mean(axis=2))
+        ctx.close()
+    return rho_out, u_out, steps, done, sec
+
+
+def save_mixed_net(net, mean, std, path):
+    """The mixed surrogate's parameters and output scale as an .npz file."""
+    np.savez(path, params=net.get_params(), mean=np.asarray(mean, np.float32), std=np.asarray(std, np.float32),
+             shape=np.array([N_PLAIN_MIXED, N_FOURIER_MIXED, net.width, net.depth]))
+
+
+def load_mixed_net(path, max_batch=16384):
+    """An LBMlp holding a saved mixed surrogate (save_mixed_net)."""
+    z = np.load(path)
+    npl, nf, w, d = (int(v) for v in z["shape"])
+    net = L.LBMlp(n_fourier=nf, width=w, depth=d, max_batch=max_batch, n_plain=npl)
+    net.set_params(z["params"])
+    net.set_output_scale(z["mean"], z["std"])
+    return net
+
+
+def predict_mixed(net, inst, ntheta):
+    """The surrogate's fields for instance inst on its grid with ntheta theta
+    nodes: rho (N,), u (3, N) for lb_init_fields."""
+    import torch
+    xi = torch.from_numpy(mixed_inputs(inst, inst.nr, inst.n3)).cuda()
+    yi = np.concatenate([net.predict(xi[s:s + net.max_batch]).cpu().numpy()
+                         for s in range(0, len(xi), net.max_batch)])
+    return mixed_fields(inst, yi, ntheta)
+
+
+def run_mixed(n_train=2000, n_test=256, chunk=500, epochs=30, batch=16384, lr=2e-3, max_steps=600_000,
+              check_every=10_000, train_ntheta=1, test_ntheta=4, seed=20241111, speed_cap=0.25, log=print,
+              save=None):
+    """The surrogate over the mixed-channel distribution: n_train converged
+    states (generated with train_ntheta theta nodes: the developed flow is
+    theta-uniform), a network of (De, kind, R2/R1, aspect, r, theta, z) ->
+    (rho', u), then n_test held-out instances on their own grids (test_ntheta
+    theta nodes) run to convergence from rest plus noise (cold) and from the
+    network's prediction (warm). Reports steps and field error per metric
+    kind."""
+    import torch
+    rep = {"n_train": n_train, "n_test": n_test, "speed_cap": speed_cap, "tol": 1e-8,
+           "check_every": check_every, "max_steps": max_steps, "train_ntheta": train_ntheta,
+           "test_ntheta": test_ntheta}
+    train_set = draw_mixed(n_train, seed, speed_cap)
+    test_set = draw_mixed(n_test, seed + 1_000_003, speed_cap)
+    # 1. converged training states
+    t0 = time.perf_counter()
+    X, Y, st = [], [], []
+    for s in range(0, n_train, chunk):
+        part = train_set[s:s + chunk]
+        rho, u, steps, ok, sec = converge_mixed(part, ntheta=train_ntheta, max_steps=max_steps,
+                                                check_every=check_every)
+        for inst, r_, u_, good in zip(part, rho, u, ok):
+            if not (good and np.isfinite(r_).all() and np.isfinite(u_).all()):
+                continue
+            r_, u_ = align_mixed(inst, r_, u_)
+            X.append(mixed_inputs(inst, inst.nr, inst.n3))
+            Y.append(mixed_targets(inst, r_, u_))
+        st.append(steps)
+        log(f"train states {s}..{s + len(part)}: {sec:.1f} s, {int(ok.sum())} converged")
+    rep["train_generation_s"] = time.perf_counter() - t0
+    rep["train_states_used"] = len(X)
+    rep["train_steps_mean"] = float(np.mean(np.concatenate(st)))
+    x = np.concatenate(X)
+    y = np.concatenate(Y)
+    # 2. training
+    t0 = time.perf_counter()
+    net = L.LBMlp(n_fourier=N_FOURIER_MIXED, width=256, depth=5, max_batch=batch, seed=seed,
+                  n_plain=N_PLAIN_MIXED)
+    y_mean, y_std = y.mean(axis=0), np.maximum(y.std(axis=0), 1e-12)
+    net.set_output_scale(y_mean, y_std)
+    xd, yd = torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()
+    g = torch.Generator(device="cuda").manual_seed(seed)
+    nsamp = len(x)
+    losses = []
+    for ep in range(epochs):
+        step_lr = lr * 0.5 * (1 + math.cos(math.pi * ep / epochs))
+        perm = torch.randperm(nsamp, device="cuda", generator=g)
+        last = None
+        for s in range(0, nsamp - batch + 1, batch):
+            idx = perm[s:s + batch]
+            want = s + 2 * batch > nsamp
+            l_ = net.train_step(xd[idx].contiguous(), yd[idx].contiguous(), step_lr, want_loss=want)
+            if want:
+                last = l_
+        losses.append(last)
+        log(f"epoch {ep} loss {last:.3e}")
+    rep["train_s"] = time.perf_counter() - t0
+    rep["train_samples"] = nsamp
+    rep["loss_first_last"] = [losses[0], losses[-1]]
+    del xd, yd
+    if save:
+        save_mixed_net(net, y_mean, y_std, save)
+    # 3. held-out: cold and warm starts to convergence
+    t0 = time.perf_counter()
+    preds = [predict_mixed(net, inst, test_ntheta) for inst in test_set]
+    rep["inference_s"] = time.perf_counter() - t0
+    rho_c, u_c, sc, okc, sec_c = converge_mixed(test_set, ntheta=test_ntheta, max_steps=max_steps,
+                                                check_every=check_every, log=log)
+    rho_w, u_w, sw, okw, sec_w = converge_mixed(test_set, ntheta=test_ntheta, max_steps=max_steps,
+                                                check_every=check_every, warm=preds, log=log)
+    rep["seconds_cold_warm"] = [sec_c, sec_w]
+    err_pred, err_final = [], []
+    for k, inst in enumerate(test_set):
+        up = preds[k][1].reshape(3, inst.nr, test_ntheta, inst.n3).mean(axis=2)
+        _, a = align_mixed(inst, rho_c[k], u_c[k])
+        _, bp = align_mixed(inst, rho_c[k], up)
+        _, bw = align_mixed(inst, rho_w[k], u_w[k])
+        nrm = np.sqrt((a ** 2).sum())
+        err_pred.append(float(np.sqrt(((bp - a) ** 2).sum()) / nrm))
+        err_final.append(float(np.sqrt(((bw - a) ** 2).sum()) / nrm))
+    err_pred, err_final = np.array(err_pred), np.array(err_final)
+    for kind in ("cylindrical", "ellipsoidal"):
+        sel = np.array([i.metric == kind for i in test_set])
+        both = sel & okc & okw
+        rep[kind] = {
+            "instances": int(sel.sum()), "converged_cold": int((sel & okc).sum()),
+            "converged_warm": int((sel & okw).sum()),
+            "steps_cold_mean": float(sc[both].mean()) if both.any() else None,
+            "steps_warm_mean": float(sw[both].mean()) if both.any() else None,
+            "steps_saved_fraction": float(1.0 - sw[both].sum() / sc[both].sum()) if both.any() else None,
+            "surrogate_rel_l2_median": float(np.median(err_pred[sel])),
+            "surrogate_rel_l2_p90": float(np.percentile(err_pred[sel], 90)),
+            "warm_vs_cold_final_rel_l2_median": float(np.median(err_final[sel])),
+        }
+    rep["test"] = [{"metric": i.metric, "nr": i.nr, "n3": i.n3, "dean": i.dean, "R2_over_R1": i.R2_over_R1,
+                    "steps_cold": int(sc[k]), "steps_warm": int(sw[k]), "err_pred": float(err_pred[k]),
+                    "err_final": float(err_final[k])} for k, i in enumerate(test_set)]
+    net.close()
+    return rep
+
+
 if __name__ == "__main__":
     import argparse
     import json
@@ -289,9 +583,23 @@ if __name__ == "__main__":
     ap.add_argument("--epochs", type=int, default=40)
     ap.add_argument("--max-steps", type=int, default=400_000)
 
+    ap.add_argument("--mixed", action="store_true",
+                    help="the surrogate over the mixed-channel distribution (cylinders and double-curved "
+                         "channels, inputs De, kind, R2/R1, aspect, r, theta, z)")
+    ap.add_argument("--chunk", type=int, default=500)
+    ap.add_argument("--save", default=None, help="--mixed: write the trained network here (.npz)")
+    ap.add_argument("--check-every", type=int, default=10_000)
     ap.add_argument("--out", default=None)
     a = ap.parse_args()
     L.load_library()
+    if a.mixed:
+        r = run_mixed(a.train, a.test, chunk=a.chunk, epochs=a.epochs, max_steps=a.max_steps,
+                      check_every=a.check_every, save=a.save)
+        print(json.dumps({k: v for k, v in r.items() if k != "test"}, indent=1))
+        if a.out:
+            with open(a.out, "w") as f:
+                json.dump(r, f)
+        raise SystemExit(0)
     r = run(a.train, a.test, epochs=a.epochs, max_steps=a.max_steps)
     print(json.dumps({k: v for k, v in r.items() if not isinstance(v, list)}, indent=1))
     if a.out:

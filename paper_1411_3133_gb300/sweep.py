@@ -91,11 +91,13 @@ def critical_dean(deans, sigmas):
 
 def run_sweep(spec: L.ChannelSpec, taus, deans, steps: int, sample_every: int = 1000,
               precision: str = "fp32", seed: int = 20241111, noise_amp: float = 1e-4,
-              use_graph: bool = True, capture_at: int = 20_000) -> SweepResult:
+              use_graph: bool = True, capture_at: int = 20_000, init_fields=None) -> SweepResult:
     """One batched run: instance b has tau = taus[b] and target De = deans[b].
     With 2-byte storage the developed laminar state becomes the storage
     reference at step `capture_at` (lb_capture_reference), before the
-    vortices have grown out of the noise floor."""
+    vortices have grown out of the noise floor. init_fields (rho (B, N), u
+    (B, 3, N)): start from these fields (lb_init_fields, e.g. a surrogate's
+    prediction) instead of the laminar profile plus noise."""
     import time
 
     import torch
@@ -109,7 +111,11 @@ def run_sweep(spec: L.ChannelSpec, taus, deans, steps: int, sample_every: int = 
     ctx = L.LBContext(spec, batch=len(taus), precision=precision)
     ctx.lb_set_option(L.LB_OPT_USE_GRAPH, int(use_graph))
     ctx.lb_set_option(L.LB_OPT_CHECK_EVERY, 0)
-    ctx.lb_init(params)
+    if init_fields is None:
+        ctx.lb_init(params)
+    else:
+        ctx.lb_init_fields(params, np.ascontiguousarray(init_fields[0], dtype=np.float64),
+                           np.ascontiguousarray(init_fields[1], dtype=np.float64))
     ts, amps, des, vort = [], [], [], []
     t0 = time.perf_counter()
     done = 0
@@ -279,6 +285,79 @@ def compare_time_to_critical_dean(steps=300_000, sample_every=2000, modes=None):
     return out
 
 
+def critical_dean_fixed(res: SweepResult):
+    """The estimator of the combined-sweep comparison, one rule for every
+    mode: per tau, the A^2 line (critical_dean_saturation, four points)
+    through the final amplitudes of the instances is_saturated marks, the
+    floor taken as in summarize, against the *target* Dean numbers (the
+    force of lb_force_for_dean): a warm-started run has no laminar phase in
+    which to measure De, and at eta = 0.975 the laminar flow's measured De
+    sits within 0.2 % of the target. {tau: De_c}."""
+    out = {}
+    S = len(res.times)
+    for tau in sorted(set(res.taus)):
+        idx = [b for b, t in enumerate(res.taus) if t == tau]
+        de = np.array([res.deans[b] for b in idx], float)
+        a_fin = np.array([float(np.nanmean(res.amp[-max(2, S // 8):, b])) for b in idx])
+        quiet = a_fin[a_fin < 1e-5]
+        floor = float(np.median(quiet)) if len(quiet) else 1e-7
+        sat = np.array([is_saturated(res.amp[:, b], floor) for b in idx])
+        out[tau] = critical_dean_saturation(de, a_fin, floor, saturated=sat)
+    return out
+
+
+def combined_sweep(net_path, steps=300_000, sample_every=2000, precision="fp16_shifted", baseline=True,
+                   noise_amp=1e-4, seed=20241111):
+    """The whole pattern on the narrow-gap sweep (64 x 4 x 256 cylinder, eta
+    = 0.975, 12 De in [25, 60] x tau in {0.55, 0.6}): every instance starts
+    from the mixed surrogate's prediction (surrogate.predict_mixed of the
+    saved network, plus the sweep's seeded noise), all 24 run in one batched
+    launch per step (graph replay) in 2-byte storage with the laminar state
+    captured as the storage reference at step 20 000, and De_c comes from
+    critical_dean_fixed. With baseline, the plain FP64 sweep (instances one
+    after another, laminar profile plus noise, the same steps) runs first
+    and is estimated by the same rule. Wall times include the surrogate's
+    inference, not its training."""
+    import time
+
+    import torch
+
+    from . import surrogate as SG
+    from .workloads import Instance, noise_field
+    spec = L.ChannelSpec("cylindrical", 1.0, 1 / 0.975, 64, 4, 256)
+    deans = list(np.linspace(25.0, 60.0, 12))
+    taus = [0.55] * 12 + [0.6] * 12
+    deans2 = deans + deans
+    out = {"steps": steps, "precision": precision, "estimator": "critical_dean_fixed"}
+    if baseline:
+        res = run_sweep_sequential(spec, taus, deans2, steps, sample_every, "fp64", seed, noise_amp)
+        out["fp64_sequential"] = {"seconds": res.seconds,
+                                  "De_c": {str(t): v for t, v in critical_dean_fixed(res).items()},
+                                  "De_c_measured_de": {str(t): v["De_c"] for t, v in summarize(res).items()}}
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    net = SG.load_mixed_net(net_path)
+    N = spec.ncells
+    rho = np.empty((24, N))
+    u = np.empty((24, 3, N))
+    for b, (tau, de) in enumerate(zip(taus, deans2)):
+        inst = Instance("cylindrical", 1.0, 1 / 0.975, 64, 4, 256, tau, de, seed + b)
+        rho[b], u[b] = SG.predict_mixed(net, inst, 4)
+        u[b] += noise_field(seed + b, N, noise_amp).T
+    net.close()
+    t_inf = time.perf_counter() - t0
+    res = run_sweep(spec, taus, deans2, steps, sample_every, precision, seed, noise_amp, init_fields=(rho, u))
+    total = time.perf_counter() - t0
+    out["combined"] = {"seconds": total, "inference_seconds": t_inf, "lb_seconds": res.seconds,
+                       "De_c": {str(t): v for t, v in critical_dean_fixed(res).items()},
+                       "a_final": res.amp[-1].tolist()}
+    if baseline:
+        ref = out["fp64_sequential"]
+        out["speedup"] = ref["seconds"] / total
+        out["De_c_rel_err"] = {t: out["combined"]["De_c"][t] / ref["De_c"][t] - 1.0 for t in ref["De_c"]}
+    return out
+
+
 def critical_dean_knee(deans, w):
     """De_c of an imperfect bifurcation read off the mean-vorticity curve
     <omega>(De) (Sec. IV: the double-curved channel carries a secondary flow
@@ -341,6 +420,16 @@ def vortex_cells(u_r, nr, ntheta, n3, rel=0.2, periodic=True, weights=None):
     return int(np.count_nonzero(sig[1:] != sig[:-1]))
 
 
+def first_dean_with_cells(deans, cells, n):
+    """Smallest Dean number whose final state has at least n Dean cells
+    (vortex_cells), or NaN when none has: the measured onset of the 4- and
+    6-cell flows of Sec. IV.B on the sampled Dean numbers."""
+    d = np.asarray(deans, float)
+    c = np.asarray(cells)
+    hit = d[c >= n]
+    return float(hit.min()) if hit.size else float("nan")
+
+
 def decay_rate(t, A, floor, skip_frac=0.25, above=100.0):
     """Slope of ln A over the samples after the first skip_frac of the run that
     lie above `above` x the round-off floor: the decay rate (negative) of a
@@ -390,6 +479,19 @@ def develop_donor(spec: L.ChannelSpec, tau, donor_dean, donor_steps=400_000, pre
         return donor.lb_get_populations(), amp
     finally:
         donor.close()
+
+
+def donor_cells(spec: L.ChannelSpec, f_donor, tau):
+    """Dean cells of a donor state (host populations (1, Q, N)): loaded into
+    a scratch context, its u^r counted by vortex_cells (periodic x3)."""
+    ctx = L.LBContext(spec, batch=1, precision="fp64")
+    try:
+        ctx.lb_init([L.make_params(tau, 0.0, False, 0, 0.0, False)])
+        ctx.lb_set_populations(np.ascontiguousarray(f_donor, dtype=np.float64))
+        _, u = ctx.lb_macros()
+        return vortex_cells(u[0, 0], spec.nr, spec.ntheta, spec.n3, periodic=bool(spec.periodic3))
+    finally:
+        ctx.close()
 
 
 def continue_from(spec: L.ChannelSpec, tau, deans, f_donor, steps=400_000, sample_every=2000,
@@ -560,6 +662,11 @@ def double_curved_study(cases, deans=None, steps=300_000, sample_every=2000, tau
             des[k].append([x["dean"] for x in dg])
     torch.cuda.synchronize()
     sec = time.perf_counter() - t0
+    # Dean cells of the final state of every instance (periodic phi)
+    cells = []
+    for ctx in ctxs:
+        _, u = ctx.lb_macros()
+        cells.append([vortex_cells(u[i, 0], nr, ntheta, n3, periodic=True) for i in range(u.shape[0])])
     out = {"seconds": sec, "steps": steps, "nodes": batch.lb_batch_nodes(), "cases": []}
     for k, (label, ri, b) in enumerate(cases):
         A = np.array(amps[k])
@@ -574,11 +681,51 @@ def double_curved_study(cases, deans=None, steps=300_000, sample_every=2000, tau
                              "dean_target": kept[k], "dean": de.tolist(),
                              "vorticity": w_fin.tolist(), "a_final": A[-max(2, S // 8):].mean(axis=0).tolist(),
                              "drift": drift.tolist(),
+                             "cells": cells[k],
+                             "De_4cell": first_dean_with_cells(de, cells[k], 4),
+                             "De_6cell": first_dean_with_cells(de, cells[k], 6),
                              "De_c": critical_dean_knee(de, w_fin)})
     batch.close()
     for c in ctxs:
         c.close()
     return out
+
+
+def forcing_comparison(etas=(0.8, 0.9, 0.975), forcings=(0, 1), steps=400_000, sample_every=2000,
+                       tau=0.9, n=16, precision="fp32", donor_factors=(1.1, 1.18, 1.26, 1.35)):
+    """De_c(eta) of the cylinder (Sec. III: 129 x 1 x 256 nodes with the
+    paper's equilibrium walls, L_z / L_r = 2, tau = 0.9) with the improved
+    forcing (old_forcing 0: the non-equilibrium stress in the forcing term's
+    second-order coefficient) and the old one of the earlier publication
+    (old_forcing 1: that coefficient from the equilibrium alone), the
+    comparison of Sec. III (Fig. 4). Each pair continues n Dean numbers in
+    [0.8, 1.25] x a first guess 36 + 60 (1 - eta) from a donor at the first
+    of donor_factors x the guess whose developed state holds exactly two
+    Dean cells (donor_cells). Returns one row per (eta, forcing)."""
+    import time
+    rows = []
+    for eta in etas:
+        guess = 36.0 + 60.0 * (1.0 - eta)
+        deans = list(np.linspace(0.8 * guess, 1.25 * guess, n))
+        spec = L.ChannelSpec("cylindrical", 1.0, 1.0 / eta, 129, 1, 256, wall="equilibrium")
+        for fo in forcings:
+            # the donor must carry the 2-cell vortex: a donor above the second
+            # bifurcation (4 cells) continues the 4-cell branch, whose lower
+            # end lies above the first threshold
+            t0 = time.perf_counter()
+            tried = []
+            for fac in donor_factors:
+                f, amp = develop_donor(spec, tau, fac * guess, steps, precision, forcing=fo)
+                cells = donor_cells(spec, f, tau) if amp > 1e-4 else 0
+                tried.append({"donor_dean": fac * guess, "amp": amp, "cells": cells})
+                if cells == 2:
+                    break
+            r = continue_from(spec, tau, deans, f, steps, sample_every, precision, forcing=fo)
+            r["donor_amp"], r["donor_dean"], r["donors_tried"] = amp, fac * guess, tried
+            r["seconds"] = time.perf_counter() - t0
+            rows.append({"eta": eta, "old_forcing": fo, "deans_target": deans,
+                         **{k: v for k, v in r.items() if k not in ("amp", "times")}})
+    return rows
 
 
 def streamwise_curvature_cases(bs=(0.8, 0.85, 0.9, 0.95, 1.0, 1.05, 1.1, 1.2)):
@@ -610,10 +757,37 @@ if __name__ == "__main__":
     ap.add_argument("--forcing", type=int, default=0,
                     help="lb_params.old_forcing for --continuation: 0 the paper's improved forcing, "
                          "2 the half-force velocity variant")
+    ap.add_argument("--combined", default=None, metavar="NET",
+                    help="the combined sweep (surrogate warm start from the saved network NET, batched, "
+                         "2-byte storage) against the plain FP64 sweep")
+    ap.add_argument("--no-baseline", action="store_true", help="--combined: skip the FP64 sweep")
+    ap.add_argument("--forcing-comparison", action="store_true",
+                    help="De_c(eta) at eta 0.8, 0.9, 0.975 with the improved and the old forcing (Sec. III, "
+                         "129 x 1 x 256, tau 0.9), by continuation")
     ap.add_argument("--precisions", action="store_true",
                     help="De_c of the 64 x 4 x 256 narrow-gap sweep by continuation in every storage precision")
     a = ap.parse_args()
     L.load_library()
+    if a.combined:
+        r = combined_sweep(a.combined, steps=a.steps, sample_every=a.sample_every,
+                           baseline=not a.no_baseline)
+        print(json.dumps({k: ({kk: vv for kk, vv in v.items() if kk != "a_final"} if isinstance(v, dict) else v)
+                          for k, v in r.items()}, indent=1))
+        if a.out:
+            with open(a.out, "w") as f:
+                json.dump(r, f)
+        raise SystemExit(0)
+    if a.forcing_comparison:
+        rows = forcing_comparison(steps=a.steps, sample_every=a.sample_every)
+        for r in rows:
+            print("eta %.3f old_forcing %d  De_c %.2f (A^2 line) %.2f (decay line)  bracket %s  donor De %.1f "
+                  "(%s)  %.1f s" %
+                  (r["eta"], r["old_forcing"], r["De_c_saturation"], r["De_c_decay"], r["De_c_bracket"],
+                   r["donor_dean"], r["donors_tried"], r["seconds"]))
+        if a.out:
+            with open(a.out, "w") as f:
+                json.dump(rows, f)
+        raise SystemExit(0)
     if a.precisions:
         modes = [m for m in a.modes.split(",") if m != "fp64_sequential"]
         r = compare_precisions_continuation(modes=modes, steps=a.steps,
@@ -628,8 +802,10 @@ if __name__ == "__main__":
         r = double_curved_study(streamwise_curvature_cases() + cross_section_curvature_cases(),
                                 steps=a.steps, sample_every=a.sample_every)
         for c in r["cases"]:
-            print("%-10s R_theta %.3f R_phi %.2f De_c %.2f  max drift %.3f" %
-                  (c["label"], c["R_theta"], c["R_phi"], c["De_c"], max(c["drift"])))
+            print("%-10s R_theta %.3f R_phi %.2f De_c %.2f  4-cell from De %.1f  6-cell from De %.1f  "
+                  "cells %s  max drift %.3f" %
+                  (c["label"], c["R_theta"], c["R_phi"], c["De_c"], c["De_4cell"], c["De_6cell"],
+                   c["cells"], max(c["drift"])))
         print("seconds %.1f  nodes %d" % (r["seconds"], r["nodes"]))
         if a.out:
             with open(a.out, "w") as f:

@@ -15,16 +15,16 @@ def bf16(a):
     return ((b + r) & 0xFFFF0000).astype(np.uint32).view(np.float32)
 
 
-def layer_shapes(n_fourier, width, depth):
-    nin = 2 + 2 * n_fourier
+def layer_shapes(n_fourier, width, depth, n_plain=2):
+    nin = n_plain + 2 * n_fourier
     fi = [nin] + [width] * (depth - 1)
     fo = [width] * (depth - 1) + [NOUT]
     return list(zip(fo, fi))
 
 
-def unpack(params, n_fourier, width, depth):
+def unpack(params, n_fourier, width, depth, n_plain=2):
     out, k = [], 0
-    for fo, fi in layer_shapes(n_fourier, width, depth):
+    for fo, fi in layer_shapes(n_fourier, width, depth, n_plain):
         W = params[k:k + fo * fi].reshape(fo, fi)
         k += fo * fi
         b = params[k:k + fo]
@@ -35,8 +35,9 @@ def unpack(params, n_fourier, width, depth):
 
 
 def features(x, n_fourier):
-    de, r, z = x[:, 0], x[:, 1], x[:, 2]
-    cols = [de, r]
+    """Rows (p_1 .. p_P, z): the plain inputs, then sin, cos(2 pi k z)."""
+    z = x[:, -1]
+    cols = [x[:, j] for j in range(x.shape[1] - 1)]
     for k in range(1, n_fourier + 1):
         cols += [np.sin(2 * np.pi * k * z), np.cos(2 * np.pi * k * z)]
     return np.stack(cols, axis=1).astype(np.float64)
@@ -50,7 +51,7 @@ def forward(params, x, n_fourier, width, depth):
     """Normalised outputs and the per-layer (input, pre-activation) cache."""
     h = features(np.asarray(x, np.float64), n_fourier)
     cache = []
-    layers = unpack(params, n_fourier, width, depth)
+    layers = unpack(params, n_fourier, width, depth, np.shape(x)[1] - 1)
     for l, (W, b) in enumerate(layers):
         z = h @ bf16(W).astype(np.float64).T + b
         cache.append((h, z))
@@ -65,7 +66,7 @@ def grads(params, x, y, mean, std, n_fourier, width, depth):
     n = len(x)
     loss = ((Y - T) ** 2).mean()
     dz = 2.0 * (Y - T) / (n * NOUT)
-    layers = unpack(params, n_fourier, width, depth)
+    layers = unpack(params, n_fourier, width, depth, np.shape(x)[1] - 1)
     g = []
     for l in range(len(layers) - 1, -1, -1):
         h, z = cache[l]

@@ -171,10 +171,12 @@ def test_batch_entry_points_reject_bad_arguments_without_a_gpu(L):
 def test_mlp_create_rejects_bad_arguments_without_a_gpu(L):
     lib = L.load_library()
     out = ctypes.c_void_p(5)
-    assert lib.lb_mlp_create(2, 2, 5, 16, 1, None, ctypes.byref(out)) == L.LB_ERR_ARG
+    assert lib.lb_mlp_create(2, 2, 2, 5, 16, 1, None, ctypes.byref(out)) == L.LB_ERR_ARG
     assert out.value is None
-    assert lib.lb_mlp_create(2, 64, 1, 16, 1, None, ctypes.byref(out)) == L.LB_ERR_ARG
+    assert lib.lb_mlp_create(2, 2, 64, 1, 16, 1, None, ctypes.byref(out)) == L.LB_ERR_ARG
     assert b"width" in lib.lb_mlp_last_error(None)
+    assert lib.lb_mlp_create(0, 2, 64, 3, 16, 1, None, ctypes.byref(out)) == L.LB_ERR_ARG
+    assert b"n_plain" in lib.lb_mlp_last_error(None)
     assert lib.lb_mlp_param_count(None) == 0
     lib.lb_mlp_destroy(None)
 

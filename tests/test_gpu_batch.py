@@ -130,12 +130,12 @@ def test_batch_autotune_steps_are_real_steps():
     batched, alone = _contexts("fp32"), _contexts("fp32")
     batch = L.LBBatch(batched)
     best, trials = batch.lb_batch_autotune(steps_per_trial=3)
-    assert len(trials) == 6                               # FP32: blocks up to 128
-    assert {(t["block_threads"], t["schedule"]) for t in trials} == \
-        {(t, s) for t in (64, 96, 128) for s in (0, 1)}
+    assert len(trials) == 18                              # FP32: blocks up to 128
+    assert {(t["block_threads"], t["schedule"], t["tile_nodes"]) for t in trials} == \
+        {(t, s, t * k) for t in (64, 96, 128) for s in (0, 1) for k in (1, 2, 4)}
     assert all(t["ms_per_step"] > 0 for t in trials)
     assert best["ms_per_step"] == min(t["ms_per_step"] for t in trials)
-    steps = 6 * (3 + 1)
+    steps = 18 * (3 + 1)
     assert batch.lb_batch_step_count() == steps
     batch.lb_batch_step(5)          # with the chosen configuration
     for c in alone:
@@ -153,17 +153,16 @@ def test_context_autotune_steps_are_real_steps():
     a.lb_init(params)
     b.lb_init(params)
     best, trials = a.lb_autotune(steps_per_trial=2)
-    # three block sizes for the plain, region-split and tiled kernels, the
-    # TMA kernel (n3 = 128), six prefetching configurations
-    assert len(trials) == 16
-    assert {t["schedule"] for t in trials} == {1, 2, 3, 4, 5}
+    # three block sizes for the plain, region-split and tiled kernels, and
+    # the TMA kernel (n3 = 128)
+    assert len(trials) == 10
+    assert {t["schedule"] for t in trials} == {1, 2, 4, 5}
     for k in (1, 4, 5):
         assert {t["block_threads"] for t in trials if t["schedule"] == k} == {64, 96, 128}
-    assert {(t["block_threads"], t["nodes_per_thread"]) for t in trials if t["schedule"] == 3} == \
-        {(t, n) for t in (128, 256) for n in (2, 4, 8)}
+    assert all(t["tile_nodes"] == 0 for t in trials)
     assert best["ms_per_step"] == min(t["ms_per_step"] for t in trials)
-    assert a.lb_step_count() == 16 * 3
-    b.lb_step(48)
+    assert a.lb_step_count() == 10 * 3
+    b.lb_step(30)
     assert np.array_equal(_state(a), _state(b))
     a.close()
     b.close()

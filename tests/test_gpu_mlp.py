@@ -9,31 +9,43 @@ from mlp_reference import adam_step, forward, grads, unpack
 
 pytestmark = pytest.mark.gpu
 
-NF, W, D = 3, 40, 4          # small enough for an exact numpy check, ragged vs the 64-wide tiles
+# (n_fourier, width, depth, plain inputs): a small net, ragged against the
+# 64-wide tiles of the products; and the surrogate's own shape (5 layers of
+# 256, six plain inputs), which spans several tiles in every dimension
+SHAPES = {"small": (3, 40, 4, 2), "surrogate": (4, 256, 5, 6)}
 
 
-def _net(max_batch=300, seed=7):
+@pytest.fixture(params=list(SHAPES), ids=list(SHAPES))
+def shape(request):
+    return SHAPES[request.param]
+
+
+def _net(shape, max_batch=300, seed=7):
     L = lib()
-    return L.LBMlp(n_fourier=NF, width=W, depth=D, max_batch=max_batch, seed=seed)
+    nf, w, d, npl = shape
+    return L.LBMlp(n_fourier=nf, width=w, depth=d, max_batch=max_batch, seed=seed, n_plain=npl)
 
 
-def _inputs(n, seed):
+def _inputs(n, seed, n_plain=2):
     rng = np.random.default_rng(seed)
-    x = np.stack([rng.uniform(0.2, 0.8, n), rng.uniform(0, 1, n), rng.uniform(0, 1, n)], axis=1)
-    y = np.stack([1 + 0.01 * np.sin(2 * np.pi * x[:, 2]), x[:, 0] * np.sin(np.pi * x[:, 1]),
-                  x[:, 1] * (1 - x[:, 1]), 0.1 * np.cos(2 * np.pi * x[:, 2]) * x[:, 0]], axis=1)
+    cols = [rng.uniform(0.2, 0.8, n)] + [rng.uniform(0, 1, n) for _ in range(n_plain)]
+    x = np.stack(cols, axis=1)          # (De-like, ..., r-like, z)
+    a, r, z = x[:, 0], x[:, n_plain - 1], x[:, n_plain]
+    y = np.stack([1 + 0.01 * np.sin(2 * np.pi * z), a * np.sin(np.pi * r),
+                  r * (1 - r), 0.1 * np.cos(2 * np.pi * z) * a], axis=1)
     return x.astype(np.float32), y.astype(np.float32)
 
 
-def test_forward_matches_reference():
+def test_forward_matches_reference(shape):
     import torch
-    net = _net()
+    NF, W, D, NP = shape
+    net = _net(shape)
     rng = np.random.default_rng(3)
-    p = rng.normal(0, 0.3, net.param_count()).astype(np.float32)
+    p = rng.normal(0, 0.3 * (40 / W) ** 0.5, net.param_count()).astype(np.float32)
     net.set_params(p)
     mean, std = np.array([1.0, 0.1, 0.2, 0.0], np.float32), np.array([0.5, 2.0, 1.0, 0.25], np.float32)
     net.set_output_scale(mean, std)
-    x, _ = _inputs(257, 1)
+    x, _ = _inputs(257, 1, NP)
     y = net.predict(torch.from_numpy(x).cuda()).cpu().numpy()
     Y, _ = forward(p.astype(np.float64), x, NF, W, D)
     ref = Y * std + mean
@@ -41,14 +53,15 @@ def test_forward_matches_reference():
     net.close()
 
 
-def test_gradients_and_adam_step_match_reference():
+def test_gradients_and_adam_step_match_reference(shape):
     import torch
-    net = _net()
+    NF, W, D, NP = shape
+    net = _net(shape)
     p0 = net.get_params()
-    assert np.all(np.concatenate([b for _, b in unpack(p0, NF, W, D)]) == 0)   # zero biases
+    assert np.all(np.concatenate([b for _, b in unpack(p0, NF, W, D, NP)]) == 0)   # zero biases
     mean, std = np.array([1.0, 0.0, 0.1, 0.0], np.float32), np.array([0.01, 0.5, 0.1, 0.05], np.float32)
     net.set_output_scale(mean, std)
-    x, y = _inputs(300, 2)
+    x, y = _inputs(300, 2, NP)
     loss = net.train_step(torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda(), 1e-3)
     g = net.get_grads()
     loss_ref, g_ref = grads(p0.astype(np.float64), x, y, mean, std, NF, W, D)
@@ -60,10 +73,10 @@ def test_gradients_and_adam_step_match_reference():
     net.close()
 
 
-def test_training_fits_a_smooth_field():
+def test_training_fits_a_smooth_field(shape):
     import torch
-    net = _net(max_batch=4096, seed=11)
-    x, y = _inputs(4096, 5)
+    net = _net(shape, max_batch=4096, seed=11)
+    x, y = _inputs(4096, 5, shape[3])
     net.set_output_scale(y.mean(axis=0), y.std(axis=0))
     xd, yd = torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()
     first = net.train_step(xd, yd, 3e-3)
@@ -80,7 +93,7 @@ def test_argument_errors():
     with pytest.raises(L.LBError) as e:
         L.LBMlp(n_fourier=2, width=2, depth=5)
     assert e.value.status == L.LB_ERR_ARG
-    net = _net(max_batch=16)
+    net = _net(SHAPES["small"], max_batch=16)
     x = torch.zeros((17, 3), device="cuda")
     with pytest.raises(L.LBError) as e:
         net.predict(x)

@@ -421,33 +421,6 @@ def test_tma_kernel_is_bitwise_equal_to_plain_kernel(ch, batch):
     assert np.array_equal(outs[0], outs[1])
 
 
-@pytest.mark.parametrize("precision", ["fp32", "fp64", "fp16_shifted", "bf16_shifted"])
-@pytest.mark.parametrize("ch,batch", [
-    (Channel("cylindrical", 1.0, 1 / ETA, 16, 4, 256), 2),
-    (Channel("cylindrical", 1.0, 1 / 0.9, 9, 3, 13), 3),
-    (Channel("ellipsoidal", 1.0, 1.1, 12, 3, 40, b=0.9, periodic3=False), 1),
-    (Channel("flat", 0.0, 1.0, 8, 2, 9, periodic3=False), 2),
-], ids=["cyl256", "cyl_ragged", "ell4wall", "flat4wall"])
-def test_prefetching_kernel_is_bitwise_equal_to_plain_kernel(ch, batch, precision):
-    """The cp.async prefetching kernel (several nodes per thread, ragged last
-    block) gives the plain kernel's states bit for bit."""
-    L = lib()
-    params = [dict(tau=0.6 + 0.1 * b, G=2e-4, seed=50 + b, amp=1e-2) for b in range(batch)]
-    outs = []
-    for kern, threads, npt in ((1, 128, 1), (3, 64, 1), (3, 128, 3), (3, 256, 8)):
-        tw = Twin(ch, params, precision)
-        tw.ctx.lb_set_option(L.LB_OPT_STEP_KERNEL, kern)
-        tw.ctx.lb_set_option(L.LB_OPT_BLOCK_THREADS, threads)
-        tw.ctx.lb_set_option(L.LB_OPT_NODES_PER_THREAD, npt)
-        tw.ctx.lb_set_option(L.LB_OPT_USE_GRAPH, 1)
-        tw.ctx.lb_init(tw.lparams)
-        tw.ctx.lb_step(21)
-        outs.append(tw.ctx.lb_get_populations())
-        tw.close()
-    for o in outs[1:]:
-        assert np.array_equal(outs[0], o)
-
-
 @pytest.mark.parametrize("precision", ["fp32", "fp64", "bf16_shifted"])
 @pytest.mark.parametrize("ch,batch", [
     (Channel("cylindrical", 1.0, 1 / ETA, 16, 4, 256), 2),
@@ -505,15 +478,13 @@ def test_tiled_step_is_bitwise_equal_to_plain_kernel(ch, batch, precision):
         assert np.array_equal(outs[0], o)
 
 
-def test_prefetching_kernel_option_validation():
+def test_step_kernel_option_validation():
     L = lib()
     tw = Twin(CYL1, [dict(tau=0.8)], "fp16_shifted")
-    with pytest.raises(L.LBError) as e:
-        tw.ctx.lb_set_option(L.LB_OPT_STEP_KERNEL, 6)
-    assert e.value.status == L.LB_ERR_ARG
-    for bad in (0, 65):
-        with pytest.raises(L.LBError):
-            tw.ctx.lb_set_option(L.LB_OPT_NODES_PER_THREAD, bad)
+    for bad in (3, 6, -1):                 # 3: the prefetching kernel, no longer built
+        with pytest.raises(L.LBError) as e:
+            tw.ctx.lb_set_option(L.LB_OPT_STEP_KERNEL, bad)
+        assert e.value.status == L.LB_ERR_ARG
     tw.close()
 
 
