@@ -269,15 +269,16 @@ cudaError_t launch_lane(const lb_batch* b, const Group& gr, int m, cudaStream_t 
   const int* cells = reinterpret_cast<const int*>(base + gr.cells_off);
   const int grid = b->schedule == 1 ? std::max(1, gr.blocks_per_sm) * b->nsm : 0;
   const int4* work = reinterpret_cast<const int4*>(base + gr.work_off[m]);
+  const int sel = m | (b->built_tile_blocks > 1 ? 2 : 0);  // wall-node tiles; multi-block tiles
   switch (b->prec) {
     case LB_FP64:
-      return launch_step_list_f64(gr.K, m, insts, work, gr.nwork[m], cells, b->threads, grid, b->parity, s);
+      return launch_step_list_f64(gr.K, sel, insts, work, gr.nwork[m], cells, b->threads, grid, b->parity, s);
     case LB_FP32:
-      return launch_step_list_f32(gr.K, m, insts, work, gr.nwork[m], cells, b->threads, grid, b->parity, s);
+      return launch_step_list_f32(gr.K, sel, insts, work, gr.nwork[m], cells, b->threads, grid, b->parity, s);
     case LB_FP16_SHIFTED:
-      return launch_step_list_h16(gr.K, m, insts, work, gr.nwork[m], cells, b->threads, grid, b->parity, s);
+      return launch_step_list_h16(gr.K, sel, insts, work, gr.nwork[m], cells, b->threads, grid, b->parity, s);
     default:
-      return launch_step_list_b16(gr.K, m, insts, work, gr.nwork[m], cells, b->threads, grid, b->parity, s);
+      return launch_step_list_b16(gr.K, sel, insts, work, gr.nwork[m], cells, b->threads, grid, b->parity, s);
   }
 }
 

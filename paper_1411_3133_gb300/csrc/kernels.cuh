@@ -73,13 +73,14 @@ __device__ __forceinline__ void step_node(const S* __restrict__ fin, S* __restri
 }
 
 // Launch bounds of k_step per storage / compute type. FP32 arithmetic: at
-// most 128 threads per block and 6 (FP32 storage) or 5 (2-byte storage,
-// which also reads reference populations) resident blocks per SM, i.e. a
-// register cap that trades a few spilled values for more resident warps
-// (the kernel is bound by latency and issue, not by HBM alone; measured best
-// of 5..8). FP64 keeps its registers (bound
-// by the FP64 units). LBGM_STEP32_MAXT / LBGM_STEP32_MINB / LBGM_STEP16_MINB
-// override the FP32 values for tuning builds.
+// most 128 threads per block and 6 (FP32 storage) or 4 (2-byte storage,
+// whose stream-table reads and conversions need registers) resident blocks
+// per SM, i.e. a register cap that trades a few spilled values for more
+// resident warps (the FP32 kernel is bound by latency and issue as much as
+// by HBM; measured best of 5..8; the 2-byte kernels measured 4 > 5 > 6).
+// FP64 keeps its registers (bound by the FP64 units). LBGM_STEP32_MAXT /
+// LBGM_STEP32_MINB / LBGM_STEP16_MINB override the FP32 values for tuning
+// builds.
 #ifndef LBGM_STEP32_MAXT
 #define LBGM_STEP32_MAXT 128
 #endif
@@ -87,7 +88,7 @@ __device__ __forceinline__ void step_node(const S* __restrict__ fin, S* __restri
 #define LBGM_STEP32_MINB 6
 #endif
 #ifndef LBGM_STEP16_MINB
-#define LBGM_STEP16_MINB 5
+#define LBGM_STEP16_MINB 4
 #endif
 template <class S, class Real>
 struct StepBounds {
@@ -98,13 +99,15 @@ template <>
 struct StepBounds<double, double> {
   static constexpr int maxt = 256, minb = 1;
 };
-// Per metric kind: one block fewer per SM for the ellipsoid, whose (i_r,
-// i_3) geometry rows and extra Christoffel terms need more registers.
+// Per metric kind: one block fewer per SM for the ellipsoid with FP32
+// storage, whose (i_r, i_3) geometry rows and extra Christoffel terms need
+// more registers (the 2-byte kernels' cap already leaves room for them).
 template <class S, class Real, int K>
 struct KBounds {
   static constexpr int maxt = StepBounds<S, Real>::maxt;
-  static constexpr int minb = K == KELL && StepBounds<S, Real>::minb > 1 ? StepBounds<S, Real>::minb - 1
-                                                                          : StepBounds<S, Real>::minb;
+  static constexpr int minb = K == KELL && sizeof(S) != 2 && StepBounds<S, Real>::minb > 1
+                                  ? StepBounds<S, Real>::minb - 1
+                                  : StepBounds<S, Real>::minb;
 };
 // Uniform batch: fin/fout are whole states (batch blocks of Q * ncell);
 // block (x, y) updates nodes [x blockDim, (x + 1) blockDim) of instance y, so
@@ -139,8 +142,12 @@ __global__ void __launch_bounds__(KBounds<S, Real, K>::maxt, KBounds<S, Real, K>
   step_node<S, Real, K, 0>(fin + base, fout + base, ref_of(d, b), geo, inst[b], d, p, flag);
 }
 
+// Wall-layer kernel: 4 resident blocks per SM whatever the storage (no
+// spills with the six fold variants' address arithmetic; it runs beside the
+// interior kernel, which keeps the SMs' other slots; measured +1 % on the
+// whole FP32 step against the interior kernel's cap).
 template <typename S, typename Real, int K>
-__global__ void __launch_bounds__(KBounds<S, Real, K>::maxt, KBounds<S, Real, K>::minb)
+__global__ void __launch_bounds__(KBounds<S, Real, K>::maxt, KBounds<S, Real, K>::minb < 4 ? KBounds<S, Real, K>::minb : 4)
     k_step_edge(const S* __restrict__ fin, S* __restrict__ fout, GeoDev<Real> geo,
                 const InstParams<Real>* __restrict__ inst, Dims d, int* __restrict__ flag) {
   const uint32_t layer = uint32_t(d.nt) * uint32_t(d.n3);
@@ -170,8 +177,10 @@ struct ListInst {
 };
 
 // Work-list step over instances of one metric kind. Work item j = (instance,
-// first, count) covers `count` nodes of one instance (a tile of one or more
-// blocks' worth; thread t takes nodes t, t + blockDim.x, ...): with
+// first, count) covers `count` nodes of one instance: at most blockDim.x,
+// one per thread, or with MULTI a tile of several blocks' worth (thread t
+// takes nodes t, t + blockDim.x, ...; a separate instantiation, because the
+// loop costs the one-block tiles ~5 % on the four-wall ellipsoid): with
 // WALLS = 0 the interior nodes first .. first + count - 1 (no wall within 3
 // nodes: the far-from-wall gather alone), with WALLS = 2 the nodes
 // cells[first .. first + count - 1] (the wall nodes: folds, or clamps for
@@ -181,7 +190,7 @@ struct ListInst {
 // persistent grid when gridDim.x < nwork). `parity` 0 reads f0 and writes f1,
 // 1 the reverse. The instance record is staged once per item in shared
 // memory.
-template <typename S, typename Real, int K, int WALLS>
+template <typename S, typename Real, int K, int WALLS, bool MULTI>
 __global__ void __launch_bounds__(KBounds<S, Real, K>::maxt, KBounds<S, Real, K>::minb)
     k_step_list(const ListInst<S, Real>* __restrict__ insts, const int4* __restrict__ work, int nwork,
                 const int* __restrict__ cells, int parity) {
@@ -200,13 +209,18 @@ __global__ void __launch_bounds__(KBounds<S, Real, K>::maxt, KBounds<S, Real, K>
       sh.w[threadIdx.x] = reinterpret_cast<const uint32_t*>(insts + w.x)[threadIdx.x];
     __syncthreads();
     const ListInst<S, Real>& I = sh.rec;
-    for (int i = int(threadIdx.x); i < w.z; i += int(blockDim.x)) {
+    auto node = [&](int i) {
       const uint32_t t = WALLS == 0 ? uint32_t(w.y + i) : uint32_t(cells[w.y + i]);
       const Dims d = I.d;
       const CellPos p = locate(d, t);
       const S* fin = parity ? I.f1 : I.f0;
       S* fout = const_cast<S*>(parity ? I.f0 : I.f1);
       step_node<S, Real, K, WALLS>(fin, fout, d.ref, I.geo, *I.ip, d, p, I.flag);
+    };
+    if constexpr (MULTI) {
+      for (int i = int(threadIdx.x); i < w.z; i += int(blockDim.x)) node(i);
+    } else {
+      if (int(threadIdx.x) < w.z) node(int(threadIdx.x));
     }
   }
 }

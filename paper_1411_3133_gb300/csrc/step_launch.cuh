@@ -55,16 +55,20 @@ cudaError_t launch_step_split_t(int K, const S* fin, S* fout, const GeoDev<R>& g
 }
 
 // grid 0: one block per work item; otherwise `grid` persistent blocks.
-// walls 0: interior tiles (cells NULL); 1: wall-node tiles over `cells`.
+// walls bit 0 clear: interior tiles (cells NULL); set: wall-node tiles over
+// `cells`; bit 1: tiles of more than one block's worth of nodes.
 template <class S, class R>
 cudaError_t launch_step_list_t(int K, int walls, const void* insts, const int4* work, int nwork, const int* cells,
                                int threads, int grid, int parity, cudaStream_t s) {
   if (nwork == 0) return cudaSuccess;
   const auto* I = static_cast<const ListInst<S, R>*>(insts);
   const int g = grid > 0 && grid < nwork ? grid : nwork;
-#define LB_LIST(KK)                                                                          \
-  (walls ? (k_step_list<S, R, KK, 2><<<g, threads, 0, s>>>(I, work, nwork, cells, parity), 0) \
-         : (k_step_list<S, R, KK, 0><<<g, threads, 0, s>>>(I, work, nwork, cells, parity), 0))
+  const int sel = walls & 3;
+#define LB_LIST(KK)                                                                                       \
+  (sel == 0   ? (k_step_list<S, R, KK, 0, false><<<g, threads, 0, s>>>(I, work, nwork, cells, parity), 0) \
+   : sel == 1 ? (k_step_list<S, R, KK, 2, false><<<g, threads, 0, s>>>(I, work, nwork, cells, parity), 0) \
+   : sel == 2 ? (k_step_list<S, R, KK, 0, true><<<g, threads, 0, s>>>(I, work, nwork, cells, parity), 0)  \
+              : (k_step_list<S, R, KK, 2, true><<<g, threads, 0, s>>>(I, work, nwork, cells, parity), 0))
   switch (K) {
     case KFLAT: LB_LIST(KFLAT); break;
     case KCYL: LB_LIST(KCYL); break;
@@ -86,11 +90,14 @@ template <class S, class R>
 cudaError_t step_list_occupancy_t(int K, int threads, int* blocks_per_sm) {
   switch (K) {
     case KFLAT:
-      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_step_list<S, R, KFLAT, 0>, threads, 0);
+      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_step_list<S, R, KFLAT, 0, false>, threads,
+                                                           0);
     case KCYL:
-      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_step_list<S, R, KCYL, 0>, threads, 0);
+      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_step_list<S, R, KCYL, 0, false>, threads,
+                                                           0);
     case KELL:
-      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_step_list<S, R, KELL, 0>, threads, 0);
+      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_step_list<S, R, KELL, 0, false>, threads,
+                                                           0);
     default:
       return cudaErrorInvalidValue;
   }

@@ -662,11 +662,13 @@ def double_curved_study(cases, deans=None, steps=300_000, sample_every=2000, tau
             des[k].append([x["dean"] for x in dg])
     torch.cuda.synchronize()
     sec = time.perf_counter() - t0
-    # Dean cells of the final state of every instance (periodic phi)
-    cells = []
+    # Dean cells of the final state of every instance (periodic phi), and
+    # its mid-gap radial velocity along phi (theta mean)
+    cells, ur_mid = [], []
     for ctx in ctxs:
         _, u = ctx.lb_macros()
         cells.append([vortex_cells(u[i, 0], nr, ntheta, n3, periodic=True) for i in range(u.shape[0])])
+        ur_mid.append([u[i, 0].reshape(nr, ntheta, n3)[nr // 2].mean(axis=0).tolist() for i in range(u.shape[0])])
     out = {"seconds": sec, "steps": steps, "nodes": batch.lb_batch_nodes(), "cases": []}
     for k, (label, ri, b) in enumerate(cases):
         A = np.array(amps[k])
@@ -681,7 +683,7 @@ def double_curved_study(cases, deans=None, steps=300_000, sample_every=2000, tau
                              "dean_target": kept[k], "dean": de.tolist(),
                              "vorticity": w_fin.tolist(), "a_final": A[-max(2, S // 8):].mean(axis=0).tolist(),
                              "drift": drift.tolist(),
-                             "cells": cells[k],
+                             "cells": cells[k], "ur_midgap": ur_mid[k],
                              "De_4cell": first_dean_with_cells(de, cells[k], 4),
                              "De_6cell": first_dean_with_cells(de, cells[k], 6),
                              "De_c": critical_dean_knee(de, w_fin)})
