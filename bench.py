@@ -76,6 +76,25 @@ def measured_traffic():
     return profile_value(PROFILE_FILE, "dram_bytes_per_launch")
 
 
+# ncu summaries of the other timed configurations: DRAM bytes of one whole
+# step (all its kernels), valid for the step sources of that storage type
+STEP_SOURCES = {p: ["paper_1411_3133_gb300/csrc/lbm_device.cuh", "paper_1411_3133_gb300/csrc/kernels.cuh",
+                    "paper_1411_3133_gb300/csrc/step_launch.cuh", f"paper_1411_3133_gb300/csrc/step_{t}.cu",
+                    "paper_1411_3133_gb300/csrc/lattice.cuh"]
+                for p, t in (("fp32", "f32"), ("fp16_shifted", "h16"), ("bf16_shifted", "b16"))}
+STEP_PROFILES = {("sweep", "fp16_shifted"): "k_step_split_fp16_cyl64x4x256_b24.md",
+                 ("ellipsoid", "fp32"): "k_step_list_fp32_ell64x4x256_b24.md",
+                 ("mixed", "fp32"): "k_step_list_fp32_mixed128.md"}
+
+
+def step_traffic(workload, precision):
+    """DRAM bytes per step of a profiled (workload, precision), else None."""
+    name = STEP_PROFILES.get((workload, precision))
+    if name is None:
+        return None
+    return profile_value(os.path.join(ROOT, "profiles", name), "dram_bytes_per_step", STEP_SOURCES[precision])
+
+
 def measured_fp32_flops():
     """FP32 flops per lattice update of the region-split FP32 step, both
     kernels (ncu FFMA, FADD, FMUL thread-instruction counts, committed
@@ -517,7 +536,7 @@ def main():
     bpu = BYTES_PER_UPDATE[args.precision]
     achieved = bpu * cells / per_launch / 1e9
     peak, peak_kind = peaks()
-    traffic = measured_traffic() if runner.profiled else None
+    traffic = measured_traffic() if runner.profiled else step_traffic(args.workload, args.precision)
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
                 "unit": "GB/s", "frac": round(achieved / peak, 4),
                 "traffic": traffic, "peak_source": peak_kind,

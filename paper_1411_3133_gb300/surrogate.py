@@ -559,15 +559,18 @@ def run_mixed(n_train=2000, n_test=256, chunk=500, epochs=30, batch=16384, lr=2e
     for kind in ("cylindrical", "ellipsoidal"):
         sel = np.array([i.metric == kind for i in test_set])
         both = sel & okc & okw
+        fin = sel & np.isfinite(err_pred) & np.isfinite(err_final)
         rep[kind] = {
             "instances": int(sel.sum()), "converged_cold": int((sel & okc).sum()),
-            "converged_warm": int((sel & okw).sum()),
+            "converged_warm": int((sel & okw).sum()), "converged_both": int(both.sum()),
             "steps_cold_mean": float(sc[both].mean()) if both.any() else None,
             "steps_warm_mean": float(sw[both].mean()) if both.any() else None,
             "steps_saved_fraction": float(1.0 - sw[both].sum() / sc[both].sum()) if both.any() else None,
-            "surrogate_rel_l2_median": float(np.median(err_pred[sel])),
-            "surrogate_rel_l2_p90": float(np.percentile(err_pred[sel], 90)),
-            "warm_vs_cold_final_rel_l2_median": float(np.median(err_final[sel])),
+            "steps_saved_fraction_all_capped": float(1.0 - sw[sel].sum() / sc[sel].sum()),
+            "nonfinite_fields": int((sel & ~fin).sum()),
+            "surrogate_rel_l2_median": float(np.median(err_pred[fin])) if fin.any() else None,
+            "surrogate_rel_l2_p90": float(np.percentile(err_pred[fin], 90)) if fin.any() else None,
+            "warm_vs_cold_final_rel_l2_median": float(np.median(err_final[fin])) if fin.any() else None,
         }
     rep["test"] = [{"metric": i.metric, "nr": i.nr, "n3": i.n3, "dean": i.dean, "R2_over_R1": i.R2_over_R1,
                     "steps_cold": int(sc[k]), "steps_warm": int(sw[k]), "err_pred": float(err_pred[k]),

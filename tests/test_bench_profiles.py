@@ -32,3 +32,15 @@ def test_fp64_figures_hash_only_the_fp64_kernel_body(tmp_path):
     p = _summary(tmp_path, sha, "    fp64_flops_per_update: 1085")
     assert bench.profile_value(p, "fp64_flops_per_update", bench.FP64_KERNEL_SOURCES) == 1085.0
     assert bench.profile_value(p, "fp64_flops_per_update") is None
+
+
+def test_step_traffic_of_other_workloads(tmp_path, monkeypatch):
+    assert bench.step_traffic("sweep", "fp64") is None              # not profiled
+    sha = bench.kernel_source_hash(bench.STEP_SOURCES["fp32"])
+    p = _summary(tmp_path, sha, "    dram_bytes_per_step: 123456")
+    monkeypatch.setattr(bench, "STEP_PROFILES", {("ellipsoid", "fp32"): p})
+    assert bench.step_traffic("ellipsoid", "fp32") == 123456.0
+    q = _summary(tmp_path, bench.kernel_source_hash(bench.STEP_SOURCES["bf16_shifted"]),
+                 "    dram_bytes_per_step: 1")
+    monkeypatch.setattr(bench, "STEP_PROFILES", {("ellipsoid", "fp32"): q})
+    assert bench.step_traffic("ellipsoid", "fp32") is None          # another storage's sources

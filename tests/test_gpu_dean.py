@@ -64,3 +64,24 @@ def test_double_curved_study_runs_both_curvature_families():
         assert np.all(np.diff(c["dean"]) > 0)           # measured De follows the force
         assert isinstance(c["De_c"], float)
     assert r["cases"][1]["R_theta"] == pytest.approx(1.0)
+
+
+def test_developed_vortex_has_two_dean_cells():
+    """A supercritical narrow channel with the paper's cross-section shape
+    (L_z = 2 L_r, Sec. III: "perfectly adapted to the 2-cell vortex
+    solution") develops one pair of counter-rotating cells: u^r at mid-gap
+    changes sign twice along the periodic z (sweep.vortex_cells)."""
+    lib()
+    from paper_1411_3133_gb300 import lbgm as L
+    from paper_1411_3133_gb300.sweep import vortex_cells
+    spec = L.ChannelSpec("cylindrical", 1.0, 1 / 0.975, 32, 1, 64)
+    G = L.lb_force_for_dean("cylindrical", spec.desc(), 0.6, 44.0)
+    ctx = L.LBContext(spec, batch=1, precision="fp32")
+    ctx.lb_set_option(L.LB_OPT_USE_GRAPH, 1)
+    ctx.lb_init([L.make_params(0.6, G, False, 20241111, 1e-3, True)])
+    ctx.lb_step(400_000)
+    d = ctx.lb_diagnostics()[0]
+    _, u = ctx.lb_macros()
+    ctx.close()
+    assert d["vortex_amp_x3"] > 1e-3 * d["max_speed"], d       # developed, not noise
+    assert vortex_cells(u[0, 0], 32, 1, 64, periodic=True) == 2
