@@ -127,9 +127,8 @@ __global__ void __launch_bounds__(KBounds<S, Real, K>::maxt, KBounds<S, Real, K>
 // The same update split by region for channels periodic in x3, where only
 // the three node layers next to each r-wall need the wall rule: k_step_bulk
 // covers the contiguous interior layers 3 .. nr - 4 with the far-from-wall
-// gather alone, k_step_edge the 6 wall layers with the folds selected at run
-// time (gather_edge_rt: one code path for all six layers), so neither kernel
-// carries the other's code.
+// gather alone, k_step_edge the 6 wall layers with the per-layer constant
+// folds (gather_edge), so neither kernel carries the other's code.
 template <typename S, typename Real, int K>
 __global__ void __launch_bounds__(KBounds<S, Real, K>::maxt, KBounds<S, Real, K>::minb)
     k_step_bulk(const S* __restrict__ fin, S* __restrict__ fout, GeoDev<Real> geo,
@@ -160,7 +159,7 @@ __global__ void __launch_bounds__(KBounds<S, Real, K>::maxt, KBounds<S, Real, K>
   const size_t base = size_t(b) * Q * uint32_t(d.ncell);
   const float* ref = ref_of(d, b);
   Real f[Q];
-  gather_edge_rt<K, S, Real, Codec<S, Real>::uses_ref>(fin + base, ref, p, d, f);
+  gather_edge<K, S, Real, Codec<S, Real>::uses_ref>(fin + base, ref, p, d, f);
   collide_store<S, Real, K>(f, fout + base, ref, geo, inst[b], d, p, flag);
 }
 

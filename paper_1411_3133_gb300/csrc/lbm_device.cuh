@@ -465,50 +465,6 @@ __device__ __forceinline__ void for_each_source_layer(const S* __restrict__ fin,
   });
 }
 
-// The same sources as for_each_source_layer for a node J = 0, 1, 2 layers
-// from the r-wall on side `side`, with side and J known only at run time:
-// one code path for all six wall layers (the compile-time variants, one per
-// layer, made the wall-layer kernel wait on instruction fetch). A population
-// whose velocity points away from that wall (c^r > 0 at the inner wall, < 0
-// at the outer one) and whose path is long enough (J < s, s = |c|_inf)
-// folds once: its source is x + q sigma, q = s - 1 - 2 J, and it arrives as
-// the opposite population; every other population comes from x - c.
-template <int K, int CX, int CY, int CZ, int L, int LO, int S, class SP, class Fn>
-__device__ __forceinline__ void edge_source_rt(const SP* __restrict__ fin, const CellPos& p, const Dims& d,
-                                               const Neighbours& nb, int side, int J, Fn&& fn) {
-  const uint32_t N = uint32_t(d.ncell);
-  const uint32_t far = uint32_t(src_far<CX, CY, CZ>(nb, d));
-  if constexpr (CX == 0) {
-    fn(std::integral_constant<int, L>{}, fin + (uint32_t(L) * N + far), L, geo_row<K>(d, p.ir, nb.zcol[CZ + 3]));
-  } else {
-    constexpr int sx = CX > 0 ? 1 : -1, sy = (CY > 0) - (CY < 0), sz = (CZ > 0) - (CZ < 0);
-    const bool fold = side == (CX > 0 ? 0 : 1) && (S == 3 || J == 0);   // J < s within the three layers
-    const int q = S - 1 - 2 * J;
-    const int yr = p.ir + q * sx;
-    int yt = p.it, yz = p.i3;
-    if constexpr (sy != 0) yt = wrap_small(p.it + q * sy, d.nt);
-    if constexpr (sz != 0) yz = wrap_small(p.i3 + q * sz, d.n3);
-    const uint32_t fc = uint32_t((yr * d.nt + yt) * d.n3 + yz);
-    const uint32_t src = fold ? uint32_t(LO) * N + fc : uint32_t(L) * N + far;
-    const int sl = fold ? LO : L;
-    const int row = fold ? geo_row<K>(d, yr, yz) : geo_row<K>(d, p.ir - CX, nb.zcol[CZ + 3]);
-    fn(std::integral_constant<int, L>{}, fin + src, sl, row);
-  }
-}
-
-template <int K, class S, class Fn>
-__device__ __forceinline__ void for_each_source_edge_rt(const S* __restrict__ fin, const CellPos& p,
-                                                        const Dims& d, int side, int J, Fn&& fn) {
-  Neighbours nb;
-  make_neighbours(p, d, nb);
-  static_for<0, NPAIR>([&](auto P_) {
-    constexpr int P = decltype(P_)::value;
-    using C = Pair<P>;
-    edge_source_rt<K, C::x, C::y, C::z, 2 * P + 1, 2 * P + 2, C::s>(fin, p, d, nb, side, J, fn);
-    edge_source_rt<K, -C::x, -C::y, -C::z, 2 * P + 2, 2 * P + 1, C::s>(fin, p, d, nb, side, J, fn);
-  });
-}
-
 // Decoding visitor: f[L] from the stored value at src, with the reference
 // row table ref (instance base; NULL for FP32 / FP64 storage).
 template <int K, class S, class R>
@@ -573,16 +529,6 @@ template <int K, class S, class R, bool RAW = false>
 __device__ __forceinline__ void gather_edge(const S* __restrict__ fin, const float* ref, const CellPos& p,
                                             const Dims& d, R (&f)[Q]) {
   gather_edge_v<K>(fin, p, d, GatherPut<K, S, R, RAW>::make(f, ref, d));
-}
-
-// As gather_edge, through the run-time folds (for_each_source_edge_rt).
-template <int K, class S, class R, bool RAW = false>
-__device__ __forceinline__ void gather_edge_rt(const S* __restrict__ fin, const float* ref, const CellPos& p,
-                                               const Dims& d, R (&f)[Q]) {
-  const auto put = GatherPut<K, S, R, RAW>::make(f, ref, d);
-  put(std::integral_constant<int, 0>{}, fin + uint32_t(p.cell), 0, geo_row<K>(d, p.ir, p.i3));
-  const int side = p.ir < 3 ? 0 : 1;
-  for_each_source_edge_rt<K>(fin, p, d, side, side == 0 ? p.ir : d.nr - 1 - p.ir, put);
 }
 
 // Load the 41 streamed populations of node p from the post-collision state
