@@ -144,11 +144,18 @@ def test_fp64_laminar_5000_steps():
 
 
 def _smooth_flow(ch, amp=0.05):
-    """Streamwise flow vanishing on the walls of r (and x3 when walled)."""
+    """Streamwise flow vanishing on the walls of r (and x3 when walled): half
+    a node outside the end nodes for bounce-back walls, on the end nodes for
+    equilibrium walls (whose end nodes lie on the walls)."""
     ir, it, i3 = np.meshgrid(np.arange(ch.nr), np.arange(ch.ntheta), np.arange(ch.n3), indexing="ij")
-    prof = np.sin(np.pi * (ir + 0.5) / ch.nr)
-    if not ch.periodic3:
-        prof = prof * np.sin(np.pi * (i3 + 0.5) / ch.n3)
+    if ch.wall == "equilibrium":
+        prof = np.sin(np.pi * ir / (ch.nr - 1))
+        if not ch.periodic3:
+            prof = prof * np.sin(np.pi * i3 / (ch.n3 - 1))
+    else:
+        prof = np.sin(np.pi * (ir + 0.5) / ch.nr)
+        if not ch.periodic3:
+            prof = prof * np.sin(np.pi * (i3 + 0.5) / ch.n3)
     u = np.zeros(ch.shape + (3,))
     u[..., 1] = amp * prof
     return u.reshape(-1, 3)
@@ -629,4 +636,45 @@ def test_reduced_precision_state_round_trips(prec):
     tw.ctx.lb_set_state(buf)
     tw.ctx.lb_step(7)
     assert np.array_equal(tw.ctx.lb_get_populations(), b)
+    tw.close()
+
+
+@pytest.mark.parametrize("prec,tol", [("fp16_shifted", 1e-4), ("bf16_shifted", 1e-3)])
+@pytest.mark.parametrize("ch,kern", [
+    (Channel("flat", 0.0, 1.0, 8, 2, 9, periodic3=False), 0),                        # walls on x3: 7 row classes
+    (Channel("cylindrical", 1.0, 1 / ETA, 9, 3, 13, periodic3=False), 0),
+    (Channel("cylindrical", 1.0, 1 / ETA, 16, 2, 16, wall="equilibrium"), 0),        # wall nodes store f^eq
+    (Channel("ellipsoidal", 1.0, 1.1, 10, 3, 20, b=0.9, periodic3=False, wall="equilibrium"), 0),
+    (Channel("cylindrical", 1.0, 1 / ETA, 16, 4, 64), 4),                            # region split
+    (Channel("cylindrical", 1.0, 1 / ETA, 16, 4, 64), 5),                            # tiled
+], ids=["flat4wall", "cyl_walled_x3", "cyl_eqwall", "ell_eqwall", "cyl_split", "cyl_tiled"])
+def test_deviation_collision_every_stream_row_kind(ch, kern, prec, tol):
+    """The 2-byte collision runs on the stored deviations through a table per
+    stream row (i_r; (i_r, i_3) for the ellipsoid; (i_r, distance class to an
+    x3 wall) when x3 has walls), including equilibrium-wall nodes, which store
+    f^eq against the reference table: every kind against the FP64 oracle
+    after 1, 10 and 60 steps, in each step kernel that runs it. Where x3 has
+    walls but the geometry rows (and so the reference) are per i_r only, the
+    flow's x3 profile is not in the reference and is stored in 2 bytes: the
+    tolerance there is the reduced-precision bound of the target, 1e-3 u_max
+    (FP16), and 1e-2 u_max for BF16's 8-bit mantissa (as with the rest-state
+    reference). The channels are sized so that the laminar flow of the first
+    instance's force is about the initial one: the stored deviations then
+    stay small (a flow far from its reference, e.g. a 9-node channel whose
+    laminar speed is a quarter of the initial one, stores O(u_max)
+    deviations and needs the reference recaptured, lb_capture_reference)."""
+    L = lib()
+    if not ch.periodic3 and ch.metric != "ellipsoidal" and ch.wall == "bounceback":
+        tol *= 10
+    tw = Twin(ch, [dict(tau=0.8, G=G_LAMINAR), dict(tau=0.65, G=2 * G_LAMINAR)], prec)
+    if kern:
+        tw.ctx.lb_set_option(L.LB_OPT_STEP_KERNEL, kern)
+    rho = np.stack([1.0 / s.sqrtg for s in tw.sims])
+    u = np.stack([_smooth_flow(ch) + noise_field(41 + b, tw.N, 1e-3) for b in range(2)])
+    tw.init_fields(rho, u)
+    done = 0
+    for n in (1, 10, 60):
+        tw.step(n - done)
+        done = n
+        _compare_macros(tw, tol, tol)
     tw.close()
