@@ -307,7 +307,7 @@ def critical_dean_fixed(res: SweepResult):
 
 
 def combined_sweep(net_path, steps=300_000, sample_every=2000, precision="fp16_shifted", baseline=True,
-                   noise_amp=1e-4, seed=20241111):
+                   noise_amp=1e-4, seed=20241111, warm=True):
     """The whole pattern on the narrow-gap sweep (64 x 4 x 256 cylinder, eta
     = 0.975, 12 De in [25, 60] x tau in {0.55, 0.6}): every instance starts
     from the mixed surrogate's prediction (surrogate.predict_mixed of the
@@ -317,7 +317,8 @@ def combined_sweep(net_path, steps=300_000, sample_every=2000, precision="fp16_s
     critical_dean_fixed. With baseline, the plain FP64 sweep (instances one
     after another, laminar profile plus noise, the same steps) runs first
     and is estimated by the same rule. Wall times include the surrogate's
-    inference, not its training."""
+    inference, not its training. warm=False starts the batched run from the
+    laminar profile plus noise instead (the same run without the surrogate)."""
     import time
 
     import torch
@@ -336,19 +337,22 @@ def combined_sweep(net_path, steps=300_000, sample_every=2000, precision="fp16_s
                                   "De_c_measured_de": {str(t): v["De_c"] for t, v in summarize(res).items()}}
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    net = SG.load_mixed_net(net_path)
-    N = spec.ncells
-    rho = np.empty((24, N))
-    u = np.empty((24, 3, N))
-    for b, (tau, de) in enumerate(zip(taus, deans2)):
-        inst = Instance("cylindrical", 1.0, 1 / 0.975, 64, 4, 256, tau, de, seed + b)
-        rho[b], u[b] = SG.predict_mixed(net, inst, 4)
-        u[b] += noise_field(seed + b, N, noise_amp).T
-    net.close()
+    init = None
+    if warm:
+        net = SG.load_mixed_net(net_path)
+        N = spec.ncells
+        rho = np.empty((24, N))
+        u = np.empty((24, 3, N))
+        for b, (tau, de) in enumerate(zip(taus, deans2)):
+            inst = Instance("cylindrical", 1.0, 1 / 0.975, 64, 4, 256, tau, de, seed + b)
+            rho[b], u[b] = SG.predict_mixed(net, inst, 4)
+            u[b] += noise_field(seed + b, N, noise_amp).T
+        net.close()
+        init = (rho, u)
     t_inf = time.perf_counter() - t0
-    res = run_sweep(spec, taus, deans2, steps, sample_every, precision, seed, noise_amp, init_fields=(rho, u))
+    res = run_sweep(spec, taus, deans2, steps, sample_every, precision, seed, noise_amp, init_fields=init)
     total = time.perf_counter() - t0
-    out["combined"] = {"seconds": total, "inference_seconds": t_inf, "lb_seconds": res.seconds,
+    out["combined"] = {"seconds": total, "inference_seconds": t_inf, "lb_seconds": res.seconds, "warm": warm,
                        "De_c": {str(t): v for t, v in critical_dean_fixed(res).items()},
                        "a_final": res.amp[-1].tolist()}
     if baseline:
@@ -763,6 +767,9 @@ if __name__ == "__main__":
                     help="the combined sweep (surrogate warm start from the saved network NET, batched, "
                          "2-byte storage) against the plain FP64 sweep")
     ap.add_argument("--no-baseline", action="store_true", help="--combined: skip the FP64 sweep")
+    ap.add_argument("--precision", default="fp16_shifted", help="--combined: storage of the batched run")
+    ap.add_argument("--cold", action="store_true",
+                    help="--combined: start the batched run from the laminar profile (no surrogate)")
     ap.add_argument("--forcing-comparison", action="store_true",
                     help="De_c(eta) at eta 0.8, 0.9, 0.975 with the improved and the old forcing (Sec. III, "
                          "129 x 1 x 256, tau 0.9), by continuation")
@@ -772,7 +779,7 @@ if __name__ == "__main__":
     L.load_library()
     if a.combined:
         r = combined_sweep(a.combined, steps=a.steps, sample_every=a.sample_every,
-                           baseline=not a.no_baseline)
+                           baseline=not a.no_baseline, precision=a.precision, warm=not a.cold)
         print(json.dumps({k: ({kk: vv for kk, vv in v.items() if kk != "a_final"} if isinstance(v, dict) else v)
                           for k, v in r.items()}, indent=1))
         if a.out:
