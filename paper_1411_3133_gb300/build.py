@@ -22,7 +22,7 @@ LIB_PATH = os.path.join(LIB_DIR, "liblbgm.so")
 SOURCES = ["api.cu", "aux.cu", "step_f64.cu", "step_f32.cu", "step_h16.cu", "step_b16.cu",
            "step_tma.cu", "noalloc.cu", "batch.cu", "mlp.cu", "probe.cu", "step_shift.cu", "geometry.cpp"]
 HEADERS = ["lattice.cuh", "lbm_device.cuh", "kernels.cuh", "step_launch.cuh", "launch.h", "geometry.h",
-           "ctx.h"]
+           "ctx.h", "mbarrier.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-fmad=false", "-Xcompiler", "-fPIC,-O2", "-Xptxas", "-v"]
 

@@ -40,7 +40,7 @@ __device__ __forceinline__ void collide_store(Real (&f)[Q], S* __restrict__ fout
       return;
     }
     const Coef<float> k = coefficients<float, K>(m, g, ip.kappa, ip.G);
-    collide_dev<K>(f, k, g, ip.omega, st, stride, tc.z);
+    collide_dev<K>(f, k, g, ip.omega, TabGlobal{st, stride}, tc.z);
     store_raw<S>(fout, p, d, f);
     return;
   }
@@ -140,6 +140,95 @@ __global__ void __launch_bounds__(KBounds<S, Real, K>::maxt, KBounds<S, Real, K>
   const CellPos p = locate_cell(d, b, cell);
   const size_t base = size_t(b) * Q * uint32_t(d.ncell);
   step_node<S, Real, K, 0>(fin + base, fout + base, ref_of(d, b), geo, inst[b], d, p, flag);
+}
+
+// 2-byte storage for metrics whose geometry and stream rows are i_r alone
+// (flat, cylinder), with blocks that never straddle an i_r layer (nt n3 a
+// multiple of blockDim.x): the block's nodes share one geometry row, one
+// stream-table row and one instance, which three threads copy into shared
+// memory while the gather's loads are in flight; the collision then reads
+// them from shared memory instead of waiting on dependent global loads
+// inside the arithmetic (long-scoreboard stalls per issue 2.6 -> 1.7 on the
+// 24 x 64x4x256 cylinder sweep, 15.4 -> 16.8 GLUPS at equal occupancy). Same
+// arithmetic as collide_store: bitwise-equal states. The gather fills f (stored deviations) for node p; live is false
+// for the threads past the end of the range, which only take part in the
+// block barrier.
+template <typename S, int K, class Gather>
+__device__ __forceinline__ void step_row_shared(S* __restrict__ fout, GeoDev<float> geo,
+                                                const InstParams<float>* __restrict__ inst, const Dims& d,
+                                                const CellPos& p, bool live, int* __restrict__ flag,
+                                                Gather&& gather_into) {
+  static_assert(Codec<S, float>::uses_ref && K != KELL, "2-byte storage, rows of i_r alone");
+  __shared__ float4 s_tab[ST_K];
+  __shared__ __align__(16) unsigned char s_geo_raw[sizeof(NodeGeo<float, K>)];
+  __shared__ InstParams<float> s_ip;
+  auto& s_geo = *reinterpret_cast<NodeGeo<float, K>*>(s_geo_raw);
+  const uint32_t stride = uint32_t(d.nr) * uint32_t(d.st_rows3);
+  float4 tv;
+  if (threadIdx.x < ST_K) tv = __ldg(stream_of(d, p.b) + p.ir + threadIdx.x * stride);
+  float f[Q];
+  gather_into(f);
+  if (threadIdx.x < ST_K) s_tab[threadIdx.x] = tv;
+  if (threadIdx.x == 32) s_geo = load_geo<float, K>(geo, p.ir);
+  if (threadIdx.x == 33) s_ip = inst[p.b];
+  __syncthreads();
+  if (!live) return;
+  const Moments<float> m = moments_dev(f, s_tab[0], s_tab[1], s_tab[2]);
+  if (!finite_v(m.rho)) {
+    if (*flag == 0) atomicExch(flag, 1);
+  }
+  const NodeGeo<float, K> g = s_geo;
+  const InstParams<float> ip = s_ip;
+  const Coef<float> k = coefficients<float, K>(m, g, ip.kappa, ip.G);
+  collide_dev<K>(f, k, g, ip.omega, TabShared{s_tab}, s_tab[2].z);
+  store_raw<S>(fout, p, d, f);
+}
+
+// Interior kernel of the region split with step_row_shared: 6 resident
+// blocks per SM (80 registers, 28 bytes spilled for the cylinder; the row
+// in shared memory frees the registers the stream-table prefetch held).
+// Measured on the 24 x 64x4x256 cylinder sweep, FP16 storage, with the
+// wall-layer kernel at 5: 19.0 GLUPS; at 5 / 4 / 3 blocks 18.8 / 16.9 /
+// 14.9. LBGM_ROWSM_MINB overrides it for tuning builds.
+#ifndef LBGM_ROWSM_MINB
+#define LBGM_ROWSM_MINB 6
+#endif
+template <typename S, int K>
+__global__ void __launch_bounds__(KBounds<S, float, K>::maxt, LBGM_ROWSM_MINB)
+    k_step_bulk_rowsm(const S* __restrict__ fin, S* __restrict__ fout, GeoDev<float> geo,
+                      const InstParams<float>* __restrict__ inst, Dims d, int* __restrict__ flag) {
+  const uint32_t layer = uint32_t(d.nt) * uint32_t(d.n3);
+  const uint32_t cell0 = 3u * layer + blockIdx.x * blockDim.x;
+  const uint32_t cell = cell0 + threadIdx.x;
+  const bool live = cell < uint32_t(d.nr - 3) * layer;
+  const int b = int(blockIdx.y);
+  const CellPos p = locate_cell(d, b, live ? cell : cell0);
+  const size_t base = size_t(b) * Q * uint32_t(d.ncell);
+  step_row_shared<S, K>(fout + base, geo, inst, d, p, live, flag,
+                        [&](float (&f)[Q]) { gather<K, S, float, 0, true>(fin + base, nullptr, p, d, f); });
+}
+
+// Wall-layer kernel of the region split with step_row_shared: 5 resident
+// blocks per SM (96 registers; +0.5 % on the step against 4).
+// LBGM_EDGE_ROWSM_MINB overrides it for tuning builds.
+#ifndef LBGM_EDGE_ROWSM_MINB
+#define LBGM_EDGE_ROWSM_MINB 5
+#endif
+template <typename S, int K>
+__global__ void __launch_bounds__(KBounds<S, float, K>::maxt, LBGM_EDGE_ROWSM_MINB)
+    k_step_edge_rowsm(const S* __restrict__ fin, S* __restrict__ fout, GeoDev<float> geo,
+                      const InstParams<float>* __restrict__ inst, Dims d, int* __restrict__ flag) {
+  const uint32_t layer = uint32_t(d.nt) * uint32_t(d.n3);
+  const uint32_t e0 = blockIdx.x * blockDim.x;
+  const uint32_t e = e0 + threadIdx.x;
+  const bool live = e < 6u * layer;
+  const uint32_t ee = live ? e : e0;
+  const uint32_t cell = ee < 3u * layer ? ee : ee + uint32_t(d.nr - 6) * layer;
+  const int b = int(blockIdx.y);
+  const CellPos p = locate_cell(d, b, cell);
+  const size_t base = size_t(b) * Q * uint32_t(d.ncell);
+  step_row_shared<S, K>(fout + base, geo, inst, d, p, live, flag,
+                        [&](float (&f)[Q]) { gather_edge<K, S, float, true>(fin + base, nullptr, p, d, f); });
 }
 
 // Wall-layer kernel: 4 resident blocks per SM whatever the storage (no

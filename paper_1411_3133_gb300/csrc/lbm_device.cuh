@@ -941,22 +941,33 @@ __device__ __forceinline__ void collide(V (&f)[Q], const Coef<V>& k, const NodeG
   });
 }
 
+// A node's stream-table row: entry k of the table in global memory (st the
+// k = 0 entry, stride the table's rows), or of a block's shared-memory copy
+// of one row.
+struct TabGlobal {
+  const float4* __restrict__ st;
+  uint32_t stride;
+  __device__ __forceinline__ float4 at(int k) const { return __ldg(st + k * stride); }
+};
+struct TabShared {
+  const float4* st;
+  __device__ __forceinline__ float4 at(int k) const { return st[k]; }
+};
+
 // BGK collision with forcing on the stored deviations g of 2-byte storage,
-// in place (collide_pair with DEV): st points at the node's stream row (k =
-// 0 entry), stride the table's rows.
-template <int K>
+// in place (collide_pair with DEV), with the node's stream-table row tab.
+template <int K, class Tab>
 __device__ __forceinline__ void collide_dev(float (&g)[Q], const Coef<float>& k, const NodeGeo<float, K>& geo,
-                                            float omega, const float4* __restrict__ st, uint32_t stride,
-                                            float t0) {
+                                            float omega, const Tab& tab, float t0) {
   const float om1 = 1.0f - omega;
   g[0] = fmaf(om1, g[0], fmaf(omega, k.e0, fmaf(k.nfB, k.uy * k.fext_t, t0)));
-  // each table entry is requested one pair group ahead of its use, so its
-  // load overlaps the arithmetic of the group before
-  float4 t = __ldg(st + 3 * stride);
+  // each table entry is requested one pair group ahead of its use, so a
+  // global load overlaps the arithmetic of the group before
+  float4 t = tab.at(3);
   static_for<0, NPAIR / 2>([&](auto J_) {
     constexpr int J = decltype(J_)::value;
     float4 tn = t;
-    if constexpr (J + 1 < NPAIR / 2) tn = __ldg(st + (4 + J) * stride);
+    if constexpr (J + 1 < NPAIR / 2) tn = tab.at(4 + J);
     collide_pair<float, K, 2 * J, true>(g[4 * J + 1], g[4 * J + 2], k, geo, omega, om1, t.x, t.y);
     collide_pair<float, K, 2 * J + 1, true>(g[4 * J + 3], g[4 * J + 4], k, geo, omega, om1, t.z, t.w);
     t = tn;

@@ -23,6 +23,21 @@ cudaError_t launch_step_t(int K, const S* fin, S* fout, const GeoDev<R>& geo, co
   return cudaGetLastError();
 }
 
+// The region split of 2-byte storage for the flat and cylindrical metrics
+// (geometry and stream rows of i_r alone) with blocks that never straddle an
+// i_r layer: the kernels that keep the block's row in shared memory
+// (step_row_shared); false for the other storage types and metrics.
+template <class S, class R, int K>
+bool launch_split_rowsm(dim3 gb, dim3 ge, int threads, cudaStream_t s, cudaStream_t se, const S* fin, S* fout,
+                        const GeoDev<R>& geo, const InstParams<R>* inst, const Dims& d, int* flag) {
+  if constexpr (Codec<S, R>::uses_ref && K != KELL) {
+    k_step_bulk_rowsm<S, K><<<gb, threads, 0, s>>>(fin, fout, geo, inst, d, flag);
+    k_step_edge_rowsm<S, K><<<ge, threads, 0, se>>>(fin, fout, geo, inst, d, flag);
+    return true;
+  }
+  return false;
+}
+
 // Region-split step (periodic x3 only): the interior on stream s, then the
 // 6 wall layers on stream se (the caller orders the two streams around the
 // step). Launched second, the small wall-layer kernel takes SMs as interior
@@ -35,12 +50,15 @@ cudaError_t launch_step_split_t(int K, const S* fin, S* fout, const GeoDev<R>& g
   const uint32_t layer = uint32_t(d.nt) * uint32_t(d.n3);
   const dim3 ge((6u * layer + threads - 1) / threads, uint32_t(d.batch));
   const dim3 gb((uint32_t(d.nr - 6) * layer + threads - 1) / threads, uint32_t(d.batch));
+  const bool rowsm = layer % uint32_t(threads) == 0;
   switch (K) {
     case KFLAT:
+      if (rowsm && launch_split_rowsm<S, R, KFLAT>(gb, ge, threads, s, se, fin, fout, geo, inst, d, flag)) break;
       k_step_bulk<S, R, KFLAT><<<gb, threads, 0, s>>>(fin, fout, geo, inst, d, flag);
       k_step_edge<S, R, KFLAT><<<ge, threads, 0, se>>>(fin, fout, geo, inst, d, flag);
       break;
     case KCYL:
+      if (rowsm && launch_split_rowsm<S, R, KCYL>(gb, ge, threads, s, se, fin, fout, geo, inst, d, flag)) break;
       k_step_bulk<S, R, KCYL><<<gb, threads, 0, s>>>(fin, fout, geo, inst, d, flag);
       k_step_edge<S, R, KCYL><<<ge, threads, 0, se>>>(fin, fout, geo, inst, d, flag);
       break;

@@ -11,50 +11,18 @@
 // Rows within 3 nodes of an r-wall, and nodes near x3-walls, gather from
 // global memory with the folded bounce-back path instead.
 //
-// Every wait on an mbarrier is bounded; on expiry the kernel sets bit 1 of
-// the status flag, waits (bounded) for its copies still in flight, and
-// returns.
+// Every wait on an mbarrier is bounded (mbarrier.cuh); on expiry the kernel
+// sets bit 1 of the status flag, waits (bounded) for its copies still in
+// flight, and returns.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
 #include "kernels.cuh"
 #include "launch.h"
+#include "mbarrier.cuh"
 
 namespace lbgm {
 namespace {
-
-constexpr uint32_t kWaitPolls = 1u << 24;
-
-__device__ __forceinline__ uint32_t smem_addr(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
-               : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(smem_addr(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
-  for (uint32_t i = 0; i < kWaitPolls; ++i)
-    if (mbar_try_wait(bar, parity)) return true;
-  return false;
-}
 
 __device__ __forceinline__ void tma_load_row(float* dst, const CUtensorMap* map, uint64_t* bar, int x,
                                              int t, int r, int pl) {
@@ -79,9 +47,6 @@ __device__ __forceinline__ TileRow tile_row(int tile, const Dims& d) {
   return tr;
 }
 
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
-}
 
 // The 41 box loads of one tile into a stage, issued by the lanes of one warp
 // (population l by lane l % 32); the barrier expects all their bytes.
@@ -182,7 +147,7 @@ __global__ void __launch_bounds__(NX, 512 / NX) k_step_tma(const __grid_constant
         }
         return;
       }
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      fence_proxy_async_smem();
       issue_tile<NX>(&map, stages + s * Q * NX, &full[s], tile + 2 * G, d, vel, lane);
     }
     const Moments<float> m = moments(f);

@@ -647,7 +647,8 @@ def test_reduced_precision_state_round_trips(prec):
     (Channel("ellipsoidal", 1.0, 1.1, 10, 3, 20, b=0.9, periodic3=False, wall="equilibrium"), 0),
     (Channel("cylindrical", 1.0, 1 / ETA, 16, 4, 64), 4),                            # region split
     (Channel("cylindrical", 1.0, 1 / ETA, 16, 4, 64), 5),                            # tiled
-], ids=["flat4wall", "cyl_walled_x3", "cyl_eqwall", "ell_eqwall", "cyl_split", "cyl_tiled"])
+    (Channel("cylindrical", 1.0, 1 / ETA, 16, 4, 64), 1),                            # one kernel
+], ids=["flat4wall", "cyl_walled_x3", "cyl_eqwall", "ell_eqwall", "cyl_split", "cyl_tiled", "cyl_plain"])
 def test_deviation_collision_every_stream_row_kind(ch, kern, prec, tol):
     """The 2-byte collision runs on the stored deviations through a table per
     stream row (i_r; (i_r, i_3) for the ellipsoid; (i_r, distance class to an
