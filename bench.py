@@ -302,8 +302,13 @@ class SweepRunner:
         self.stream = self.ctx.stream
         if args.step_kernel == "auto":      # the library's automatic choice for this workload
             args.step_kernel = "plain" if args.precision == "fp64" else "split"
+        # 2-byte storage: the split kernels that keep the block's row in shared
+        # memory (blocks within one i_r layer: nt n3 a multiple of the block)
+        rowsm = "_rowsm" if (args.precision.endswith("_shifted")
+                             and (wl.ntheta * wl.n3) % args.threads == 0) else ""
         self.kernel = {"tma": "k_step_tma<KCYL,256>",
-                       "split": f"k_step_bulk<{args.precision},KCYL> + k_step_edge ({args.threads} threads)"}.get(
+                       "split": f"k_step_bulk{rowsm}<{args.precision},KCYL> + k_step_edge{rowsm} "
+                                f"({args.threads} threads)"}.get(
             args.step_kernel, f"k_step<{args.precision},KCYL> ({args.threads} threads)")
         self.profiled = args.precision == "fp32" and args.step_kernel == "split"
         self.launches_per_step = 2 if args.step_kernel == "split" else 1
