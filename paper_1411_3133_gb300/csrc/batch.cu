@@ -1,12 +1,14 @@
 // Batches of contexts of different geometry (lb_batch_* of include/lbgm.h).
 //
 // Every instance of every member becomes one ListInst record; instances are
-// grouped by metric kind and each group gets two work lists: tiles of
-// interior nodes (instance, first node, count) and tiles of wall nodes
-// (instance, first index into a list of wall-node indices, count). One batch
-// step is one k_step_list launch per non-empty list; the lists after the
-// first run on forked streams, so the wall-node kernels (bound by
-// instruction fetch) overlap the interior kernels (bound by memory).
+// grouped by metric kind and each group gets four work lists: tiles of
+// interior nodes (instance, first node, count) and, per wall-node class,
+// tiles of wall nodes (instance, first index into a list of wall-node
+// indices, count) -- nodes near an r-wall only, near an x3-wall only, and
+// the rest (corners, equilibrium walls, short axes). One batch step is one
+// k_step_list launch per non-empty list; the lists after the first run on
+// forked streams, so the wall-node kernels (bound by instruction fetch)
+// overlap the interior kernels (bound by memory).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -22,32 +24,49 @@ using namespace lbgm;
 namespace {
 
 constexpr int kMaxGroups = 3;  // flat, cylinder, ellipsoid
-constexpr int kMaxLanes = 2 * kMaxGroups;  // interior and wall-node tiles of each
+constexpr int kLists = 4;                  // interior tiles, three wall-node classes
+constexpr int kMaxLanes = kLists * kMaxGroups;
 
 struct Group {
   int K = 0;
   int ninst = 0;
-  int nwork[2] = {0, 0};        // interior tiles, wall-node tiles
-  size_t inst_off = 0;          // byte offset of the ListInst records in dmem
-  size_t work_off[2] = {0, 0};  // byte offsets of the int4 tiles in dmem
+  int nwork[kLists] = {};        // interior tiles, wall-node tiles per class
+  size_t inst_off = 0;           // byte offset of the ListInst records in dmem
+  size_t work_off[kLists] = {};  // byte offsets of the int4 tiles in dmem
   size_t cells_off = 0;         // byte offset of the wall-node indices in dmem
   int blocks_per_sm = 0;        // occupancy of the interior kernel at the built block size
 };
 
+// Wall-node class of node (i_r, i_3) near a wall (lists 1..3): 1 within 3
+// layers of an r-wall only, 2 of an x3-wall only -- each with one
+// compile-time fold per layer, which needs bounce-back walls and the walled
+// axis at least 7 nodes long -- and 3 the rest (the general wall rule).
+int wall_class(const Dims& d, int ir, int i3) {
+  const bool near_r = ir < 3 || ir > d.nr - 4;
+  const bool near_3 = !d.periodic3 && (i3 < 3 || i3 > d.n3 - 4);
+  if (d.wall_eq) return 3;
+  if (near_r && !near_3 && d.nr >= 7) return 1;
+  if (near_3 && !near_r && d.n3 >= 7) return 2;
+  return 3;
+}
+
 // Tiles of one instance (group-local index li): runs of interior nodes (no
-// wall within 3 nodes) as (li, first node, count), and the wall nodes' indices
-// appended to `cells` as (li, first index, count); counts <= tile.
-void instance_tiles(const Dims& d, int li, int tile, std::vector<int4>& interior, std::vector<int4>& wall,
-                    std::vector<int>& cells) {
+// wall within 3 nodes) as (li, first node, count), counts <= tile, into
+// lists[0]; the wall nodes' indices appended to cells[c - 1] by class c and
+// tiled as (li, first index into cells[c - 1], count), counts <= wall_tile,
+// into lists[c].
+void instance_tiles(const Dims& d, int li, int tile, int wall_tile, std::vector<int4> (&lists)[kLists],
+                    std::vector<int> (&cells)[kLists - 1]) {
   const int nr = d.nr, nt = d.nt, n3 = d.n3;
   auto inner_r = [&](int ir) { return ir >= 3 && ir <= nr - 4; };
   auto inner_3 = [&](int i3) { return d.periodic3 || (i3 >= 3 && i3 <= n3 - 4); };
   int run_start = -1;
   auto close_run = [&](int end) {
-    for (int a = run_start; a < end; a += tile) interior.push_back(make_int4(li, a, std::min(tile, end - a), 0));
+    for (int a = run_start; a < end; a += tile) lists[0].push_back(make_int4(li, a, std::min(tile, end - a), 0));
     run_start = -1;
   };
-  const size_t w0 = cells.size();
+  size_t w0[kLists - 1];
+  for (int c = 0; c < kLists - 1; ++c) w0[c] = cells[c].size();
   for (int ir = 0; ir < nr; ++ir)
     for (int it = 0; it < nt; ++it)
       for (int i3 = 0; i3 < n3; ++i3) {
@@ -56,12 +75,14 @@ void instance_tiles(const Dims& d, int li, int tile, std::vector<int4>& interior
           if (run_start < 0) run_start = cell;
         } else {
           if (run_start >= 0) close_run(cell);
-          cells.push_back(cell);
+          cells[wall_class(d, ir, i3) - 1].push_back(cell);
         }
       }
   if (run_start >= 0) close_run(nr * nt * n3);
-  for (size_t a = w0; a < cells.size(); a += size_t(tile))
-    wall.push_back(make_int4(li, int(a), int(std::min(size_t(tile), cells.size() - a)), 0));
+  for (int c = 0; c < kLists - 1; ++c)
+    for (size_t a = w0[c]; a < cells[c].size(); a += size_t(wall_tile))
+      lists[c + 1].push_back(
+          make_int4(li, int(a), int(std::min(size_t(wall_tile), cells[c].size() - a)), 0));
 }
 
 }  // namespace
@@ -183,7 +204,7 @@ lb_status build(lb_batch* b) {
   drop_graph(b);
   b->built = false;
   std::vector<unsigned char> recs;
-  std::vector<int4> tiles[kMaxGroups][2];
+  std::vector<int4> tiles[kMaxGroups][kLists];
   std::vector<int> cells[kMaxGroups];
   b->ngroups = 0;
   for (int K : {int(KCYL), int(KELL), int(KFLAT)}) {
@@ -201,13 +222,19 @@ lb_status build(lb_batch* b) {
     // tiles, instance-major; instance ids are local to the group
     const int gi = b->ngroups;
     int local = 0;
+    std::vector<int> cls[kLists - 1];
     for (const lb_ctx* c : b->m) {
       if (c->K != K) continue;
       for (int bi = 0; bi < c->batch; ++bi, ++local)
-        instance_tiles(c->dims, local, b->threads * b->tile_blocks, tiles[gi][0], tiles[gi][1], cells[gi]);
+        instance_tiles(c->dims, local, b->threads * b->tile_blocks, b->threads, tiles[gi], cls);
     }
-    gr.nwork[0] = int(tiles[gi][0].size());
-    gr.nwork[1] = int(tiles[gi][1].size());
+    // one index list per group: the classes one after the other
+    for (int c = 0; c < kLists - 1; ++c) {
+      const int shift = int(cells[gi].size());
+      for (int4& t : tiles[gi][c + 1]) t.y += shift;
+      cells[gi].insert(cells[gi].end(), cls[c].begin(), cls[c].end());
+    }
+    for (int m = 0; m < kLists; ++m) gr.nwork[m] = int(tiles[gi][m].size());
     cudaError_t e = occupancy(b->prec, K, b->threads, &gr.blocks_per_sm);
     if (e != cudaSuccess) return bcuda(b, e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
     b->g[b->ngroups++] = gr;
@@ -216,7 +243,7 @@ lb_status build(lb_batch* b) {
   auto al = [](size_t x) { return (x + 255) / 256 * 256; };
   size_t off = al(recs.size());
   for (int i = 0; i < b->ngroups; ++i) {
-    for (int m = 0; m < 2; ++m) {
+    for (int m = 0; m < kLists; ++m) {
       b->g[i].work_off[m] = off;
       off = al(off + tiles[i][m].size() * sizeof(int4));
     }
@@ -234,7 +261,7 @@ lb_status build(lb_batch* b) {
   unsigned char* base = static_cast<unsigned char*>(b->dmem);
   LB_BCUDA(b, cudaMemcpyAsync(base, recs.data(), recs.size(), cudaMemcpyHostToDevice, b->stream));
   for (int i = 0; i < b->ngroups; ++i) {
-    for (int m = 0; m < 2; ++m)
+    for (int m = 0; m < kLists; ++m)
       if (!tiles[i][m].empty())
         LB_BCUDA(b, cudaMemcpyAsync(base + b->g[i].work_off[m], tiles[i][m].data(),
                                     tiles[i][m].size() * sizeof(int4), cudaMemcpyHostToDevice, b->stream));
@@ -261,15 +288,15 @@ bool records_current(const lb_batch* b) {
   return true;
 }
 
-// One work list of one group (m = 0: interior tiles, 1: wall-node tiles) on
-// stream s.
+// One work list of one group (m = 0: interior tiles, 1..3: wall-node tiles
+// of class m) on stream s.
 cudaError_t launch_lane(const lb_batch* b, const Group& gr, int m, cudaStream_t s) {
   const unsigned char* base = static_cast<const unsigned char*>(b->dmem);
   const void* insts = base + gr.inst_off;
   const int* cells = reinterpret_cast<const int*>(base + gr.cells_off);
   const int grid = b->schedule == 1 ? std::max(1, gr.blocks_per_sm) * b->nsm : 0;
   const int4* work = reinterpret_cast<const int4*>(base + gr.work_off[m]);
-  const int sel = m | (b->built_tile_blocks > 1 ? 2 : 0);  // wall-node tiles; multi-block tiles
+  const int sel = m | (m == 0 && b->built_tile_blocks > 1 ? 4 : 0);  // list class; multi-block tiles
   switch (b->prec) {
     case LB_FP64:
       return launch_step_list_f64(gr.K, sel, insts, work, gr.nwork[m], cells, b->threads, grid, b->parity, s);
@@ -291,7 +318,7 @@ cudaError_t launch_lane(const lb_batch* b, const Group& gr, int m, cudaStream_t 
 // double-curved channels; launching the wall-node lists first was slower).
 lb_status step_once(lb_batch* b) {
   int lg[kMaxLanes], lm[kMaxLanes], n = 0;
-  for (int m = 0; m < 2; ++m) {
+  for (int m = 0; m < kLists; ++m) {
     for (int i = 0; i < b->ngroups; ++i)
       if (b->g[i].nwork[m] > 0) {
         lg[n] = i;

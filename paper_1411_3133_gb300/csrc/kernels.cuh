@@ -271,10 +271,13 @@ struct ListInst {
 // takes nodes t, t + blockDim.x, ...; a separate instantiation, because the
 // loop costs the one-block tiles ~5 % on the four-wall ellipsoid): with
 // WALLS = 0 the interior nodes first .. first + count - 1 (no wall within 3
-// nodes: the far-from-wall gather alone), with WALLS = 2 the nodes
-// cells[first .. first + count - 1] (the wall nodes: folds, or clamps for
-// equilibrium walls). Splitting the two keeps the interior kernel's code small
-// (instruction fetch is what binds a kernel carrying every wall variant).
+// nodes: the far-from-wall gather alone); otherwise the wall nodes
+// cells[first .. first + count - 1] of one class, each in its own
+// instantiation -- WALLS = 3: within 3 layers of an r-wall only (the r
+// folds), 4: of an x3-wall only (the x3 folds), 1: the rest (corners,
+// equilibrium walls, short axes: the general wall rule). Splitting them
+// keeps each kernel's code small (instruction fetch is what binds a kernel
+// carrying every wall variant).
 // Blocks take items j = blockIdx.x, blockIdx.x + gridDim.x, ... (a
 // persistent grid when gridDim.x < nwork). `parity` 0 reads f0 and writes f1,
 // 1 the reverse. The instance record is staged once per item in shared

@@ -50,8 +50,9 @@ cudaError_t launch_step_split_b16(int K, const __nv_bfloat16* fin, __nv_bfloat16
                                   cudaStream_t s, cudaStream_t se);
 
 // Work-list step over instances of different geometry (ListInst<S, R> array);
-// walls bit 0 clear: interior tiles, set: wall-node tiles over `cells`; bit
-// 1: tiles longer than one block; grid 0 launches one block per work item.
+// walls bits 0-1: 0 interior tiles, 1 r-layer wall nodes, 2 x3-layer wall
+// nodes, 3 other wall nodes (1..3 over `cells`); bit 2: interior tiles
+// longer than one block; grid 0 launches one block per work item.
 cudaError_t launch_step_list_f64(int K, int walls, const void* insts, const int4* work, int nwork,
                                  const int* cells, int threads, int grid, int parity, cudaStream_t s);
 cudaError_t step_list_occupancy_f64(int K, int threads, int* blocks_per_sm);

@@ -429,22 +429,25 @@ __device__ __forceinline__ void for_each_source(const S* __restrict__ fin, const
   }
 }
 
-// Sources for a node J = 0, 1, 2 layers from the r-wall on side SIDE (0:
-// inner, 1: outer) of a channel periodic in x3 with nr >= 7: only that wall
-// can lie on a population's one-step path, so the wall rule of src_wall
-// reduces to constants. A population whose backward path (along -c, length
-// s = |c|_inf) meets the wall 2 J + 1 half-nodes away folds once: its source
-// is x + (s - 1 - 2 J) sigma (sigma = c / s) and it arrives flipped; every
-// other population comes from x - c as away from walls.
-template <int SIDE, int J, int CX, int CY, int CZ, int S>
+// Sources for a node J = 0, 1, 2 layers from the wall on side SIDE (0: low,
+// 1: high) of axis AX (0: r, 2: x3), at least 3 layers from the walls of
+// the other axis (or with that axis periodic), the walled axis at least 7
+// nodes long: only that wall can lie on a population's one-step path, so the
+// wall rule of src_wall reduces to constants. A population whose backward
+// path (along -c, length s = |c|_inf) meets the wall 2 J + 1 half-nodes away
+// folds once: its source is x + (s - 1 - 2 J) sigma (sigma = c / s) and it
+// arrives flipped; every other population comes from x - c as away from
+// walls.
+template <int AX, int SIDE, int J, int CX, int CY, int CZ, int S>
 struct LayerFold {
   static constexpr int sx = (CX > 0) - (CX < 0), sy = (CY > 0) - (CY < 0), sz = (CZ > 0) - (CZ < 0);
-  static constexpr bool hit = ((SIDE == 0 && sx > 0) || (SIDE == 1 && sx < 0)) && (2 * S > 1 + 2 * J);
+  static constexpr int sa = AX == 0 ? sx : sz;
+  static constexpr bool hit = ((SIDE == 0 && sa > 0) || (SIDE == 1 && sa < 0)) && (2 * S > 1 + 2 * J);
   static constexpr int q = hit ? S - 1 - 2 * J : -S;
   static constexpr int dx = q * sx, dy = q * sy, dz = q * sz;  // source - node
 };
 
-template <int K, int SIDE, int J, class S, class Fn>
+template <int K, int AX, int SIDE, int J, class S, class Fn>
 __device__ __forceinline__ void for_each_source_layer(const S* __restrict__ fin, const CellPos& p,
                                                       const Dims& d, Fn&& fn) {
   const uint32_t N = uint32_t(d.ncell);
@@ -453,8 +456,8 @@ __device__ __forceinline__ void for_each_source_layer(const S* __restrict__ fin,
   static_for<0, NPAIR>([&](auto P_) {
     constexpr int P = decltype(P_)::value;
     using C = Pair<P>;
-    using Fp = LayerFold<SIDE, J, C::x, C::y, C::z, C::s>;
-    using Fm = LayerFold<SIDE, J, -C::x, -C::y, -C::z, C::s>;
+    using Fp = LayerFold<AX, SIDE, J, C::x, C::y, C::z, C::s>;
+    using Fm = LayerFold<AX, SIDE, J, -C::x, -C::y, -C::z, C::s>;
     const uint32_t sp = uint32_t((nb.rrow[3 - Fp::dx] + nb.tcol[3 - Fp::dy]) * d.n3 + nb.zcol[3 - Fp::dz]);
     const uint32_t sm = uint32_t((nb.rrow[3 - Fm::dx] + nb.tcol[3 - Fm::dy]) * d.n3 + nb.zcol[3 - Fm::dz]);
     constexpr int lp = Fp::hit ? 2 * P + 2 : 2 * P + 1, lm = Fm::hit ? 2 * P + 1 : 2 * P + 2;
@@ -493,22 +496,25 @@ struct RawInto {
   }
 };
 
-// Streamed populations of a node within 3 layers of an r-wall of a channel
-// periodic in x3 (nr >= 7), through the per-layer constant folds, into the
-// visitor put (DecodeInto or RawInto).
-template <int K, class S, class Put>
+// Streamed populations of a node within 3 layers of a wall of axis AX (0:
+// an r-wall, with x3 periodic or the node at least 3 layers from the
+// x3-walls, nr >= 7; 2: an x3-wall, the node at least 3 layers from the
+// r-walls, n3 >= 7), through the per-layer constant folds, into the visitor
+// put (DecodeInto or RawInto).
+template <int K, int AX, class S, class Put>
 __device__ __forceinline__ void gather_edge_v(const S* __restrict__ fin, const CellPos& p, const Dims& d,
                                               const Put& put) {
   put(std::integral_constant<int, 0>{}, fin + uint32_t(p.cell), 0, geo_row<K>(d, p.ir, p.i3));
-  const int side = p.ir < 3 ? 0 : 1;
-  const int j = side == 0 ? p.ir : d.nr - 1 - p.ir;
+  const int i = AX == 0 ? p.ir : p.i3, n = AX == 0 ? d.nr : d.n3;
+  const int side = i < 3 ? 0 : 1;
+  const int j = side == 0 ? i : n - 1 - i;
   switch (side * 3 + j) {
-    case 0: for_each_source_layer<K, 0, 0>(fin, p, d, put); break;
-    case 1: for_each_source_layer<K, 0, 1>(fin, p, d, put); break;
-    case 2: for_each_source_layer<K, 0, 2>(fin, p, d, put); break;
-    case 3: for_each_source_layer<K, 1, 0>(fin, p, d, put); break;
-    case 4: for_each_source_layer<K, 1, 1>(fin, p, d, put); break;
-    default: for_each_source_layer<K, 1, 2>(fin, p, d, put); break;
+    case 0: for_each_source_layer<K, AX, 0, 0>(fin, p, d, put); break;
+    case 1: for_each_source_layer<K, AX, 0, 1>(fin, p, d, put); break;
+    case 2: for_each_source_layer<K, AX, 0, 2>(fin, p, d, put); break;
+    case 3: for_each_source_layer<K, AX, 1, 0>(fin, p, d, put); break;
+    case 4: for_each_source_layer<K, AX, 1, 1>(fin, p, d, put); break;
+    default: for_each_source_layer<K, AX, 1, 2>(fin, p, d, put); break;
   }
 }
 
@@ -525,23 +531,30 @@ struct GatherPut<K, S, float, true> {
   __device__ static __forceinline__ type make(float (&f)[Q], const float*, const Dims&) { return {f}; }
 };
 
-template <int K, class S, class R, bool RAW = false>
+template <int K, class S, class R, bool RAW = false, int AX = 0>
 __device__ __forceinline__ void gather_edge(const S* __restrict__ fin, const float* ref, const CellPos& p,
                                             const Dims& d, R (&f)[Q]) {
-  gather_edge_v<K>(fin, p, d, GatherPut<K, S, R, RAW>::make(f, ref, d));
+  gather_edge_v<K, AX>(fin, p, d, GatherPut<K, S, R, RAW>::make(f, ref, d));
 }
 
 // Load the 41 streamed populations of node p from the post-collision state
-// (instance block fin, reference table ref).
-// WALLS = 2 (either path): near an r-wall with bounce-back walls, at least 3
-// nodes away from any x3 wall, only the r-wall can lie on a population's
-// path, and the compile-time folds of gather_edge replace the general wall
-// rule (the same sources, fewer instructions).
+// (instance block fin, reference table ref). WALLS selects the paths
+// compiled in: 0 far from every wall; 1 the general wall rule; 2 the node
+// decides among far, the r-layer folds and the general rule; 3 the r-layer
+// folds alone (gather_edge, AX 0); 4 the x3-layer folds alone (AX 2).
+// WALLS = 2: near an r-wall with bounce-back walls, at least 3 nodes away
+// from any x3 wall, only the r-wall can lie on a population's path, and the
+// compile-time folds of gather_edge replace the general wall rule (the same
+// sources, fewer instructions).
 // RAW (2-byte storage only): f receives the stored deviations g instead of
 // the decoded populations.
 template <int K, class S, class R, int WALLS = 2, bool RAW = false>
 __device__ __forceinline__ void gather(const S* __restrict__ fin, const float* ref, const CellPos& p,
                                        const Dims& d, R (&f)[Q]) {
+  if constexpr (WALLS == 3 || WALLS == 4) {
+    gather_edge<K, S, R, RAW, WALLS == 3 ? 0 : 2>(fin, ref, p, d, f);
+    return;
+  }
   if constexpr (WALLS == 2) {
     const bool x3_clear = d.periodic3 || (p.i3 >= 3 && p.i3 <= d.n3 - 4);
     if (!d.wall_eq && d.nr >= 7 && x3_clear && (p.ir < 3 || p.ir > d.nr - 4)) {

@@ -73,20 +73,24 @@ cudaError_t launch_step_split_t(int K, const S* fin, S* fout, const GeoDev<R>& g
 }
 
 // grid 0: one block per work item; otherwise `grid` persistent blocks.
-// walls bit 0 clear: interior tiles (cells NULL); set: wall-node tiles over
-// `cells`; bit 1: tiles of more than one block's worth of nodes.
+// walls bits 0-1: the list's class -- 0 interior tiles (cells NULL), 1
+// r-layer wall nodes (compile-time folds along r), 2 x3-layer wall nodes
+// (folds along x3), 3 every other wall node (the general wall rule), the
+// last three over `cells`; bit 2: interior tiles of more than one block's
+// worth of nodes.
 template <class S, class R>
 cudaError_t launch_step_list_t(int K, int walls, const void* insts, const int4* work, int nwork, const int* cells,
                                int threads, int grid, int parity, cudaStream_t s) {
   if (nwork == 0) return cudaSuccess;
   const auto* I = static_cast<const ListInst<S, R>*>(insts);
   const int g = grid > 0 && grid < nwork ? grid : nwork;
-  const int sel = walls & 3;
+  const int sel = (walls & 3) == 0 ? (walls & 4 ? 4 : 0) : walls & 3;
 #define LB_LIST(KK)                                                                                       \
   (sel == 0   ? (k_step_list<S, R, KK, 0, false><<<g, threads, 0, s>>>(I, work, nwork, cells, parity), 0) \
-   : sel == 1 ? (k_step_list<S, R, KK, 2, false><<<g, threads, 0, s>>>(I, work, nwork, cells, parity), 0) \
-   : sel == 2 ? (k_step_list<S, R, KK, 0, true><<<g, threads, 0, s>>>(I, work, nwork, cells, parity), 0)  \
-              : (k_step_list<S, R, KK, 2, true><<<g, threads, 0, s>>>(I, work, nwork, cells, parity), 0))
+   : sel == 4 ? (k_step_list<S, R, KK, 0, true><<<g, threads, 0, s>>>(I, work, nwork, cells, parity), 0)  \
+   : sel == 1 ? (k_step_list<S, R, KK, 3, false><<<g, threads, 0, s>>>(I, work, nwork, cells, parity), 0) \
+   : sel == 2 ? (k_step_list<S, R, KK, 4, false><<<g, threads, 0, s>>>(I, work, nwork, cells, parity), 0) \
+              : (k_step_list<S, R, KK, 1, false><<<g, threads, 0, s>>>(I, work, nwork, cells, parity), 0))
   switch (K) {
     case KFLAT: LB_LIST(KFLAT); break;
     case KCYL: LB_LIST(KCYL); break;

@@ -464,10 +464,13 @@ def test_region_split_kernel_is_bitwise_equal_to_plain_kernel(ch, batch, precisi
     (Channel("flat", 0.0, 1.0, 8, 2, 9, periodic3=False), 1),
     (Channel("cylindrical", 1.0, 1 / 0.9, 9, 3, 13), 3),
     (Channel("cylindrical", 1.0, 1 / ETA, 9, 2, 16, wall="equilibrium"), 2),
-], ids=["ell4wall", "flat4wall", "cyl_ragged", "cyl_eqwall"])
+    (Channel("cylindrical", 1.0, 1 / 0.9, 7, 2, 12, periodic3=False), 2),
+], ids=["ell4wall", "flat4wall", "cyl_ragged", "cyl_eqwall", "cyl_nr7_walled"])
 def test_tiled_step_is_bitwise_equal_to_plain_kernel(ch, batch, precision):
-    """Interior runs and wall nodes in the two work-list kernels (option 5)
-    give the one-kernel states, with graph replay and odd step counts."""
+    """Interior runs and the three classes of wall nodes -- r-layer folds,
+    x3-layer folds, the general rule (corners, equilibrium walls) -- in the
+    work-list kernels (option 5) give the one-kernel states (whose x3-wall
+    nodes take the general rule), with graph replay and odd step counts."""
     L = lib()
     params = [dict(tau=0.6 + 0.1 * b, G=2e-4, seed=70 + b, amp=1e-2) for b in range(batch)]
     outs = []
