@@ -383,7 +383,7 @@ class EllipsoidRunner(SweepRunner):
         self.kernel = {"tiled": f"k_step_list<{args.precision},KELL> interior + wall tiles ({args.threads} threads)"
                        }.get(args.step_kernel, f"k_step<{args.precision},KELL> ({args.threads} threads)")
         self.profiled = False
-        self.launches_per_step = 2 if args.step_kernel == "tiled" else 1
+        self.launches_per_step = work_lists([wl] * 24) if args.step_kernel == "tiled" else 1
 
     def config(self):
         wl = self.wl
@@ -394,11 +394,32 @@ class EllipsoidRunner(SweepRunner):
                 "l2": f"inputs larger than L2: state {2 * self.state_bytes / 1e6:.0f} MB, no flush"}
 
 
+def work_lists(channels):
+    """Work-list launches of one tiled or batch step over `channels` (objects
+    with metric, nr, n3, periodic3 and wall): per metric kind the interior
+    tiles and each non-empty wall-node class the library builds -- nodes
+    near an r-wall only, near an x3-wall only, and the rest (corners and
+    equilibrium walls)."""
+    kinds = {}
+    for ch in channels:
+        lists = kinds.setdefault(ch.metric, set())
+        walled3 = not ch.periodic3
+        if ch.nr > 6 and (not walled3 or ch.n3 > 6):
+            lists.add("interior")
+        if getattr(ch, "wall", "bounceback") == "equilibrium":
+            lists.add("rest")
+            continue
+        lists.add("r-layer")
+        if walled3:
+            lists.update(("x3-layer", "rest"))
+    return sum(len(v) for v in kinds.values())
+
+
 class MixedRunner:
     """128 channels of mixed metric and size (cylinders and double-curved
     channels, N_r in {32, 48, 64}, N_3 in 128..512, De in 20..150) in one
     lb_batch: per metric kind and step, one k_step_list launch over the
-    interior tiles and one over the wall-node tiles; autotuned."""
+    interior tiles and one per wall-node class; autotuned."""
     profiled = False
 
     def __init__(self, args, L, rank):
@@ -406,8 +427,7 @@ class MixedRunner:
         from paper_1411_3133_gb300.workloads import mixed_batch
         self.args, self.L = args, L
         self.insts = mixed_batch(seed=rank_seed(20241111, rank))
-        # every channel has interior and wall nodes: two launches per metric kind
-        self.launches_per_step = 2 * len({i.metric for i in self.insts})
+        self.launches_per_step = work_lists(self.insts)
         self.ctxs, self.batch = mixed_contexts(self.insts, args.precision)
         self.batch.lb_batch_set_option(L.LB_OPT_USE_GRAPH, 1)
         self.cells = self.batch.lb_batch_nodes()
