@@ -73,6 +73,8 @@ def diagnostics(ch: Channel, geo: dict, tau: float, rho, u) -> dict:
     u = np.asarray(u, float).reshape(shp + (3,))
 
     def cells(a):
+        if ch.theta_resolved:
+            return np.asarray(a).reshape(shp)
         return np.broadcast_to(np.asarray(a).reshape(ch.nr, 1, ch.n3), shp)
 
     sqrtg, speed = cells(geo["sqrtg"]), cells(geo["speed"])

@@ -33,6 +33,11 @@ Readings (where the paper is silent or ambiguous):
   * The metric is evaluated at theta = 0 for every theta node (quasi-2-D
     channel, periodic in theta). Gamma does not depend on theta for either
     coordinate system.
+  * theta-resolved channel (Channel.theta_resolved): the metric is evaluated
+    at each theta node, theta = dtheta_scale * (i_theta + 1/2 - N_theta/2) h,
+    centred on theta = 0 like the third axis, and the theta axis stays
+    periodic (the paper's inlet and outlet are not specified). Off theta = 0
+    and with b != 1 the metric has every off-diagonal component (Sec. IV).
   * Body force: constant covariant streamwise component F_theta = G, i.e.
     F^i = g^{i theta} G (the only reading that is a pure theta pressure
     gradient).
@@ -172,6 +177,8 @@ class Channel:
     wall          'bounceback' (walls halfway outside the end nodes) or
                   'equilibrium' (the end nodes are wall nodes held at
                   f^eq(rho', u = 0), Sec. III)
+    theta_resolved  False: the metric of theta = 0 at every theta node;
+                  True: the metric of each theta node's own theta
     """
     metric: str
     r_inner: float
@@ -184,6 +191,7 @@ class Channel:
     dtheta_scale: float = 1.0
     d3_scale: float = 1.0
     wall: str = "bounceback"
+    theta_resolved: bool = False
 
     @property
     def h(self) -> float:
@@ -215,8 +223,16 @@ class Channel:
         return math.inf
 
 
+def geometry_shape(ch: Channel):
+    """Leading axes of the geometric fields: (N_r, N_3) rows, or every node
+    (N_r, N_theta, N_3) for a theta-resolved channel."""
+    return (ch.nr, ch.ntheta, ch.n3) if ch.theta_resolved else (ch.nr, ch.n3)
+
+
 def node_coordinates(ch: Channel):
-    """Scaled coordinates (y_r, y_theta, y_3) of the (N_r, N_3) node rows."""
+    """Scaled coordinates (y_r, y_theta, y_3) of the geometry's points
+    (geometry_shape order, flattened): the (N_r, N_3) node rows at y_theta =
+    0, or every node with y_theta = (i_theta + 1/2 - N_theta/2) h."""
     h = ch.h
     ir = np.arange(ch.nr)
     i3 = np.arange(ch.n3)
@@ -226,15 +242,20 @@ def node_coordinates(ch: Channel):
     else:
         yr = ch.r_inner + (ir + 0.5) * h
         y3 = (i3 + 0.5 - ch.n3 / 2.0) * h
+    if ch.theta_resolved:
+        yt = (np.arange(ch.ntheta) + 0.5 - ch.ntheta / 2.0) * h
+        R, T, Y3 = np.meshgrid(yr, yt, y3, indexing="ij")
+        return np.stack([R, T, Y3], axis=-1).reshape(-1, 3)
     R, Y3 = np.meshgrid(yr, y3, indexing="ij")
     pts = np.stack([R, np.zeros_like(R), Y3], axis=-1).reshape(-1, 3)
     return pts
 
 
 def channel_geometry(ch: Channel) -> dict:
-    """All per-node geometric fields on the (N_r, N_3) rows (theta-frozen).
+    """All per-node geometric fields on the (N_r, N_3) rows (theta-frozen),
+    or on every node of a theta-resolved channel.
 
-    Keys (leading axes (N_r, N_3)):
+    Keys (leading axes geometry_shape(ch): (N_r, N_3) or (N_r, N_theta, N_3)):
       g, ginv, Delta (= g^ij - delta^ij), sqrtg     scaled metric
       Gamma_hat  (.., i, j, k) = h * Gamma^i_jk      lattice Christoffels
       fdir       (.., i)      = g^{i theta}          body force per unit G
@@ -248,7 +269,7 @@ def channel_geometry(ch: Channel) -> dict:
     g, _, Gam = metric_and_christoffel(ch.metric, pts, scale=scale, b=ch.b)
     gp, _, _ = metric_and_christoffel(ch.metric, pts * np.array(scale), b=ch.b)
     ginv = np.linalg.inv(g)
-    shp = (ch.nr, ch.n3)
+    shp = geometry_shape(ch)
     out = {
         "g": g.reshape(shp + (3, 3)),
         "ginv": ginv.reshape(shp + (3, 3)),

@@ -284,9 +284,12 @@ class Simulation:
         self.geo = geometry if geometry is not None else channel_geometry(ch)
         self.smap = stream_map if stream_map is not None else StreamMap(ch)
         nt = ch.ntheta
-        # per-cell fields: rows (i_r, i_3) repeated over theta
+        # per-cell fields: rows (i_r, i_3) repeated over theta, or one value
+        # per node for a theta-resolved channel
         def cells(a):
             a = np.asarray(a)
+            if ch.theta_resolved:
+                return a.reshape((ch.ncells,) + a.shape[3:])
             rows = a.reshape((ch.nr, 1, ch.n3) + a.shape[2:])
             return np.broadcast_to(rows, (ch.nr, nt, ch.n3) + a.shape[2:]).reshape(
                 (ch.ncells,) + a.shape[2:])
