@@ -58,7 +58,12 @@ typedef enum {
 typedef enum {
   LB_METRIC_FLAT = 0,         /* Cartesian channel, walls normal to x^1 */
   LB_METRIC_CYLINDRICAL = 1,  /* (r, theta, z), Sec. III */
-  LB_METRIC_ELLIPSOIDAL = 2   /* (r, theta, phi), a = c = 1, Sec. IV */
+  LB_METRIC_ELLIPSOIDAL = 2,  /* (r, theta, phi), a = c = 1, Sec. IV */
+  LB_METRIC_ELLIPSOIDAL_THETA = 3  /* the same coordinates with the metric of
+                                      each theta node (theta-resolved; see
+                                      lb_geometry_desc); FP64 and FP32
+                                      storage, the plain step kernel, no
+                                      lb_batch membership */
 } lb_metric;
 
 typedef enum {
@@ -99,7 +104,12 @@ typedef enum {
  *   x3 = (i_3 - (n3 - 1)/2) h * d3_scale, a periodic one as above.
  *   The metric is evaluated at theta = 0 for every theta node (quasi-2-D
  *   channel, periodic in theta); the Christoffel symbols of both coordinate
- *   systems do not depend on theta. */
+ *   systems do not depend on theta. LB_METRIC_ELLIPSOIDAL_THETA evaluates
+ *   the printed Sec. IV metric at each theta node instead, theta =
+ *   (i_theta + 1/2 - ntheta/2) h * dtheta_scale (centred on theta = 0), the
+ *   theta axis still periodic: off theta = 0 with b != 1 every off-diagonal
+ *   metric component is present (full Delta^ij, body force g^{i theta} G
+ *   with r and phi components). */
 typedef struct {
   double r_inner, r_outer;  /* wall positions, 0 < r_inner < r_outer
                                (any r_inner < r_outer for FLAT) */
@@ -241,7 +251,9 @@ int lb_velocity_set(int* c, double* w);
 
 /* Host-only geometry evaluation (Sec. III metric and symbols; Sec. IV metric
  * and symbols; Sec. IV.B rescaling; lattice Christoffels h * Gamma). Writes
- * nr * n3 rows (row = i_r * n3 + i_3) of LB_GEO_STRIDE doubles:
+ * nr * n3 rows (row = i_r * n3 + i_3; LB_METRIC_ELLIPSOIDAL_THETA: nr *
+ * ntheta * n3 rows, row = (i_r * ntheta + i_theta) * n3 + i_3) of
+ * LB_GEO_STRIDE doubles:
  *   [0..8]   Delta^ij = g^ij - delta^ij   (row-major 3x3, scaled metric)
  *   [9..35]  h * Gamma^i_jk               (index (i*3 + j)*3 + k)
  *   [36..38] g^{i theta}                  (body force per unit force_G)
@@ -356,7 +368,8 @@ long long lb_step_count(const lb_ctx* ctx);
  * library until the process exits. Sizes needing more return LB_ERR_ARG.
  * Every call looks the array's address up on the current device (the one
  * rho and u live on). All calls share the array, so calls that overlap on
- * the GPU race. Synchronises cuda_stream. Errors are reported through
+ * the GPU race. Synchronises cuda_stream. LB_METRIC_ELLIPSOIDAL_THETA (whose
+ * weights differ per node) returns LB_ERR_ARG. Errors are reported through
  * lb_last_error(NULL). */
 #define LB_NOALLOC_SCRATCH_BYTES (4u << 20)
 #define LB_NOALLOC_MAX_BATCH 64

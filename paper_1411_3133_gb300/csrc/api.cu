@@ -105,6 +105,10 @@ lb_status upload_params(lb_ctx* c, const lb_params* p) {
     if (p[b].old_forcing == 2 && c->prec != LB_FP64 && c->prec != LB_FP32)
       return fail(c, LB_ERR_ARG, "instance " + std::to_string(b) +
                                      ": the half-force velocity (old_forcing 2) needs FP64 or FP32 storage");
+    if (p[b].old_forcing == 2 && c->K == KELT)
+      return fail(c, LB_ERR_ARG, "instance " + std::to_string(b) +
+                                     ": the half-force velocity (old_forcing 2) is not built for the "
+                                     "theta-resolved ellipsoid");
   }
   c->any_shift = false;
   for (int b = 0; b < c->batch; ++b) c->any_shift = c->any_shift || p[b].old_forcing == 2;
@@ -137,17 +141,33 @@ void geo_arrays(Real* base, size_t nrows, GeoDev<Real>& g) {
   g.g_ttp = base + 6 * nrows;
   g.g_ptt = base + 7 * nrows;
   g.fth = base + 8 * nrows;
+  g.ext = base + 9 * nrows;  // theta-resolved ellipsoid only
+  g.ext_stride = uint32_t(nrows);
 }
+
+// Device geometry arrays of metric kind K in the compute precision: the 9
+// arrays of GeoDev over the kind's rows (i_r; (i_r, i_3); every node for the
+// theta-resolved ellipsoid, which adds the 6 arrays of GeoDev::ext).
+size_t geo_arrays_count(int K) { return K == KELT ? 15 : 9; }
 
 template <typename Real>
 std::vector<Real> geo_host_tables(const std::vector<double>& rows, const lb_geometry_desc& g, int K) {
-  const size_t rows3 = (K == KELL) ? g.n3 : 1;
+  const size_t rows3 = K == KELL ? g.n3 : K == KELT ? size_t(g.ntheta) * g.n3 : 1;
   const size_t nrows = size_t(g.nr) * rows3;
-  std::vector<Real> t(9 * nrows);
+  std::vector<Real> t(geo_arrays_count(K) * nrows);
   for (int ir = 0; ir < g.nr; ++ir)
     for (size_t i3 = 0; i3 < rows3; ++i3) {
-      const double* r = &rows[(size_t(ir) * g.n3 + i3) * LB_GEO_STRIDE];
+      // host rows: (i_r, i_3) for the frozen kinds, (i_r, i_theta, i_3) = i3 here for KELT
+      const double* r = &rows[(size_t(ir) * (K == KELT ? rows3 : g.n3) + i3) * LB_GEO_STRIDE];
       const size_t k = ir * rows3 + i3;
+      if (K == KELT) {
+        t[9 * nrows + k] = Real(r[GEO_DELTA + 0]);
+        t[10 * nrows + k] = Real(r[GEO_DELTA + 1]);
+        t[11 * nrows + k] = Real(r[GEO_DELTA + 2]);
+        t[12 * nrows + k] = Real(r[GEO_DELTA + 5]);
+        t[13 * nrows + k] = Real(r[GEO_FDIR + 0]);
+        t[14 * nrows + k] = Real(r[GEO_FDIR + 2]);
+      }
       auto gam = [&](int i, int j, int l) { return r[GEO_GAMMA + (i * 3 + j) * 3 + l]; };
       t[0 * nrows + k] = Real(r[GEO_DELTA + 4]);
       t[1 * nrows + k] = Real(r[GEO_DELTA + 8]);
@@ -165,27 +185,32 @@ std::vector<Real> geo_host_tables(const std::vector<double>& rows, const lb_geom
 // The kernels read only the components listed in GeoDev; check that every
 // other component of the evaluated geometry is zero for this metric kind.
 std::string check_sparsity(const std::vector<double>& rows, const lb_geometry_desc& g, int K) {
-  const size_t n = size_t(g.nr) * g.n3;
+  const size_t n = rows.size() / LB_GEO_STRIDE;
   for (size_t k = 0; k < n; ++k) {
     const double* r = &rows[k * LB_GEO_STRIDE];
     for (int i = 0; i < 9; ++i) {
-      const bool used = (i == 4 && K != KFLAT) || (i == 8 && K == KELL);
+      const bool used = (i == 4 && K != KFLAT) || (i == 8 && (K == KELL || K == KELT)) || K == KELT;
       if (!used && r[GEO_DELTA + i] != 0.0) return "unexpected Delta component";
+    }
+    if (K == KELT) {  // a symmetric Delta, as the kernels read it
+      if (r[GEO_DELTA + 3] != r[GEO_DELTA + 1] || r[GEO_DELTA + 6] != r[GEO_DELTA + 2] ||
+          r[GEO_DELTA + 7] != r[GEO_DELTA + 5])
+        return "Delta not symmetric";
     }
     for (int idx = 0; idx < 27; ++idx) {
       const int i = idx / 9, j = (idx / 3) % 3, l = idx % 3;
       bool used = false;
-      if (K == KCYL || K == KELL)
+      if (K == KCYL || K == KELL || K == KELT)
         used = (i == 0 && j == 1 && l == 1) || (i == 1 && ((j == 0 && l == 1) || (j == 1 && l == 0)));
-      if (K == KELL)
+      if (K == KELL || K == KELT)
         used = used || (i == 0 && j == 2 && l == 2) || (i == 2 && ((j == 0 && l == 2) || (j == 2 && l == 0))) ||
                (i == 1 && ((j == 1 && l == 2) || (j == 2 && l == 1))) || (i == 2 && j == 1 && l == 1);
       if (!used && r[GEO_GAMMA + idx] != 0.0) return "unexpected Christoffel component";
     }
-    if (r[GEO_FDIR] != 0.0 || r[GEO_FDIR + 2] != 0.0) return "unexpected force direction";
+    if (K != KELT && (r[GEO_FDIR] != 0.0 || r[GEO_FDIR + 2] != 0.0)) return "unexpected force direction";
   }
   // the cylinder and flat kernels read rows by i_r only
-  if (K != KELL)
+  if (K == KFLAT || K == KCYL)
     for (int ir = 0; ir < g.nr; ++ir)
       for (int i3 = 1; i3 < g.n3; ++i3)
         for (int f = 0; f < 39; ++f)
@@ -244,6 +269,7 @@ cudaError_t launch_split(lb_ctx* c, int src, int dst) {
 // arithmetic is FP32 (measured fastest there), the one-kernel step otherwise.
 int resolved_kernel(const lb_ctx* c) {
   if (c->any_shift) return 1;  // the half-force variant runs in the plain kernel only
+  if (c->K == KELT) return 1;   // the theta-resolved ellipsoid too
   if (c->step_kernel != 0) return c->step_kernel;
   if (c->prec == LB_FP64) return 1;
   return (c->geom.periodic3 && c->geom.wall == LB_WALL_BOUNCEBACK) ? 4 : 5;
@@ -340,7 +366,7 @@ lb_status lb_geometry_eval(lb_metric metric, const lb_geometry_desc* geom, doubl
   if (!geom || !out) return fail(nullptr, LB_ERR_ARG, "null argument");
   const std::string v = validate_geometry(metric, *geom);
   if (!v.empty()) return fail(nullptr, LB_ERR_ARG, v);
-  const size_t need = size_t(geom->nr) * geom->n3 * LB_GEO_STRIDE;
+  const size_t need = geometry_rows(metric, *geom) * LB_GEO_STRIDE;
   if (out_len < need) return fail(nullptr, LB_ERR_ARG, "output too small: need " + std::to_string(need));
   const std::vector<double> rows = evaluate_geometry(metric, *geom);
   std::memcpy(out, rows.data(), need * sizeof(double));
@@ -380,6 +406,8 @@ lb_status lb_create_geometry(lb_metric metric, const lb_geometry_desc* geom, int
   if (batch < 1) return fail(nullptr, LB_ERR_ARG, "need batch >= 1");
   if (prec != LB_FP64 && prec != LB_FP32 && prec != LB_FP16_SHIFTED && prec != LB_BF16_SHIFTED)
     return fail(nullptr, LB_ERR_ARG, "unknown precision");
+  if (metric == LB_METRIC_ELLIPSOIDAL_THETA && prec != LB_FP64 && prec != LB_FP32)
+    return fail(nullptr, LB_ERR_ARG, "the theta-resolved ellipsoid needs FP64 or FP32 storage");
   if (alloc && (!alloc->alloc || !alloc->free)) return fail(nullptr, LB_ERR_ARG, "allocator needs alloc and free");
   const double total = double(batch) * geom->nr * geom->ntheta * geom->n3;
   if (total >= 4294967295.0) return fail(nullptr, LB_ERR_ARG, "batch * nodes must fit in uint32");
@@ -395,7 +423,10 @@ lb_status lb_create_geometry(lb_metric metric, const lb_geometry_desc* geom, int
   c->geom = *geom;
   c->batch = batch;
   c->prec = prec;
-  c->K = metric == LB_METRIC_FLAT ? KFLAT : metric == LB_METRIC_CYLINDRICAL ? KCYL : KELL;
+  c->K = metric == LB_METRIC_FLAT ? KFLAT
+         : metric == LB_METRIC_CYLINDRICAL ? KCYL
+         : metric == LB_METRIC_ELLIPSOIDAL ? KELL
+                                           : KELT;
   if (alloc) {
     c->alloc = *alloc;
     c->has_alloc = true;
@@ -435,7 +466,8 @@ lb_status lb_create_geometry(lb_metric metric, const lb_geometry_desc* geom, int
   d.periodic3 = geom->periodic3 ? 1 : 0;
   d.wall_eq = geom->wall == LB_WALL_EQUILIBRIUM ? 1 : 0;
   d.batch = batch;
-  d.geo_rows3 = c->K == KELL ? geom->n3 : 1;
+  d.geo_rows3 = c->K == KELL ? geom->n3 : c->K == KELT ? geom->ntheta * geom->n3 : 1;
+  d.geo_theta = c->K == KELT ? 1 : 0;
   d.div_ncell = FastDiv::make(uint32_t(d.ncell));
   d.div_n3 = FastDiv::make(uint32_t(d.n3));
   d.div_nt = FastDiv::make(uint32_t(d.nt));
@@ -444,11 +476,11 @@ lb_status lb_create_geometry(lb_metric metric, const lb_geometry_desc* geom, int
   c->elem_bytes = prec == LB_FP64 ? 8 : prec == LB_FP32 ? 4 : 2;
 
   const size_t nrows = size_t(geom->nr) * d.geo_rows3;
-  const size_t nrow64 = size_t(geom->nr) * geom->n3;
+  const size_t nrow64 = geometry_rows(metric, *geom);
   c->nblk = int(std::min<size_t>(1024, (c->ncell + 255) / 256));
   c->f[0] = dalloc(c, c->state_elems * c->elem_bytes);
   c->f[1] = dalloc(c, c->state_elems * c->elem_bytes);
-  c->geo_real = dalloc(c, 9 * nrows * (prec == LB_FP64 ? sizeof(double) : sizeof(float)));
+  c->geo_real = dalloc(c, geo_arrays_count(c->K) * nrows * (prec == LB_FP64 ? sizeof(double) : sizeof(float)));
   c->geo64 = static_cast<double*>(dalloc(c, nrow64 * 4 * sizeof(double)));
   c->sqrtg = static_cast<double*>(dalloc(c, nrow64 * sizeof(double)));
   c->base_uth = static_cast<double*>(dalloc(c, size_t(batch) * geom->nr * sizeof(double)));
@@ -502,7 +534,7 @@ lb_status lb_create_geometry(lb_metric metric, const lb_geometry_desc* geom, int
   if (e == cudaSuccess) e = cudaMemsetAsync(c->flag, 0, sizeof(int), c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return bail(LB_ERR_CUDA, std::string("geometry upload: ") + cudaGetErrorString(e));
-  if (prec == LB_FP32 && geom->wall == LB_WALL_BOUNCEBACK && tma_step_supported(d) &&
+  if (prec == LB_FP32 && c->K != KELT && geom->wall == LB_WALL_BOUNCEBACK && tma_step_supported(d) &&
       tensor_map_bytes() <= sizeof(c->tmap[0]))
     c->tma_ok = make_state_tensor_map(c->tmap[0], static_cast<const float*>(c->f[0]), d) == cudaSuccess &&
                 make_state_tensor_map(c->tmap[1], static_cast<const float*>(c->f[1]), d) == cudaSuccess;
@@ -809,6 +841,8 @@ lb_status lb_set_option(lb_ctx* c, int option, long long value) {
     case LB_OPT_STEP_KERNEL:
       if (value < 0 || value > 5 || value == 3)
         return fail(c, LB_ERR_ARG, "need 0 (auto), 1 (plain), 2 (TMA), 4 (region split) or 5 (tiled)");
+      if (c->K == KELT && value > 1)
+        return fail(c, LB_ERR_ARG, "the theta-resolved ellipsoid runs the plain step kernel only");
       if (value == 4 && (!c->geom.periodic3 || c->geom.wall != LB_WALL_BOUNCEBACK))
         return fail(c, LB_ERR_ARG, "the region-split step kernel needs a periodic x3 axis and bounce-back walls");
       if (value == 2 && !c->tma_ok)
@@ -839,7 +873,7 @@ lb_status lb_autotune(lb_ctx* c, int steps_per_trial, lb_tune* best, lb_tune* tr
     for (int t : {64, 128, 192, 256}) cand.push_back({t, 1, 0, 0.0});
   else
     for (int t : {64, 96, 128}) cand.push_back({t, 1, 0, 0.0});
-  if (!c->any_shift) {  // the half-force variant has the plain kernel only
+  if (!c->any_shift && c->K != KELT) {  // the half-force variant and KELT have the plain kernel only
     if (c->geom.periodic3 && c->geom.wall == LB_WALL_BOUNCEBACK)
       for (int t : {64, 96, 128}) cand.push_back({t, 4, 0, 0.0});
     for (int t : {64, 96, 128}) cand.push_back({t, 5, 0, 0.0});

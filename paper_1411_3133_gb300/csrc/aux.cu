@@ -20,6 +20,12 @@ cudaError_t macros_t(int K, const S* fin, double* rho, double* u, const Dims& d,
     case KFLAT: k_macros<S, Real, KFLAT><<<nb, 256, 0, s>>>(fin, rho, u, d); break;
     case KCYL: k_macros<S, Real, KCYL><<<nb, 256, 0, s>>>(fin, rho, u, d); break;
     case KELL: k_macros<S, Real, KELL><<<nb, 256, 0, s>>>(fin, rho, u, d); break;
+    case KELT:
+      if constexpr (!Codec<S, Real>::uses_ref) {  // FP64 / FP32 storage only
+        k_macros<S, Real, KELT><<<nb, 256, 0, s>>>(fin, rho, u, d);
+        break;
+      }
+      return cudaErrorInvalidValue;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -34,6 +40,12 @@ cudaError_t init_t(int K, S* f, const GeoDev<Real>& geo, const double* sqrtg, co
     case KFLAT: k_init<S, Real, KFLAT><<<nb, 256, 0, s>>>(f, geo, sqrtg, base, ini, rho_in, u_in, d); break;
     case KCYL: k_init<S, Real, KCYL><<<nb, 256, 0, s>>>(f, geo, sqrtg, base, ini, rho_in, u_in, d); break;
     case KELL: k_init<S, Real, KELL><<<nb, 256, 0, s>>>(f, geo, sqrtg, base, ini, rho_in, u_in, d); break;
+    case KELT:
+      if constexpr (!Codec<S, Real>::uses_ref) {  // FP64 / FP32 storage only
+        k_init<S, Real, KELT><<<nb, 256, 0, s>>>(f, geo, sqrtg, base, ini, rho_in, u_in, d);
+        break;
+      }
+      return cudaErrorInvalidValue;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -165,7 +177,7 @@ __global__ void __launch_bounds__(DIAG_THREADS)
     const int rem = c - ir * plane;
     const int it = rem / d.n3;
     const int i3 = rem - it * d.n3;
-    const double* gr = geo64 + size_t(ir * d.n3 + i3) * 4;
+    const double* gr = geo64 + size_t(d.geo_theta ? c : ir * d.n3 + i3) * 4;
     const double sg = gr[0], sp = gr[1], wA = gr[2], wOm = gr[3];
     const double r = rb[c];
     const bool eqw = d.wall_eq != 0;

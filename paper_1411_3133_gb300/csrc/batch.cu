@@ -369,6 +369,9 @@ lb_status ready(lb_batch* b) {
     lb_status s;
     if (!ctx_usable(b->m[i], &s))
       return bfail(b, LB_ERR_STATE, "member " + std::to_string(i) + ": " + b->m[i]->err);
+    if (b->m[i]->K == KELT)
+      return bfail(b, LB_ERR_ARG, "member " + std::to_string(i) +
+                                      " is a theta-resolved ellipsoid, which only the plain step kernel carries");
     if (b->m[i]->any_shift)
       return bfail(b, LB_ERR_ARG, "member " + std::to_string(i) +
                                       " uses the half-force velocity (old_forcing 2), which only the plain "

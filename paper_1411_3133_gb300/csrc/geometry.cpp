@@ -25,9 +25,10 @@ namespace lbgm {
 
 std::string validate_geometry(lb_metric metric, const lb_geometry_desc& g) {
   char buf[256];
-  if (metric != LB_METRIC_FLAT && metric != LB_METRIC_CYLINDRICAL &&
-      metric != LB_METRIC_ELLIPSOIDAL)
+  if (metric != LB_METRIC_FLAT && metric != LB_METRIC_CYLINDRICAL && metric != LB_METRIC_ELLIPSOIDAL &&
+      metric != LB_METRIC_ELLIPSOIDAL_THETA)
     return "unknown metric";
+  const bool ell = metric == LB_METRIC_ELLIPSOIDAL || metric == LB_METRIC_ELLIPSOIDAL_THETA;
   if (!(g.r_outer > g.r_inner)) return "need r_outer > r_inner";
   if (metric != LB_METRIC_FLAT && !(g.r_inner > 0.0)) return "need r_inner > 0";
   if (g.wall != LB_WALL_BOUNCEBACK && g.wall != LB_WALL_EQUILIBRIUM) return "unknown wall condition";
@@ -41,7 +42,7 @@ std::string validate_geometry(lb_metric metric, const lb_geometry_desc& g) {
   if (!g.periodic3 && g.n3 < (eq ? 3 : 7))
     return eq ? "need n3 >= 3 when the third axis has walls" : "need n3 >= 7 when the third axis has walls";
   if (!(g.dtheta_scale > 0.0) || !(g.d3_scale > 0.0)) return "need positive dtheta_scale, d3_scale";
-  if (metric == LB_METRIC_ELLIPSOIDAL) {
+  if (ell) {
     if (!(g.b > 0.0)) return "need b > 0";
     const double h = lattice_h(g);
     const double phmax = (eq && !g.periodic3 ? 0.5 * (g.n3 - 1) : 0.5 * g.n3) * h * g.d3_scale;
@@ -58,11 +59,79 @@ std::string validate_geometry(lb_metric metric, const lb_geometry_desc& g) {
 
 double curvature_radius(lb_metric metric, const lb_geometry_desc& g) {
   if (metric == LB_METRIC_CYLINDRICAL) return g.r_inner;
-  if (metric == LB_METRIC_ELLIPSOIDAL) return g.r_inner * g.b * g.b;
+  if (metric == LB_METRIC_ELLIPSOIDAL || metric == LB_METRIC_ELLIPSOIDAL_THETA) return g.r_inner * g.b * g.b;
   return 0.0;
 }
 
+namespace {
+
+// One row of the theta-resolved ellipsoid at physical (r, theta, phi): the
+// six printed Sec. IV metric components, scaled by the lattice map and
+// inverted; the frozen channel's Christoffel symbols (they depend on neither
+// b nor theta); the observables' weights of the node.
+void theta_row(const lb_geometry_desc& gd, double r, double th, double ph, double* row) {
+  const double h = lattice_h(gd);
+  const double s[3] = {1.0, gd.dtheta_scale, gd.d3_scale};
+  const double b2 = gd.b * gd.b;
+  const double ct = std::cos(th), st = std::sin(th), cp = std::cos(ph), sp = std::sin(ph);
+  const double q = ct * ct + b2 * st * st;  // cos^2 th + b^2 sin^2 th
+  double g[3][3];
+  g[0][0] = sp * sp + cp * cp * q;
+  g[1][1] = r * r * cp * cp * (st * st + b2 * ct * ct);
+  g[2][2] = r * r * (cp * cp + sp * sp * q);
+  g[0][1] = g[1][0] = r * (b2 - 1.0) * cp * cp * ct * st;
+  g[0][2] = g[2][0] = r * (1.0 - b2) * st * st * cp * sp;
+  g[1][2] = g[2][1] = r * r * (1.0 - b2) * cp * sp * ct * st;
+  double gs[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) gs[i][j] = g[i][j] * s[i] * s[j];
+  // inverse by cofactors
+  const double c00 = gs[1][1] * gs[2][2] - gs[1][2] * gs[2][1];
+  const double c01 = gs[1][2] * gs[2][0] - gs[1][0] * gs[2][2];
+  const double c02 = gs[1][0] * gs[2][1] - gs[1][1] * gs[2][0];
+  const double det = gs[0][0] * c00 + gs[0][1] * c01 + gs[0][2] * c02;
+  double inv[3][3];
+  inv[0][0] = c00 / det;
+  inv[1][0] = c01 / det;
+  inv[2][0] = c02 / det;
+  inv[0][1] = (gs[0][2] * gs[2][1] - gs[0][1] * gs[2][2]) / det;
+  inv[1][1] = (gs[0][0] * gs[2][2] - gs[0][2] * gs[2][0]) / det;
+  inv[2][1] = (gs[0][1] * gs[2][0] - gs[0][0] * gs[2][1]) / det;
+  inv[0][2] = (gs[0][1] * gs[1][2] - gs[0][2] * gs[1][1]) / det;
+  inv[1][2] = (gs[0][2] * gs[1][0] - gs[0][0] * gs[1][2]) / det;
+  inv[2][2] = (gs[0][0] * gs[1][1] - gs[0][1] * gs[1][0]) / det;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) row[GEO_DELTA + i * 3 + j] = inv[i][j] - (i == j ? 1.0 : 0.0);
+  double G[3][3][3] = {};
+  G[0][1][1] = -r * cp * cp;
+  G[0][2][2] = -r;
+  G[1][0][1] = G[1][1][0] = 1.0 / r;
+  G[2][0][2] = G[2][2][0] = 1.0 / r;
+  G[1][1][2] = G[1][2][1] = -sp / cp;
+  G[2][1][1] = sp * cp;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j)
+      for (int k = 0; k < 3; ++k) row[GEO_GAMMA + (i * 3 + j) * 3 + k] = h * G[i][j][k] * s[j] * s[k] / s[i];
+  for (int i = 0; i < 3; ++i) row[GEO_FDIR + i] = inv[i][1];
+  row[GEO_SQRTG] = std::sqrt(det);
+  row[GEO_SPEED] = std::sqrt(gs[1][1]);
+  row[GEO_WA] = std::sqrt(g[0][0] * g[2][2] - g[0][2] * g[0][2]);
+  row[GEO_WOMEGA] = std::sqrt(g[1][1]);
+  row[GEO_RPHYS] = r;
+}
+
+}  // namespace
+
 std::vector<double> evaluate_geometry(lb_metric metric, const lb_geometry_desc& gd) {
+  if (metric == LB_METRIC_ELLIPSOIDAL_THETA) {
+    std::vector<double> out(geometry_rows(metric, gd) * LB_GEO_STRIDE, 0.0);
+    for (int ir = 0; ir < gd.nr; ++ir)
+      for (int it = 0; it < gd.ntheta; ++it)
+        for (int i3 = 0; i3 < gd.n3; ++i3)
+          theta_row(gd, node_r(gd, ir), node_theta(gd, it), node_x3(gd, i3),
+                    &out[((size_t(ir) * gd.ntheta + it) * gd.n3 + i3) * LB_GEO_STRIDE]);
+    return out;
+  }
   const int nr = gd.nr, n3 = gd.n3;
   const double h = lattice_h(gd);
   const double s[3] = {1.0, gd.dtheta_scale, gd.d3_scale};

@@ -25,7 +25,8 @@ enum GeoField {
 // Validate a descriptor; returns an empty string when valid.
 std::string validate_geometry(lb_metric metric, const lb_geometry_desc& g);
 
-// nr * n3 rows of LB_GEO_STRIDE doubles (row = i_r * n3 + i_3).
+// geometry_rows rows of LB_GEO_STRIDE doubles (row = i_r * n3 + i_3, or
+// (i_r * ntheta + i_theta) * n3 + i_3 for LB_METRIC_ELLIPSOIDAL_THETA).
 std::vector<double> evaluate_geometry(lb_metric metric, const lb_geometry_desc& g);
 
 // Functions compiled for the host and, inside CUDA translation units, for the
@@ -50,6 +51,17 @@ inline LBGM_HD double node_r(const lb_geometry_desc& g, int ir) {
 inline LBGM_HD double node_x3(const lb_geometry_desc& g, int i3) {
   const bool on_walls = g.wall == LB_WALL_EQUILIBRIUM && !g.periodic3;
   return (on_walls ? i3 - 0.5 * (g.n3 - 1) : i3 + 0.5 - 0.5 * g.n3) * lattice_h(g) * g.d3_scale;
+}
+
+// theta of node i_theta of a theta-resolved channel, centred on theta = 0.
+inline LBGM_HD double node_theta(const lb_geometry_desc& g, int it) {
+  return (it + 0.5 - 0.5 * g.ntheta) * lattice_h(g) * g.dtheta_scale;
+}
+
+// Geometry rows of a descriptor: nr * n3, or nr * ntheta * n3 when the metric
+// is evaluated at each theta node.
+inline size_t geometry_rows(lb_metric metric, const lb_geometry_desc& g) {
+  return size_t(g.nr) * g.n3 * (metric == LB_METRIC_ELLIPSOIDAL_THETA ? size_t(g.ntheta) : 1);
 }
 
 // Physical metric of a node at theta = 0 (diagonal there: g_rr, g_thth,

@@ -32,7 +32,7 @@ __device__ __forceinline__ void collide_store(Real (&f)[Q], S* __restrict__ fout
     if (!finite_v(m.rho)) {
       if (*flag == 0) atomicExch(flag, 1);
     }
-    const int row = K == KELL ? p.ir * d.geo_rows3 + p.i3 : p.ir;
+    const int row = geo_row_node<K>(d, p.ir, p.it, p.i3);
     const NodeGeo<float, K> g = load_geo<float, K>(geo, row);
     if (d.wall_eq && (p.ir == 0 || p.ir == d.nr - 1 || (!d.periodic3 && (p.i3 == 0 || p.i3 == d.n3 - 1)))) {
       equilibrium<float, K>(m.rho, 0.0f, 0.0f, 0.0f, g, f);
@@ -48,7 +48,7 @@ __device__ __forceinline__ void collide_store(Real (&f)[Q], S* __restrict__ fout
   if (!finite_v(m.rho)) {  // NaN or Inf
     if (*flag == 0) atomicExch(flag, 1);
   }
-  const int row = K == KELL ? p.ir * d.geo_rows3 + p.i3 : p.ir;
+  const int row = geo_row_node<K>(d, p.ir, p.it, p.i3);
   const NodeGeo<Real, K> g = load_geo<Real, K>(geo, row);
   if (d.wall_eq && (p.ir == 0 || p.ir == d.nr - 1 || (!d.periodic3 && (p.i3 == 0 || p.i3 == d.n3 - 1)))) {
     equilibrium<Real, K>(m.rho, Real(0.0), Real(0.0), Real(0.0), g, f);
@@ -105,7 +105,7 @@ struct StepBounds<double, double> {
 template <class S, class Real, int K>
 struct KBounds {
   static constexpr int maxt = StepBounds<S, Real>::maxt;
-  static constexpr int minb = K == KELL && sizeof(S) != 2 && StepBounds<S, Real>::minb > 1
+  static constexpr int minb = (K == KELL || K == KELT) && sizeof(S) != 2 && StepBounds<S, Real>::minb > 1
                                   ? StepBounds<S, Real>::minb - 1
                                   : StepBounds<S, Real>::minb;
 };
@@ -370,7 +370,7 @@ __global__ void __launch_bounds__(256) k_init(S* __restrict__ f, GeoDev<Real> ge
     u[1] = u_in[ub + d.ncell];
     u[2] = u_in[ub + 2 * size_t(d.ncell)];
   } else {
-    rho = 1.0 / sqrtg[p.ir * d.n3 + p.i3];
+    rho = 1.0 / sqrtg[d.geo_theta ? p.cell : p.ir * d.n3 + p.i3];
     u[0] = 0.0;
     u[1] = base_uth ? base_uth[size_t(p.b) * d.nr + p.ir] : 0.0;
     u[2] = 0.0;
@@ -382,7 +382,7 @@ __global__ void __launch_bounds__(256) k_init(S* __restrict__ f, GeoDev<Real> ge
       u[i] += in.amp * (2.0 * U - 1.0);
     }
   }
-  const int row = K == KELL ? p.ir * d.geo_rows3 + p.i3 : p.ir;
+  const int row = geo_row_node<K>(d, p.ir, p.it, p.i3);
   const NodeGeo<Real, K> g = load_geo<Real, K>(geo, row);
   Real fe[Q];
   equilibrium<Real, K>(Real(rho), Real(u[0]), Real(u[1]), Real(u[2]), g, fe);

@@ -17,7 +17,10 @@
 
 namespace lbgm {
 
-enum MetricKind { KFLAT = 0, KCYL = 1, KELL = 2 };
+// KELT: the theta-resolved double-curved channel -- the ellipsoidal metric
+// of each theta node (full Delta^ij, body force with r and phi components),
+// the frozen channel's Christoffel symbols, one geometry row per node.
+enum MetricKind { KFLAT = 0, KCYL = 1, KELL = 2, KELT = 3 };
 
 // ---------------------------------------------------------------------------
 // launch geometry
@@ -46,7 +49,8 @@ struct Dims {
   int ncell;       // nr * nt * n3 (one instance)
   int periodic3;   // 0: walls on x3
   int batch;
-  int geo_rows3;   // n3 for the ellipsoid's (r, x3) rows, 1 otherwise
+  int geo_rows3;   // geometry rows per i_r: n3 for the ellipsoid's (r, x3)
+                   // rows, nt n3 for the theta-resolved one, 1 otherwise
   FastDiv div_ncell, div_n3, div_nt;
   // 2-byte storage: reference populations over the nr * geo_rows3 geometry
   // rows, per instance (ref_index; NULL for FP32 / FP64 storage)
@@ -56,6 +60,7 @@ struct Dims {
   // for FP32 / FP64 storage) over nr * st_rows3 stream rows
   const float4* st;
   int st_rows3;    // n3 (ellipsoid), 1 (periodic x3), 7 (walls on x3)
+  int geo_theta;   // 1: geometry rows (and observable weights) per node
 };
 
 // Index of reference population l of geometry row r in an instance's table:
@@ -74,6 +79,15 @@ __device__ __forceinline__ uint32_t ref_index(const Dims& d, int l, int row) {
 template <int K>
 __device__ __forceinline__ int geo_row(const Dims& d, int ir, int i3) {
   if constexpr (K == KELL) return ir * d.geo_rows3 + i3;
+  else return ir;
+}
+
+// Geometry row of node p for metric kind K: i_r (flat, cylinder), (i_r, i_3)
+// (ellipsoid), the node itself (theta-resolved ellipsoid).
+template <int K>
+__device__ __forceinline__ int geo_row_node(const Dims& d, int ir, int it, int i3) {
+  if constexpr (K == KELL) return ir * d.geo_rows3 + i3;
+  else if constexpr (K == KELT) return ir * d.geo_rows3 + it * d.n3 + i3;
   else return ir;
 }
 
@@ -128,6 +142,10 @@ struct GeoDev {
   const Real* g_ttp;  // h Gamma^theta_{theta 3}
   const Real* g_ptt;  // h Gamma^3_{theta theta}
   const Real* fth;    // g^{theta theta}
+  // theta-resolved ellipsoid only: Delta^rr, Delta^{r theta}, Delta^{r 3},
+  // Delta^{theta 3}, g^{r theta}, g^{3 theta} at ext + j * ext_stride
+  const Real* ext;
+  uint32_t ext_stride;
 };
 
 template <typename Real>
@@ -739,21 +757,38 @@ struct NodeGeo {
   V fth = V(1.0);
 };
 
+// The theta-resolved ellipsoid adds the off-diagonal and r r components of
+// Delta and the r and x3 components of the body force direction.
+template <typename V>
+struct NodeGeo<V, KELT> : NodeGeo<V, KELL> {
+  V drr = V(0.0), drt = V(0.0), drp = V(0.0), dtp = V(0.0);
+  V fr = V(0.0), fp = V(0.0);
+};
+
 template <typename Real, int K>
 __device__ __forceinline__ NodeGeo<Real, K> load_geo(const GeoDev<Real>& g, int row) {
   NodeGeo<Real, K> n;
   n.fth = __ldg(g.fth + row);
-  if constexpr (K == KCYL || K == KELL) {
+  if constexpr (K == KCYL || K == KELL || K == KELT) {
     n.dtt = __ldg(g.dtt + row);
     n.n_rtt = -__ldg(g.g_rtt + row);
     n.n_trt = -__ldg(g.g_trt + row);
   }
-  if constexpr (K == KELL) {
+  if constexpr (K == KELL || K == KELT) {
     n.dpp = __ldg(g.dpp + row);
     n.n_rpp = -__ldg(g.g_rpp + row);
     n.n_prp = -__ldg(g.g_prp + row);
     n.n_ttp = -__ldg(g.g_ttp + row);
     n.n_ptt = -__ldg(g.g_ptt + row);
+  }
+  if constexpr (K == KELT) {
+    const Real* e = g.ext + row;
+    n.drr = __ldg(e);
+    n.drt = __ldg(e + g.ext_stride);
+    n.drp = __ldg(e + 2 * g.ext_stride);
+    n.dtp = __ldg(e + 3 * g.ext_stride);
+    n.fr = __ldg(e + 4 * g.ext_stride);
+    n.fp = __ldg(e + 5 * g.ext_stride);
   }
   return n;
 }
@@ -799,6 +834,10 @@ struct Coef {
   V fA, nfB, t0;
   V naxx, nayy, nazz, naxy, naxz, nayz;
   V fext_t;
+  // theta-resolved ellipsoid: eA and eB times Delta^rr, Delta^{r theta},
+  // Delta^{r 3}, Delta^{theta 3}; the body force's r and x3 components
+  V eArr, eArt, eArp, eAtp, eBrr, eBrt, eBrp, eBtp;
+  V fext_r, fext_p;
 };
 
 template <typename V, int K>
@@ -815,7 +854,8 @@ __device__ __forceinline__ Coef<V> coefficients(const Moments<V>& m, const NodeG
   c.uy = uy;
   c.uz = uz;
   const V uu = fmav(uz, uz, fmav(uy, uy, ux * ux));
-  const V trD = g.dtt + g.dpp;
+  V trD = g.dtt + g.dpp;
+  if constexpr (K == KELT) trD = trD + g.drr;
   const V tra2 = rho * fmav(cs2, trD, uu);
   c.e0 = fmav(V(-0.5 / CS2), tra2, rho);
   const V eA = rho * V(0.5 / CS2);
@@ -829,21 +869,48 @@ __device__ __forceinline__ Coef<V> coefficients(const Moments<V>& m, const NodeG
   // -V / (2 cs^4), Delta diagonal (dtt on theta, dpp on x3)
   const V nvs = V(-0.5 / (CS2 * CS2)) * rho;
   const V trDc = cs2 * trD;
-  c.nvx = nvs * (fmav(trDc, ux, uu * ux));
-  c.nvy = nvs * (fmav(fmav(V(2.0 * CS2), g.dtt, trDc), uy, uu * uy));
-  c.nvz = nvs * (fmav(fmav(V(2.0 * CS2), g.dpp, trDc), uz, uu * uz));
+  if constexpr (K == KELT) {
+    // full Delta: V^k / rho = cs^2 (tr Delta u^k + 2 (Delta u)^k) + |u|^2 u^k
+    const V c2 = V(2.0 * CS2);
+    const V dux = fmav(g.drr, ux, fmav(g.drt, uy, g.drp * uz));
+    const V duy = fmav(g.drt, ux, fmav(g.dtt, uy, g.dtp * uz));
+    const V duz = fmav(g.drp, ux, fmav(g.dtp, uy, g.dpp * uz));
+    c.nvx = nvs * fmav(c2, dux, fmav(trDc, ux, uu * ux));
+    c.nvy = nvs * fmav(c2, duy, fmav(trDc, uy, uu * uy));
+    c.nvz = nvs * fmav(c2, duz, fmav(trDc, uz, uu * uz));
+    c.eArr = eA * g.drr;
+    c.eArt = eA * g.drt;
+    c.eArp = eA * g.drp;
+    c.eAtp = eA * g.dtp;
+    c.eBrr = c.eB * g.drr;
+    c.eBrt = c.eB * g.drt;
+    c.eBrp = c.eB * g.drp;
+    c.eBtp = c.eB * g.dtp;
+  } else {
+    c.nvx = nvs * (fmav(trDc, ux, uu * ux));
+    c.nvy = nvs * (fmav(fmav(V(2.0 * CS2), g.dtt, trDc), uy, uu * uy));
+    c.nvz = nvs * (fmav(fmav(V(2.0 * CS2), g.dpp, trDc), uz, uu * uz));
+  }
   c.fA = rho * inv_cs4;
   c.nfB = rho * V(-1.0 / CS2);
   // A2 = (1 - kappa) rho (cs^2 Delta + u u) + kappa (S - rho cs^2 delta)
   const V k1 = V(1.0) - kappa;
   const V rc = rho * cs2;
   const V rk = rho * k1;
-  const V axx = fmav(rk, ux * ux, kappa * (m.sxx - rc));
+  V axx, axy, axz, ayz;
+  if constexpr (K == KELT) {
+    axx = fmav(rk, fmav(cs2, g.drr, ux * ux), kappa * (m.sxx - rc));
+    axy = fmav(rk, fmav(cs2, g.drt, ux * uy), kappa * m.sxy);
+    axz = fmav(rk, fmav(cs2, g.drp, ux * uz), kappa * m.sxz);
+    ayz = fmav(rk, fmav(cs2, g.dtp, uy * uz), kappa * m.syz);
+  } else {
+    axx = fmav(rk, ux * ux, kappa * (m.sxx - rc));
+    axy = fmav(rk, ux * uy, kappa * m.sxy);
+    axz = fmav(rk, ux * uz, kappa * m.sxz);
+    ayz = fmav(rk, uy * uz, kappa * m.syz);
+  }
   const V ayy = fmav(rk, fmav(cs2, g.dtt, uy * uy), kappa * (m.syy - rc));
   const V azz = fmav(rk, fmav(cs2, g.dpp, uz * uz), kappa * (m.szz - rc));
-  const V axy = fmav(rk, ux * uy, kappa * m.sxy);
-  const V axz = fmav(rk, ux * uz, kappa * m.sxz);
-  const V ayz = fmav(rk, uy * uz, kappa * m.syz);
   const V trA2 = axx + ayy + azz;
   c.t0 = fmav(V(-0.5 / (CS2 * CS2)), trA2, rho * inv_cs2);
   const V nic4 = V(-1.0 / (CS2 * CS2));
@@ -854,7 +921,46 @@ __device__ __forceinline__ Coef<V> coefficients(const Moments<V>& m, const NodeG
   c.naxz = axz * nic4;
   c.nayz = ayz * nic4;
   c.fext_t = G * g.fth;
+  if constexpr (K == KELT) {
+    c.fext_r = G * g.fr;
+    c.fext_p = G * g.fp;
+  }
   return c;
+}
+
+// E += eA c.Delta.c and X += eB c.Delta.c for velocity (cx, cy, cz): the
+// diagonal theta and x3 terms of every curved metric, and the theta-resolved
+// ellipsoid's r r and off-diagonal terms.
+template <int K, int cx, int cy, int cz, class V>
+__device__ __forceinline__ void add_cdc(V& E, V& X, const Coef<V>& k) {
+  constexpr bool curv = K != KFLAT;
+  constexpr bool ell = K == KELL || K == KELT;
+  if constexpr (curv && cy != 0) {
+    E = mac<cy * cy>(E, k.eAt);
+    X = mac<cy * cy>(X, k.eBt);
+  }
+  if constexpr (ell && cz != 0) {
+    E = mac<cz * cz>(E, k.eAp);
+    X = mac<cz * cz>(X, k.eBp);
+  }
+  if constexpr (K == KELT) {
+    if constexpr (cx != 0) {
+      E = mac<cx * cx>(E, k.eArr);
+      X = mac<cx * cx>(X, k.eBrr);
+    }
+    if constexpr (cx * cy != 0) {
+      E = mac<2 * cx * cy>(E, k.eArt);
+      X = mac<2 * cx * cy>(X, k.eBrt);
+    }
+    if constexpr (cx * cz != 0) {
+      E = mac<2 * cx * cz>(E, k.eArp);
+      X = mac<2 * cx * cz>(X, k.eBrp);
+    }
+    if constexpr (cy * cz != 0) {
+      E = mac<2 * cy * cz>(E, k.eAtp);
+      X = mac<2 * cy * cz>(X, k.eBtp);
+    }
+  }
 }
 
 // BGK collision with the forcing term for the pair (c, -c), in place:
@@ -874,32 +980,36 @@ __device__ __forceinline__ void collide_pair(V& fp, V& fm, const Coef<V>& k, con
   using C = Pair<P>;
   constexpr int cx = C::x, cy = C::y, cz = C::z;
   constexpr bool curv = K != KFLAT;
-  constexpr bool ell = K == KELL;
+  constexpr bool ell = K == KELL || K == KELT;
+  constexpr bool gen = K == KELT;
   const V uc = dot3<cx, cy, cz>(k.ux, k.uy, k.uz);
   const V uc2 = uc * uc;
   V E = fmav(k.eB, uc2, k.e0);
   V X = fmav(k.oC, uc2, k.oA);
-  if constexpr (curv && cy != 0) {
-    E = mac<cy * cy>(E, k.eAt);
-    X = mac<cy * cy>(X, k.eBt);
-  }
-  if constexpr (ell && cz != 0) {
-    E = mac<cz * cz>(E, k.eAp);
-    X = mac<cz * cz>(X, k.eBp);
-  }
+  add_cdc<K, cx, cy, cz>(E, X, k);
   const V O = fmav(uc, X, dot3<cx, cy, cz>(k.nvx, k.nvy, k.nvz));
   // F = F_ext - Gamma(c, c), even in c; which components exist is known here
-  constexpr bool hasFr = curv && (cy != 0 || (ell && cz != 0));
-  constexpr bool hasFz = ell && (cx * cz != 0 || cy != 0);
+  // (the theta-resolved ellipsoid's body force has all three)
+  constexpr bool hasFr = gen || (curv && (cy != 0 || (ell && cz != 0)));
+  constexpr bool hasFz = gen || (ell && (cx * cz != 0 || cy != 0));
   V Fr = V(0.0), Fz = V(0.0);
-  if constexpr (curv && cy != 0) Fr = mulc<cy * cy>(g.n_rtt);
-  if constexpr (ell && cz != 0) Fr = (cy != 0) ? mac<cz * cz>(Fr, g.n_rpp) : mulc<cz * cz>(g.n_rpp);
+  if constexpr (gen) {
+    Fr = k.fext_r;
+    if constexpr (cy != 0) Fr = mac<cy * cy>(Fr, g.n_rtt);
+    if constexpr (cz != 0) Fr = mac<cz * cz>(Fr, g.n_rpp);
+    Fz = k.fext_p;
+    if constexpr (cy != 0) Fz = mac<cy * cy>(Fz, g.n_ptt);
+    if constexpr (cx * cz != 0) Fz = mac<2 * cx * cz>(Fz, g.n_prp);
+  } else {
+    if constexpr (curv && cy != 0) Fr = mulc<cy * cy>(g.n_rtt);
+    if constexpr (ell && cz != 0) Fr = (cy != 0) ? mac<cz * cz>(Fr, g.n_rpp) : mulc<cz * cz>(g.n_rpp);
+    if constexpr (ell && cx * cz != 0 && cy != 0) Fz = mac<2 * cx * cz>(mulc<cy * cy>(g.n_ptt), g.n_prp);
+    else if constexpr (ell && cx * cz != 0) Fz = mulc<2 * cx * cz>(g.n_prp);
+    else if constexpr (ell && cy != 0) Fz = mulc<cy * cy>(g.n_ptt);
+  }
   V Ft = k.fext_t;
   if constexpr (curv && cx * cy != 0) Ft = mac<2 * cx * cy>(Ft, g.n_trt);
   if constexpr (ell && cy * cz != 0) Ft = mac<2 * cy * cz>(Ft, g.n_ttp);
-  if constexpr (ell && cx * cz != 0 && cy != 0) Fz = mac<2 * cx * cz>(mulc<cy * cy>(g.n_ptt), g.n_prp);
-  else if constexpr (ell && cx * cz != 0) Fz = mulc<2 * cx * cz>(g.n_prp);
-  else if constexpr (ell && cy != 0) Fz = mulc<cy * cy>(g.n_ptt);
   // F.c and u.F
   constexpr bool hasFc = cy != 0 || (cx != 0 && hasFr) || (cz != 0 && hasFz);
   V Fc = V(0.0);
@@ -947,7 +1057,9 @@ template <typename V, int K>
 __device__ __forceinline__ void collide(V (&f)[Q], const Coef<V>& k, const NodeGeo<V, K>& g, const V& omega) {
   const V om1 = V(1.0) - omega;
   // rest velocity: f^eq = w0 e0, forcing = -w0 fB (u . F_ext)
-  f[0] = fmav(om1, f[0], fmav(omega, k.e0, k.nfB * (k.uy * k.fext_t)) * V(W_REST));
+  V uF0 = k.uy * k.fext_t;
+  if constexpr (K == KELT) uF0 = fmav(k.ux, k.fext_r, fmav(k.uz, k.fext_p, uF0));
+  f[0] = fmav(om1, f[0], fmav(omega, k.e0, k.nfB * uF0) * V(W_REST));
   static_for<0, NPAIR>([&](auto P_) {
     constexpr int P = decltype(P_)::value;
     collide_pair<V, K, P>(f[2 * P + 1], f[2 * P + 2], k, g, omega, om1);
@@ -1017,6 +1129,24 @@ __device__ __forceinline__ void equilibrium(const V& rho, const V& ux, const V& 
     if constexpr (cz != 0) {
       E = mac<cz * cz>(E, k.eAp);
       X = mac<cz * cz>(X, k.eBp);
+    }
+    if constexpr (K == KELT) {
+      if constexpr (cx != 0) {
+        E = mac<cx * cx>(E, k.eArr);
+        X = mac<cx * cx>(X, k.eBrr);
+      }
+      if constexpr (cx * cy != 0) {
+        E = mac<2 * cx * cy>(E, k.eArt);
+        X = mac<2 * cx * cy>(X, k.eBrt);
+      }
+      if constexpr (cx * cz != 0) {
+        E = mac<2 * cx * cz>(E, k.eArp);
+        X = mac<2 * cx * cz>(X, k.eBrp);
+      }
+      if constexpr (cy * cz != 0) {
+        E = mac<2 * cy * cz>(E, k.eAtp);
+        X = mac<2 * cy * cz>(X, k.eBtp);
+      }
     }
     const V O = fmav(uc, X, dot3<cx, cy, cz>(k.nvx, k.nvy, k.nvz));
     f[2 * P + 1] = (E + O) * V(C::w);

@@ -62,6 +62,8 @@ extern "C" lb_status lb_diagnostics_noalloc(lb_metric metric, const lb_geometry_
   if (!geom || !tau || !rho || !u || !out) return noalloc_fail(LB_ERR_ARG, "null argument");
   const std::string v = validate_geometry(metric, *geom);
   if (!v.empty()) return noalloc_fail(LB_ERR_ARG, v);
+  if (metric == LB_METRIC_ELLIPSOIDAL_THETA)
+    return noalloc_fail(LB_ERR_ARG, "the theta-resolved ellipsoid has per-node weights: use lb_diagnostics");
   if (batch < 1 || batch > LB_NOALLOC_MAX_BATCH)
     return noalloc_fail(LB_ERR_ARG, "need 1 <= batch <= " + std::to_string(LB_NOALLOC_MAX_BATCH));
   for (int b = 0; b < batch; ++b)

@@ -18,6 +18,12 @@ cudaError_t launch_step_t(int K, const S* fin, S* fout, const GeoDev<R>& geo, co
     case KFLAT: k_step<S, R, KFLAT><<<blocks, threads, 0, s>>>(fin, fout, geo, inst, d, flag); break;
     case KCYL: k_step<S, R, KCYL><<<blocks, threads, 0, s>>>(fin, fout, geo, inst, d, flag); break;
     case KELL: k_step<S, R, KELL><<<blocks, threads, 0, s>>>(fin, fout, geo, inst, d, flag); break;
+    case KELT:  // the theta-resolved ellipsoid: FP64 / FP32 storage, this kernel only
+      if constexpr (!Codec<S, R>::uses_ref) {
+        k_step<S, R, KELT><<<blocks, threads, 0, s>>>(fin, fout, geo, inst, d, flag);
+        break;
+      }
+      return cudaErrorInvalidValue;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

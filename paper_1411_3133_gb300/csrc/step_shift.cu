@@ -99,7 +99,7 @@ __global__ void __launch_bounds__(KBounds<S, Real, K>::maxt, KBounds<S, Real, K>
   if (!finite_v(m.rho)) {
     if (*flag == 0) atomicExch(flag, 1);
   }
-  const int row = K == KELL ? p.ir * d.geo_rows3 + p.i3 : p.ir;
+  const int row = geo_row_node<K>(d, p.ir, p.it, p.i3);
   const NodeGeo<Real, K> g = load_geo<Real, K>(geo, row);
   if (d.wall_eq && (p.ir == 0 || p.ir == d.nr - 1 || (!d.periodic3 && (p.i3 == 0 || p.i3 == d.n3 - 1)))) {
     equilibrium<Real, K>(m.rho, Real(0.0), Real(0.0), Real(0.0), g, f);

@@ -154,7 +154,7 @@ __global__ void __launch_bounds__(NX, 512 / NX) k_step_tma(const __grid_constant
     if (!finite_v(m.rho)) {
       if (*flag == 0) atomicOr(flag, 1);
     }
-    const int row = K == KELL ? p.ir * d.geo_rows3 + p.i3 : p.ir;
+    const int row = geo_row_node<K>(d, p.ir, p.it, p.i3);
     const NodeGeo<float, K> g = load_geo<float, K>(geo, row);
     const InstParams<float> ip = inst[p.b];
     const Coef<float> kc = coefficients<float, K>(m, g, ip.kappa, ip.G);

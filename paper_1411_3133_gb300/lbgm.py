@@ -23,7 +23,7 @@ LB_GEO_STRIDE = 44
 LB_OK, LB_ERR_ARG, LB_ERR_CUDA, LB_ERR_NONFINITE, LB_ERR_TIMEOUT, LB_ERR_STATE = range(6)
 STATUS_NAMES = {0: "LB_OK", 1: "LB_ERR_ARG", 2: "LB_ERR_CUDA", 3: "LB_ERR_NONFINITE",
                 4: "LB_ERR_TIMEOUT", 5: "LB_ERR_STATE"}
-METRICS = {"flat": 0, "cylindrical": 1, "ellipsoidal": 2}
+METRICS = {"flat": 0, "cylindrical": 1, "ellipsoidal": 2, "ellipsoidal_theta": 3}
 PRECISIONS = {"fp64": 0, "fp32": 1, "fp16_shifted": 2, "bf16_shifted": 3}
 LB_OPT_CHECK_EVERY, LB_OPT_BLOCK_THREADS, LB_OPT_USE_GRAPH, LB_OPT_STEP_KERNEL = 0, 1, 2, 3
 LB_OPT_SCHEDULE, LB_OPT_TILE_BLOCKS, LB_OPT_STORAGE_REFERENCE = 4, 5, 6
@@ -205,11 +205,13 @@ def make_desc(r_inner, r_outer, nr, ntheta, n3, b=1.0, periodic3=True, dtheta_sc
 
 
 def lb_geometry_eval(metric: str, desc: lb_geometry_desc) -> np.ndarray:
-    """Host-only geometry rows, shape (nr, n3, LB_GEO_STRIDE)."""
-    out = np.zeros(desc.nr * desc.n3 * LB_GEO_STRIDE)
+    """Host-only geometry rows, shape (nr, n3, LB_GEO_STRIDE), or (nr, ntheta,
+    n3, LB_GEO_STRIDE) for the theta-resolved ellipsoid."""
+    shape = (desc.nr, desc.ntheta, desc.n3) if metric == "ellipsoidal_theta" else (desc.nr, desc.n3)
+    out = np.zeros(int(np.prod(shape)) * LB_GEO_STRIDE)
     _check(load_library().lb_geometry_eval(METRICS[metric], ctypes.byref(desc),
                                            out.ctypes.data_as(_D), out.size))
-    return out.reshape(desc.nr, desc.n3, LB_GEO_STRIDE)
+    return out.reshape(shape + (LB_GEO_STRIDE,))
 
 
 def lb_force_for_dean(metric: str, desc: lb_geometry_desc, tau: float, De: float) -> float:

@@ -22,7 +22,8 @@ def perm_lib_to_oracle():
 
 
 def spec_of(ch: Channel):
-    return lib().ChannelSpec(ch.metric, ch.r_inner, ch.r_outer, ch.nr, ch.ntheta, ch.n3, ch.b,
+    metric = "ellipsoidal_theta" if ch.theta_resolved else ch.metric
+    return lib().ChannelSpec(metric, ch.r_inner, ch.r_outer, ch.nr, ch.ntheta, ch.n3, ch.b,
                              ch.periodic3, ch.dtheta_scale, ch.d3_scale, ch.wall)
 
 

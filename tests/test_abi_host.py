@@ -61,18 +61,24 @@ CHANNELS = [
     Channel("cylindrical", 1.0, 1 / 0.975, 17, 4, 32, wall="equilibrium"),
     Channel("ellipsoidal", 1.0, 1.1, 9, 4, 13, b=0.9, periodic3=False, wall="equilibrium"),
     Channel("ellipsoidal", 1.0, 1.1, 9, 4, 13, b=0.9, wall="equilibrium"),
+    Channel("ellipsoidal", 1.0, 1.2, 8, 5, 10, b=0.9, periodic3=False, dtheta_scale=8.0, d3_scale=2.0,
+            theta_resolved=True),
+    Channel("ellipsoidal", 0.25, 0.275, 9, 6, 12, b=1.7, dtheta_scale=3.0, wall="equilibrium",
+            theta_resolved=True),
 ]
 
 
-@pytest.mark.parametrize("ch", CHANNELS, ids=lambda c: f"{c.metric}{c.shape}{c.wall[:2]}{int(c.periodic3)}")
+@pytest.mark.parametrize("ch", CHANNELS,
+                         ids=lambda c: f"{c.metric}{'T' if c.theta_resolved else ''}{c.shape}{c.wall[:2]}"
+                                       f"{int(c.periodic3)}")
 def test_geometry_matches_oracle(L, ch):
     desc = L.make_desc(ch.r_inner, ch.r_outer, ch.nr, ch.ntheta, ch.n3, ch.b, ch.periodic3,
                        ch.dtheta_scale, ch.d3_scale, ch.wall)
-    rows = L.lb_geometry_eval(ch.metric, desc)
+    rows = L.lb_geometry_eval("ellipsoidal_theta" if ch.theta_resolved else ch.metric, desc)
     geo = channel_geometry(ch)
     assert np.allclose(rows[..., 0:9].reshape(geo["Delta"].shape), geo["Delta"], rtol=0, atol=1e-13)
     assert np.allclose(rows[..., 9:36].reshape(geo["Gamma_hat"].shape), geo["Gamma_hat"],
-                       rtol=0, atol=1e-15)
+                       rtol=0, atol=1e-15 * max(1.0, np.abs(geo["Gamma_hat"]).max()))
     assert np.allclose(rows[..., 36:39], geo["fdir"], rtol=1e-13, atol=0)
     for k, name in [(39, "sqrtg"), (40, "speed"), (41, "wA"), (42, "wOmega"), (43, "r_phys")]:
         assert np.allclose(rows[..., k], geo[name], rtol=1e-13, atol=0), name

@@ -12,7 +12,7 @@ import numpy as np
 import pytest
 
 from analytic import curved_poiseuille
-from gpu_helpers import Twin, lib, max_rel
+from gpu_helpers import Twin, lib, max_rel, spec_of
 from oracle.diagnostics import diagnostics
 from oracle.geometry import Channel
 from paper_1411_3133_gb300.workloads import noise_field
@@ -101,6 +101,15 @@ CASES = {
                          [dict(tau=0.8, G=2e-4, seed=21, amp=1e-2, shift=True)]),
     "flat_shift": (Channel("flat", 0.0, 1.0, 8, 2, 9, periodic3=False),
                    [dict(tau=0.6, G=1e-3, seed=9, amp=1e-2, shift=True)]),
+    # theta-resolved double-curved channel: the metric of each theta node (full Delta, body force
+    # with r and phi components), walls on r and phi / equilibrium walls with a periodic phi
+    "ellT_4wall": (Channel("ellipsoidal", 1.0, 1.1, 10, 8, 14, b=0.6, periodic3=False,
+                           dtheta_scale=1 / 0.6, theta_resolved=True),
+                   [dict(tau=0.7, G=3e-4, seed=31, amp=1e-2)]),
+    "ellT_eqwall_periodic": (Channel("ellipsoidal", 1.0, 1.1, 9, 8, 16, b=1.5, dtheta_scale=1 / 1.5,
+                                     wall="equilibrium", theta_resolved=True),
+                             [dict(tau=0.8, G=2e-4, seed=32, amp=1e-2),
+                              dict(tau=0.65, G=1e-4, seed=33, amp=1e-2, old=True)]),
     "batch3": (Channel("cylindrical", 1.0, 1 / ETA, 8, 4, 33),
                [dict(tau=0.8, G=1e-4, seed=1, amp=1e-3), dict(tau=0.6, G=3e-4, seed=2, amp=2e-3),
                 dict(tau=1.1, G=0.0, seed=3, amp=5e-3, old=True)]),
@@ -164,7 +173,10 @@ def _smooth_flow(ch, amp=0.05):
 @pytest.mark.parametrize("ch", [CYL1, Channel("ellipsoidal", 1.0, 1.1, 10, 4, 40, b=0.9,
                                               periodic3=False),
                                 Channel("ellipsoidal", 1.0, 1.1, 10, 4, 40, b=0.9, periodic3=False,
-                                        wall="equilibrium")], ids=["cyl", "ell", "ell_eqwall"])
+                                        wall="equilibrium"),
+                                Channel("ellipsoidal", 1.0, 1.1, 10, 8, 40, b=0.6, periodic3=False,
+                                        dtheta_scale=1 / 0.6, theta_resolved=True)],
+                         ids=["cyl", "ell", "ell_eqwall", "ell_theta"])
 def test_fp32_step_parity(ch):
     """FP32 against the FP64 oracle, 1e-5 of u_max for a flow of realistic
     magnitude (u_max ~ 0.05), after 1, 10 and 100 steps."""
@@ -258,6 +270,49 @@ def test_diagnostics_match_oracle(wall):
                   "vortex_amp", "vortex_amp_x3", "max_speed"):
             assert dl[b][k] == pytest.approx(do[k], rel=1e-11, abs=1e-18), k
         assert dl[b]["nonfinite"] == 0 and dl[b]["step"] == 20
+    tw.close()
+
+
+@pytest.mark.parametrize("wall", ["bounceback", "equilibrium"])
+def test_diagnostics_match_oracle_theta_resolved(wall):
+    """Observables of the theta-resolved channel: per-node weights (sqrt g,
+    sqrt g_thth, the area element of the (r, phi) block) from each node's own
+    metric."""
+    ch = Channel("ellipsoidal", 1.0, 1.1, 10, 6, 16, b=0.6, periodic3=False, dtheta_scale=1 / 0.6,
+                 wall=wall, theta_resolved=True)
+    params = [dict(tau=0.7, G=3e-4, seed=4, amp=1e-2)]
+    tw = Twin(ch, params, "fp64")
+    tw.ctx.lb_init(tw.lparams)
+    tw.sims[0].init_rest(noise_field(4, tw.N, 1e-2))
+    tw.step(20)
+    dl = tw.ctx.lb_diagnostics()
+    rho, u = tw.sims[0].macros()
+    do = diagnostics(ch, tw.geo, 0.7, rho, u)
+    for k in ("mass_rho_prime", "mass_physical", "mean_v_theta", "dean", "mean_vorticity",
+              "vortex_amp", "vortex_amp_x3", "max_speed"):
+        assert dl[0][k] == pytest.approx(do[k], rel=1e-11, abs=1e-18), k
+    tw.close()
+
+
+def test_theta_resolved_restrictions():
+    """The theta-resolved ellipsoid runs FP64 / FP32 storage in the plain
+    step kernel: 2-byte storage, the other step kernels, batches, the
+    half-force variant and the no-alloc observables are refused."""
+    L = lib()
+    ch = Channel("ellipsoidal", 1.0, 1.1, 8, 4, 12, b=0.8, periodic3=False, theta_resolved=True)
+    for prec in ("fp16_shifted", "bf16_shifted"):
+        with pytest.raises(L.LBError) as e:
+            L.LBContext(spec_of(ch), batch=1, precision=prec)
+        assert e.value.status == L.LB_ERR_ARG
+    tw = Twin(ch, [dict(tau=0.8)], "fp32")
+    tw.ctx.lb_set_option(L.LB_OPT_STEP_KERNEL, 1)
+    for bad in (2, 4, 5):
+        with pytest.raises(L.LBError) as e:
+            tw.ctx.lb_set_option(L.LB_OPT_STEP_KERNEL, bad)
+        assert e.value.status == L.LB_ERR_ARG
+    with pytest.raises(L.LBError) as e:
+        tw.ctx.lb_init([L.make_params(0.8, 1e-5, 2, 1, 0.0, False)])
+    assert e.value.status == L.LB_ERR_ARG
     tw.close()
 
 
