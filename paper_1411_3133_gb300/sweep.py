@@ -619,16 +619,19 @@ def compare_precisions_continuation(modes=("fp64", "fp32", "fp16_shifted", "bf16
 
 def double_curved_study(cases, deans=None, steps=300_000, sample_every=2000, tau=1.0, eta=0.9,
                         nr=65, ntheta=4, n3=128, noise_amp=1e-4, seed=20241111, precision="fp32",
-                        wall="equilibrium", max_speed=0.4):
+                        wall="equilibrium", max_speed=0.4, theta_resolved=False):
     """The double-curved channel of Sec. IV: walls at r_i and r_o = r_i / eta
     (the paper's Dirichlet walls by default), periodic in phi over n3 nodes,
     tau = 1, for each case (label, r_i, b): streamwise curvature radius
     R_theta = r_i b^2, cross-sectional radius R_phi = r_i. One context per
     case holds the Dean numbers (force from the cylinder of radius R_theta
     and the same width and N_r, which drops targets whose laminar mean speed
-    would exceed max_speed lattice units); one lb_batch steps all cases.
-    Per case: measured De, final mean vorticity <omega^theta> and vortex
-    amplitude, and De_c read off the vorticity curve (critical_dean_knee)."""
+    would exceed max_speed lattice units); one lb_batch steps all cases --
+    or, theta_resolved, the metric of each theta node (ntheta of them, one h
+    apart, centred on theta = 0) with each context stepped in the plain
+    kernel. Per case: measured De, final mean vorticity <omega^theta> and
+    vortex amplitude, and De_c read off the vorticity curve
+    (critical_dean_knee)."""
     import time
 
     import torch
@@ -640,7 +643,8 @@ def double_curved_study(cases, deans=None, steps=300_000, sample_every=2000, tau
     ctxs, kept = [], []
     for k, (label, ri, b) in enumerate(cases):
         ro = ri / eta
-        spec = L.ChannelSpec("ellipsoidal", ri, ro, nr, ntheta, n3, b=b, periodic3=True, wall=wall)
+        spec = L.ChannelSpec("ellipsoidal_theta" if theta_resolved else "ellipsoidal", ri, ro, nr, ntheta, n3,
+                             b=b, periodic3=True, wall=wall)
         R = ri * b * b
         d = ro - ri
         des_k = [de for de in deans if de * nu / ((nr - 1) * np.sqrt(d / R)) <= max_speed]
@@ -651,14 +655,22 @@ def double_curved_study(cases, deans=None, steps=300_000, sample_every=2000, tau
         ctx.lb_init(params)
         ctxs.append(ctx)
         kept.append(des_k)
-    batch = L.LBBatch(ctxs)
-    batch.lb_batch_set_option(L.LB_OPT_USE_GRAPH, 1)
+    batch = None if theta_resolved else L.LBBatch(ctxs)
+    if batch is not None:
+        batch.lb_batch_set_option(L.LB_OPT_USE_GRAPH, 1)
+    else:
+        for ctx in ctxs:
+            ctx.lb_set_option(L.LB_OPT_USE_GRAPH, 1)
     amps = [[] for _ in cases]
     vort = [[] for _ in cases]
     des = [[] for _ in cases]
     t0 = time.perf_counter()
     for _ in range(steps // sample_every):
-        batch.lb_batch_step(sample_every)
+        if batch is not None:
+            batch.lb_batch_step(sample_every)
+        else:
+            for ctx in ctxs:
+                ctx.lb_step(sample_every)
         for k, ctx in enumerate(ctxs):
             dg = ctx.lb_diagnostics()
             amps[k].append([x["vortex_amp_x3"] for x in dg])
@@ -673,7 +685,9 @@ def double_curved_study(cases, deans=None, steps=300_000, sample_every=2000, tau
         _, u = ctx.lb_macros()
         cells.append([vortex_cells(u[i, 0], nr, ntheta, n3, periodic=True) for i in range(u.shape[0])])
         ur_mid.append([u[i, 0].reshape(nr, ntheta, n3)[nr // 2].mean(axis=0).tolist() for i in range(u.shape[0])])
-    out = {"seconds": sec, "steps": steps, "nodes": batch.lb_batch_nodes(), "cases": []}
+    nodes = sum(c.batch * c.spec.ncells for c in ctxs) if batch is None else batch.lb_batch_nodes()
+    out = {"seconds": sec, "steps": steps, "nodes": nodes, "ntheta": ntheta,
+           "theta_resolved": theta_resolved, "cases": []}
     for k, (label, ri, b) in enumerate(cases):
         A = np.array(amps[k])
         W = np.array(vort[k])
@@ -691,7 +705,8 @@ def double_curved_study(cases, deans=None, steps=300_000, sample_every=2000, tau
                              "De_4cell": first_dean_with_cells(de, cells[k], 4),
                              "De_6cell": first_dean_with_cells(de, cells[k], 6),
                              "De_c": critical_dean_knee(de, w_fin)})
-    batch.close()
+    if batch is not None:
+        batch.close()
     for c in ctxs:
         c.close()
     return out
@@ -755,6 +770,12 @@ if __name__ == "__main__":
     ap.add_argument("--out", default=None)
     ap.add_argument("--double-curved", action="store_true",
                     help="the Sec. IV studies instead: R_theta = b^2 (r_i = 1) and R_phi = r_i (R_theta = 1)")
+    ap.add_argument("--theta-resolved", action="store_true",
+                    help="--double-curved: the metric of each theta node (with --ntheta nodes)")
+    ap.add_argument("--ntheta", type=int, default=4, help="--double-curved: theta nodes")
+    ap.add_argument("--bs", default=None,
+                    help="--double-curved: the streamwise-curvature cases only, b values (comma list)")
+    ap.add_argument("--dean-range", default=None, help="--double-curved: lo,hi,n of the target Dean numbers")
     ap.add_argument("--continuation", default=None, metavar="ETA",
                     help="De_c of the cylinder of aspect ratio ETA (128 x 1 x 256, tau 0.9, Sec. III) "
                          "by continuation from a developed vortex")
@@ -808,8 +829,14 @@ if __name__ == "__main__":
                 json.dump(r, f)
         raise SystemExit(0)
     if a.double_curved:
-        r = double_curved_study(streamwise_curvature_cases() + cross_section_curvature_cases(),
-                                steps=a.steps, sample_every=a.sample_every)
+        cases = (streamwise_curvature_cases([float(x) for x in a.bs.split(",")]) if a.bs
+                 else streamwise_curvature_cases() + cross_section_curvature_cases())
+        deans = None
+        if a.dean_range:
+            lo, hi, n = a.dean_range.split(",")
+            deans = list(np.linspace(float(lo), float(hi), int(n)))
+        r = double_curved_study(cases, deans=deans, steps=a.steps, sample_every=a.sample_every,
+                                ntheta=a.ntheta, theta_resolved=a.theta_resolved)
         for c in r["cases"]:
             print("%-10s R_theta %.3f R_phi %.2f De_c %.2f  4-cell from De %.1f  6-cell from De %.1f  "
                   "cells %s  max drift %.3f" %
