@@ -44,3 +44,17 @@ def test_step_traffic_of_other_workloads(tmp_path, monkeypatch):
                  "    dram_bytes_per_step: 1")
     monkeypatch.setattr(bench, "STEP_PROFILES", {("ellipsoid", "fp32"): q})
     assert bench.step_traffic("ellipsoid", "fp32") is None          # another storage's sources
+
+
+def test_work_list_launches_per_class():
+    """gpu_launches of the tiled and batch steps: per metric kind the interior
+    tiles and each non-empty wall-node class (r-layer, x3-layer, the rest)."""
+    from oracle.geometry import Channel
+    from paper_1411_3133_gb300.workloads import ellipsoid_cross_section, mixed_batch
+    assert bench.work_lists([ellipsoid_cross_section(1.0)] * 24) == 4     # four walls: all classes
+    assert bench.work_lists(mixed_batch(seed=20241111)) == 6              # cylinders 2 + double-curved 4
+    cyl = Channel("cylindrical", 1.0, 1.1, 16, 4, 64)
+    assert bench.work_lists([cyl, cyl]) == 2                               # periodic x3: r-layer only
+    eq = Channel("ellipsoidal", 1.0, 1.1, 9, 4, 13, b=0.9, periodic3=False, wall="equilibrium")
+    assert bench.work_lists([eq]) == 2                                     # every wall node general
+    assert bench.work_lists([cyl, eq]) == 4
