@@ -20,14 +20,20 @@ namespace lbgm {
 // reference moments plus the weighted deviations, post-collision
 // deviations from collide_dev. Only equilibrium-wall nodes, which store
 // f^eq, encode against the reference table.
+// With `staged` (2-byte storage) the node's stream-table row is already in
+// shared memory (stage_table; the caller has waited for it), else it is
+// read from global memory.
 template <typename S, typename Real, int K>
 __device__ __forceinline__ void collide_store(Real (&f)[Q], S* __restrict__ fout, const float* ref,
                                               const GeoDev<Real>& geo, const InstParams<Real>& ip, const Dims& d,
-                                              const CellPos& p, int* __restrict__ flag) {
+                                              const CellPos& p, int* __restrict__ flag,
+                                              const TabStaged* staged = nullptr) {
   if constexpr (Codec<S, Real>::uses_ref) {
     const uint32_t stride = uint32_t(d.nr) * uint32_t(d.st_rows3);
     const float4* st = stream_of(d, p.b) + stream_row<K>(d, p.ir, p.i3);
-    const float4 ta = __ldg(st), tb = __ldg(st + stride), tc = __ldg(st + 2 * stride);
+    const float4 ta = staged ? staged->at(0) : __ldg(st);
+    const float4 tb = staged ? staged->at(1) : __ldg(st + stride);
+    const float4 tc = staged ? staged->at(2) : __ldg(st + 2 * stride);
     const Moments<float> m = moments_dev(f, ta, tb, tc);
     if (!finite_v(m.rho)) {
       if (*flag == 0) atomicExch(flag, 1);
@@ -40,7 +46,10 @@ __device__ __forceinline__ void collide_store(Real (&f)[Q], S* __restrict__ fout
       return;
     }
     const Coef<float> k = coefficients<float, K>(m, g, ip.kappa, ip.G);
-    collide_dev<K>(f, k, g, ip.omega, TabGlobal{st, stride}, tc.z);
+    if (staged)
+      collide_dev<K>(f, k, g, ip.omega, *staged, tc.z);
+    else
+      collide_dev<K>(f, k, g, ip.omega, TabGlobal{st, stride}, tc.z);
     store_raw<S>(fout, p, d, f);
     return;
   }
@@ -63,13 +72,33 @@ __device__ __forceinline__ void collide_store(Real (&f)[Q], S* __restrict__ fout
 // Fused time step of one node p of one instance whose state blocks start at
 // fin and fout (reference table ref): pull streaming + walls, then
 // collide_store.
+// 2-byte storage of the ellipsoid, whose stream rows are (i_r, i_3) -- one
+// per node: the node's stream-table row is staged into shared memory before
+// the gather (stage_table), so its latency runs under the gather's and no
+// register holds it meanwhile (the four-wall 24 x 64x4x256 ellipsoid in
+// FP16 storage 9.0 -> 10.3 GLUPS with 5 blocks per SM). Where a block's
+// nodes share one row (flat, cylinder) the table reads are broadcasts from
+// L1 and staging measured slower (128 mixed channels 12.1 -> 10.6).
+#ifndef LBGM_STAGE_TABLE
+#define LBGM_STAGE_TABLE 1
+#endif
 template <typename S, typename Real, int K, int WALLS = 2>
 __device__ __forceinline__ void step_node(const S* __restrict__ fin, S* __restrict__ fout, const float* ref,
                                           const GeoDev<Real>& geo, const InstParams<Real>& ip, const Dims& d,
                                           const CellPos& p, int* __restrict__ flag) {
   Real f[Q];
-  gather<K, S, Real, WALLS, Codec<S, Real>::uses_ref>(fin, ref, p, d, f);
-  collide_store<S, Real, K>(f, fout, ref, geo, ip, d, p, flag);
+  if constexpr (Codec<S, Real>::uses_ref && K == KELL && LBGM_STAGE_TABLE) {
+    __shared__ float4 s_tab[ST_K * 128];  // the 2-byte kernels' blocks hold at most 128 threads
+    const TabStaged tab{s_tab + threadIdx.x, int(blockDim.x)};
+    stage_table(s_tab + threadIdx.x, int(blockDim.x), stream_of(d, p.b) + stream_row<K>(d, p.ir, p.i3),
+                uint32_t(d.nr) * uint32_t(d.st_rows3));
+    gather<K, S, Real, WALLS, true>(fin, ref, p, d, f);
+    stage_wait();
+    collide_store<S, Real, K>(f, fout, ref, geo, ip, d, p, flag, &tab);
+  } else {
+    gather<K, S, Real, WALLS, Codec<S, Real>::uses_ref>(fin, ref, p, d, f);
+    collide_store<S, Real, K>(f, fout, ref, geo, ip, d, p, flag);
+  }
 }
 
 // Launch bounds of k_step per storage / compute type. FP32 arithmetic: at
@@ -95,17 +124,26 @@ struct StepBounds {
   static constexpr int maxt = LBGM_STEP32_MAXT;
   static constexpr int minb = sizeof(S) == 2 ? LBGM_STEP16_MINB : LBGM_STEP32_MINB;
 };
+// step_node's staged stream-table rows hold 128 threads' worth
+static_assert(StepBounds<__half, float>::maxt <= 128 && StepBounds<__nv_bfloat16, float>::maxt <= 128,
+              "2-byte blocks of at most 128 threads");
 template <>
 struct StepBounds<double, double> {
   static constexpr int maxt = 256, minb = 1;
 };
 // Per metric kind: one block fewer per SM for the ellipsoid with FP32
 // storage, whose (i_r, i_3) geometry rows and extra Christoffel terms need
-// more registers (the 2-byte kernels' cap already leaves room for them).
+// more registers; one more for the ellipsoid with 2-byte storage, whose
+// staged stream-table rows free the registers of the table prefetch
+// (LBGM_STEP16_KELL_MINB; measured 5 > 4).
+#ifndef LBGM_STEP16_KELL_MINB
+#define LBGM_STEP16_KELL_MINB 5
+#endif
 template <class S, class Real, int K>
 struct KBounds {
   static constexpr int maxt = StepBounds<S, Real>::maxt;
-  static constexpr int minb = (K == KELL || K == KELT) && sizeof(S) != 2 && StepBounds<S, Real>::minb > 1
+  static constexpr int minb = sizeof(S) == 2 && K == KELL ? LBGM_STEP16_KELL_MINB
+                              : (K == KELL || K == KELT) && sizeof(S) != 2 && StepBounds<S, Real>::minb > 1
                                   ? StepBounds<S, Real>::minb - 1
                                   : StepBounds<S, Real>::minb;
 };

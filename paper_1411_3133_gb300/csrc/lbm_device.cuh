@@ -1079,6 +1079,29 @@ struct TabShared {
   __device__ __forceinline__ float4 at(int k) const { return st[k]; }
 };
 
+// A node's stream-table row staged in shared memory by its own thread
+// (stage_table): entry k at st[k * stride], stride the block's threads.
+struct TabStaged {
+  const float4* st;
+  int stride;
+  __device__ __forceinline__ float4 at(int k) const { return st[k * stride]; }
+};
+
+// Copy the ST_K entries of stream-table row `row` (table st0 of rows
+// `stride` apart) into this thread's shared-memory slots dst[k * step] by
+// cp.async (16-byte copies that hold no registers while in flight), so
+// their latency runs under the node's gather. The caller waits with
+// stage_wait before reading them.
+__device__ __forceinline__ void stage_table(float4* dst, int step, const float4* __restrict__ st0, uint32_t stride) {
+#pragma unroll
+  for (int k = 0; k < ST_K; ++k) {
+    const uint32_t sa = static_cast<uint32_t>(__cvta_generic_to_shared(dst + k * step));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(st0 + k * stride) : "memory");
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void stage_wait() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
 // BGK collision with forcing on the stored deviations g of 2-byte storage,
 // in place (collide_pair with DEV), with the node's stream-table row tab.
 template <int K, class Tab>
