@@ -83,6 +83,7 @@ STEP_SOURCES = {p: ["paper_1411_3133_gb300/csrc/lbm_device.cuh", "paper_1411_313
                     "paper_1411_3133_gb300/csrc/lattice.cuh"]
                 for p, t in (("fp32", "f32"), ("fp16_shifted", "h16"), ("bf16_shifted", "b16"))}
 STEP_PROFILES = {("sweep", "fp16_shifted"): "k_step_split_fp16_cyl64x4x256_b24.md",
+                 ("ellipsoid", "fp16_shifted"): "k_step_list_fp16_ell64x4x256_b24.md",
                  ("ellipsoid", "fp32"): "k_step_list_fp32_ell64x4x256_b24.md",
                  ("mixed", "fp32"): "k_step_list_fp32_mixed128.md"}
 
