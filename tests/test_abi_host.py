@@ -208,3 +208,16 @@ def test_noalloc_binding_checks_fields_before_the_call(L):
         L.lb_diagnostics_noalloc("cylindrical", desc, [0.8, 0.7], good_rho, good_u)
     with pytest.raises(L.LBError, match="CUDA tensor"):
         L.lb_diagnostics_noalloc("cylindrical", desc, [0.8, 0.7], good_rho.numpy(), good_u)
+
+
+def test_theta_resolved_geometry_validation(L):
+    """The theta-resolved ellipsoid takes the ellipsoid's checks (b > 0, phi
+    off the poles) and writes one row per node."""
+    good = L.make_desc(1.0, 1.1, 8, 3, 10, 0.9, False)
+    rows = L.lb_geometry_eval("ellipsoidal_theta", good)
+    assert rows.shape == (8, 3, 10, 44)
+    for bad in (L.make_desc(1.0, 1.1, 8, 3, 10, -1.0, False),          # b <= 0
+                L.make_desc(1.0, 1.1, 8, 3, 400, 0.9, False, d3_scale=1.0)):  # phi reaches the pole
+        with pytest.raises(L.LBError) as e:
+            L.lb_geometry_eval("ellipsoidal_theta", bad)
+        assert e.value.status == L.LB_ERR_ARG
