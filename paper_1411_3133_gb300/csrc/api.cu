@@ -412,7 +412,8 @@ lb_status lb_create_geometry(lb_metric metric, const lb_geometry_desc* geom, int
   const double total = double(batch) * geom->nr * geom->ntheta * geom->n3;
   if (total >= 4294967295.0) return fail(nullptr, LB_ERR_ARG, "batch * nodes must fit in uint32");
   if (batch > 65535) return fail(nullptr, LB_ERR_ARG, "need batch <= 65535 (one grid row per instance)");
-  const double inst_bytes = double(Q) * geom->nr * geom->ntheta * geom->n3 * (prec == LB_FP64 ? 8 : prec == LB_FP32 ? 4 : 2);
+  const int pop_bytes = prec == LB_FP64 ? 8 : prec == LB_FP32 ? 4 : 2;
+  const double inst_bytes = double(Q) * geom->nr * geom->ntheta * geom->n3 * pop_bytes;
   if (inst_bytes >= 4294967296.0)
     return fail(nullptr, LB_ERR_ARG, "one instance's populations must stay below 4 GiB (32-bit offsets)");
   if (std::fabs(SQRT10 * SQRT10 - 10.0) > 1e-14 || std::fabs(SQRT10 - std::sqrt(10.0)) > 1e-15)
