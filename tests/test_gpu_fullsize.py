@@ -7,9 +7,11 @@ step kernel, CUDA-graph replay):
   the laminar profile plus 1e-4 noise, in FP32 storage (region-split step)
   and in FP16 and BF16 deviation storage;
 * the four-wall double-curved channel of Sec. IV.B (R2/R1 = 1, 64 x 4 x
-  256), 24 instances, FP32 (tiled step);
+  256), 24 instances, FP32 and FP16 storage (tiled step; the 2-byte kernels
+  stage each node's stream-table row in shared memory);
 * the 128-channel mixed batch (cylinders and double-curved channels, N_r in
-  {32, 48, 64}, N_3 in 128..512), FP32, one lb_batch after its autotuner.
+  {32, 48, 64}, N_3 in 128..512), FP32 and BF16 storage, one lb_batch after
+  its autotuner.
 
 The oracle recomputes one step at sampled nodes (the wall layers, the
 corners of the periodic wrap and of the x3 walls, the interior) from the
@@ -31,6 +33,12 @@ pytestmark = pytest.mark.gpu
 BENCH_THREADS = 128          # bench.py --threads default
 # per storage format: (populations, u against max |u|, rho' against max rho')
 TOL = {"fp32": (1e-6, 1e-5, 1e-6), "fp16_shifted": (1e-4, 1e-4, 1e-4), "bf16_shifted": (1e-3, 1e-3, 1e-3)}
+# channels started from rest keep the rest state as the 2-byte storage
+# reference, so the stored deviations are O(u / cs^2) and the format's
+# mantissa bounds u's error: 2^-11 (FP16) and 2^-8 (BF16) relative, i.e.
+# 1e-3 and 1e-2 of u_max (the reduced-precision bound; the sweep above stores
+# deviations from the laminar rows and keeps 1e-4 / 1e-3)
+TOL_REST = {"fp32": TOL["fp32"], "fp16_shifted": (1e-4, 1e-3, 1e-4), "bf16_shifted": (1e-3, 1e-2, 1e-3)}
 
 
 def _sample_cells(ch):
@@ -153,19 +161,20 @@ def test_fields_finite_and_subsonic(run):
     assert np.abs(u0).max() < 0.5 and rho0.min() > 0.9
 
 
-def test_ellipsoid_four_walls_sampled_nodes_match_oracle():
+@pytest.mark.parametrize("precision", ["fp32", "fp16_shifted"])
+def test_ellipsoid_four_walls_sampled_nodes_match_oracle(precision):
     """bench.py --workload ellipsoid: 24 instances of the 64 x 4 x 256
     double-curved channel with walls on r and phi, De 20..150 through the
     force of the cylinder of the same streamwise radius, tau 0.55, from rest
     plus noise; the tiled step (interior and wall-node tiles)."""
     L = lib()
-    wl = ellipsoid_cross_section(1.0, precision="fp32")
+    wl = ellipsoid_cross_section(1.0, precision=precision)
     ch = Channel(**wl.geometry_kwargs())
     ref = L.make_desc(1.0, 1.0 + (wl.r_outer - wl.r_inner), wl.nr, wl.ntheta, wl.n3)
     deans = np.linspace(20, 150, 24)
     Gs = [L.lb_force_for_dean("cylindrical", ref, 0.55, float(de)) for de in deans]
     params = [L.make_params(0.55, G, False, wl.seeds[0] + b, 1e-4, False) for b, G in enumerate(Gs)]
-    ctx = L.LBContext(spec_of(ch), batch=24, precision="fp32")
+    ctx = L.LBContext(spec_of(ch), batch=24, precision=precision)
     ctx.lb_set_option(L.LB_OPT_USE_GRAPH, 1)
     ctx.lb_set_option(L.LB_OPT_BLOCK_THREADS, BENCH_THREADS)
     ctx.lb_init(params)
@@ -180,17 +189,18 @@ def test_ellipsoid_four_walls_sampled_nodes_match_oracle():
     # now, where 1e-5 u_max lies above the FP32 resolution of populations
     # ~0.3 (the low-De instances' u_max ~ 1e-3 does not)
     for b in (12, 18, 23):
-        _check_step(ch, 0.55, Gs[b], f0[b], f1[b], TOL["fp32"], geo, smap)
+        _check_step(ch, 0.55, Gs[b], f0[b], f1[b], TOL_REST[precision], geo, smap)
 
 
-def test_mixed_batch_members_match_oracle():
+@pytest.mark.parametrize("precision", ["fp32", "bf16_shifted"])
+def test_mixed_batch_members_match_oracle(precision):
     """bench.py --workload mixed: the 128-channel batch after its autotuner,
     graph replay; members of both metric kinds and every N_r checked."""
     import torch
     from paper_1411_3133_gb300.sweep import mixed_contexts
     L = lib()
     insts = mixed_batch()
-    ctxs, batch = mixed_contexts(insts, "fp32")
+    ctxs, batch = mixed_contexts(insts, precision)
     batch.lb_batch_set_option(L.LB_OPT_USE_GRAPH, 1)
     batch.lb_batch_autotune(20)
     batch.lb_batch_step(1500)
@@ -216,7 +226,7 @@ def test_mixed_batch_members_match_oracle():
         G = L.lb_force_for_dean("cylindrical", L.make_desc(r["r_inner"], r["r_outer"], r["nr"], r["ntheta"],
                                                          r["n3"]), inst.tau, inst.dean)
         assert np.isfinite(f1[k]).all()
-        _check_step(ch, inst.tau, G, f0[k], f1[k], TOL["fp32"])
+        _check_step(ch, inst.tau, G, f0[k], f1[k], TOL_REST[precision])
 
 
 def test_fp32_laminar_2000_steps():
